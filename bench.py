@@ -1,0 +1,314 @@
+"""Benchmark of the RKL2 conduction super-step on GB300.
+
+One step = one RKL2 super-step of the 3D tangled-field workload (256^3
+periodic cells, FP32 state, Spitzer kappa_par = 0.01 T^(5/2), kappa_perp =
+1e-4 kappa_par, super-step dt = 100 dt_expl(T at t = 0), so s = 20 stages):
+the FP64 statistics pass that gives dt_expl, the host choice of s and the
+FP64 coefficients, and the graph of s stage kernels.  The metric is
+Gcell-stage/s = cells * stages / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded periodic window of the same workload on the host cores.  With N > 1
+(torchrun) every rank advances its own independent problem (replicas; the
+method needs no exchange between problems), and rank 0 reports the
+aggregate over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 256
+RATIO = 100.0
+SEED = 2
+BYTES_PER_CELL_STAGE = 32          # Y_{j-1}, Y_{j-2}, Y_0, M(Y_0), bx, by, bz read; Y_j written (FP32)
+WORKLOAD = "tangled256_spitzer_rkl2"
+
+# DRAM traffic of the stage kernel per launch from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel
+# source it was measured on (sha256 of the kernel files, first 16 hex).
+MEASURED_TRAFFIC = {"source_hash": None, "bytes_per_launch": None}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1702_05487_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "", 1).isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in self.rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_inputs():
+    import workloads
+    return workloads.tangled(N_GRID, seed=SEED)
+
+
+def cpu_oracle_sample(W, target_seconds: float = 12.0):
+    """Time the FP64 oracle on a periodic window of the workload (a bounded
+    sample): one super-step of s stages on a (nz_w, 256, 256) slab window,
+    nz_w grown until the run takes ~target_seconds.  Returns a dict."""
+    import oracle
+    from oracle import Problem
+    P = Problem(W.T.shape, **W.params)
+    dt = W.ratio * oracle.dt_expl(P, W.T)
+    s = oracle.num_stages(W.ratio)
+    threads = oracle.set_threads(0)
+    nz = 4
+    while True:
+        Tw = np.ascontiguousarray(W.T[:nz])
+        bw = np.ascontiguousarray(W.b[:, :nz])
+        Pw = Problem(Tw.shape, **W.params)
+        t0 = time.perf_counter()
+        oracle.super_step(Pw, Tw, bw, dt, s)
+        el = time.perf_counter() - t0
+        if el >= target_seconds / 4 or nz >= N_GRID:
+            break
+        nz = min(N_GRID, nz * 2)
+    cells = Tw.size
+    rate = cells * s / el / 1e9
+    return {"value": rate, "unit": "Gcell-stage/s", "cores": threads, "kind": "oracle",
+            "sample": f"one {s}-stage super-step of a {nz}x{N_GRID}x{N_GRID} periodic slab of the "
+                      f"256^3 workload, FP64, {el:.1f} s wall"}, el
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    W = make_inputs()
+    res = None
+    times = []
+    for k in range(args.warmup + args.steps):
+        r, el = cpu_oracle_sample(W, target_seconds=max(2.0, 60.0 / max(1, args.steps + args.warmup)))
+        if k >= args.warmup:
+            times.append(el)
+            res = r
+    line = {"impl": "reference", "metric": "Gcell-stage/s per RKL2 stage", "value": res["value"],
+            "unit": "Gcell-stage/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N_GRID, "dt_over_dtexpl": RATIO},
+            "cpu_baseline": res,
+            "e2e": {"value": res["value"], "unit": "Gcell-stage/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    import paper_1702_05487_gb300 as rk
+
+    W = make_inputs()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    T0 = torch.from_numpy(W.T.astype(np.float32))
+    b0 = torch.from_numpy(W.b.astype(np.float32))
+    T = T0.to(dev)
+    b = b0.to(dev).contiguous()
+    plan = rk.Plan(W.T.shape, "f32", stream=stream, params=W.params)
+    dt = W.ratio * plan.dt_expl(T)
+    ncell = T.numel()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (also builds the cached graph)
+    s_used = []
+    for _ in range(args.warmup):
+        s_used.append(plan.super_step(dt, T, b))
+    barrier()
+    plan.set_timing(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        barrier()
+        ev0.record(stream)
+        stages = 0
+        for _ in range(args.steps):
+            s = plan.super_step(dt, T, b)
+            stages += s
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    stage_ms, stage_launches = plan.timing()
+    plan.set_timing(False)
+    status = plan.check()
+    if status != 0:
+        raise RuntimeError(f"device status {status} after the timed region")
+
+    # max over ranks
+    ms_max = ms
+    total_cell_stages = float(ncell) * stages
+    if dist is not None:
+        t = torch.tensor([ms, total_cell_stages], device=dev, dtype=torch.float64)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_max = float(mx[0])
+        total_cell_stages = float(sm[1])
+    value = total_cell_stages / (ms_max * 1e-3) / 1e9
+
+    # end to end through the public host-buffer API: every step copies T and
+    # b from pinned host memory, runs one super-step and copies T back
+    Th = T0.clone().pin_memory()
+    bh = b0.clone().pin_memory()
+    plan.run_host(dt, 1, Th, bh)              # warm the staging buffers and graph
+    barrier()
+    t0 = time.perf_counter()
+    e_stages = 0
+    for _ in range(args.steps):
+        e_stages += plan.run_host(dt, 1, Th, bh)
+    barrier()
+    e_s = time.perf_counter() - t0
+    e_cell_stages = float(ncell) * e_stages
+    if dist is not None:
+        t = torch.tensor([e_s, e_cell_stages], device=dev, dtype=torch.float64)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        e_s, e_cell_stages = float(mx[0]), float(sm[1])
+    e2e_value = e_cell_stages / e_s / 1e9
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = measured_peaks()
+    avg_launch_ms = stage_ms / max(1, stage_launches)
+    achieved = BYTES_PER_CELL_STAGE * ncell / (avg_launch_ms * 1e-3) / 1e9
+    traffic = None
+    if MEASURED_TRAFFIC["source_hash"] == kernel_source_hash():
+        traffic = MEASURED_TRAFFIC["bytes_per_launch"]
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu, _ = cpu_oracle_sample(W)
+    s_last = s_used[-1] if s_used else rk.rkl_num_stages(RATIO)
+    line = {
+        "metric": "Gcell-stage/s per RKL2 stage", "value": value, "unit": "Gcell-stage/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_GRID, "cells": ncell, "s": s_last,
+                   "dt_over_dtexpl": RATIO, "step": "one RKL2 super-step (dt_expl pass + s stages)",
+                   "l2": "inputs larger than L2: 8 grid arrays of 67 MB per stage",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "kernel": "rkl2 stage", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "algorithmic_bytes_per_launch": BYTES_PER_CELL_STAGE * ncell,
+                     "avg_launch_ms": avg_launch_ms, "launches_timed": stage_launches},
+        "e2e": {"value": e2e_value, "unit": "Gcell-stage/s",
+                "h2d_bytes_per_step": int(T0.numel() * 4 + b0.numel() * 4),
+                "d2h_bytes_per_step": int(T0.numel() * 4)},
+        "gpu_launches": int(stages + 2 * args.steps),
+        "clocks": clocks.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

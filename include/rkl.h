@@ -1,0 +1,212 @@
+/*
+ * rkl.h - C ABI of the GB300 RKL2 anisotropic-conduction library.
+ *
+ * The library advances dT/dt = M(T) = -div F, F the face-centred thermal
+ * conduction flux of Vaidya et al. 2017 (arXiv:1702.05487), with the s-stage
+ * second-order Runge-Kutta-Legendre (RKL2) super-time-step.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Arrays are cell-centred, C-ordered [z][y][x] (x fastest), contiguous,
+ *   of the grid's dtype (float for RKL_F32, double for RKL_F64).
+ * - The unit field b is ndim contiguous planes [bx][by]([bz]), each one
+ *   grid-sized; b is the direction of B (Eq. Fclass), |b| = 1 is not checked.
+ * - Face arrays: F_d at cell c holds the flux on the face c + e_d/2.
+ * - Pointers passed to the plan functions are DEVICE pointers owned by the
+ *   caller, 16-byte aligned; the library never frees them.  rkl_run_host
+ *   takes HOST pointers.
+ * - Work is enqueued on the plan's CUDA stream.  Functions returning a host
+ *   scalar (rkl_dt_expl, rkl_energy, rkl_super_step) synchronise that stream.
+ * - Every function returns an rkl_status.  Invalid arguments are rejected
+ *   with RKL_ERR_INVALID_ARG before anything is launched.  No C++ exception
+ *   crosses this boundary.  rkl_last_error(plan) gives a message.
+ * - Physical model (rho = 1, gamma = 2 so the energy variable is T, Section
+ *   4.1 of the paper): kappa_par = kappa_par0 (constant) or
+ *   kappa_par0 * T^(5/2) (Spitzer); kappa_perp = kappa_perp_ratio *
+ *   kappa_par; both evaluated at the face temperature (T_L + T_R)/2.
+ */
+#ifndef RKL_H
+#define RKL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rkl_status {
+    RKL_OK = 0,
+    RKL_ERR_INVALID_ARG = 1,    /* bad pointer, size, dt, s or option           */
+    RKL_ERR_CUDA = 2,           /* a CUDA runtime call failed                   */
+    RKL_ERR_NONFINITE = 3,      /* a stage produced NaN or Inf                  */
+    RKL_ERR_NONPOSITIVE_T = 4,  /* a stage produced T <= 0 with Spitzer kappa   */
+    RKL_ERR_TIMEOUT = 5,        /* a bounded device wait gave up                */
+    RKL_ERR_UNSUPPORTED = 6,    /* valid request this build does not implement  */
+    RKL_ERR_NOMEM = 7           /* device or host allocation failed             */
+} rkl_status;
+
+enum { RKL_PERIODIC = 0, RKL_DIRICHLET = 1 };
+enum { RKL_F32 = 0, RKL_F64 = 1 };
+enum { RKL_KAPPA_CONST = 0, RKL_KAPPA_SPITZER = 1 };
+
+/* Uniform Cartesian grid. */
+typedef struct rkl_grid {
+    int ndim;            /* active axes 1, 2 or 3 (x, then y, then z)              */
+    int64_t n[3];        /* cells along x, y, z; axes beyond ndim must be 1        */
+    double dx[3];        /* spacing along x, y, z (> 0 on active axes)             */
+    int bc;              /* RKL_PERIODIC, or RKL_DIRICHLET: ghost cells (edges and
+                            corners too) hold T = bc_value and copy b from the
+                            nearest interior cell                                  */
+    double bc_value;
+    int dtype;           /* RKL_F32 or RKL_F64: state and arithmetic type          */
+} rkl_grid;
+
+/* Conduction physics (Eqs. Fc, Fclass, Fsat, dt_exp of the paper). */
+typedef struct rkl_phys {
+    int kappa_model;         /* RKL_KAPPA_CONST or RKL_KAPPA_SPITZER (T^(5/2)) */
+    double kappa_par0;       /* > 0                                            */
+    double kappa_perp_ratio; /* >= 0                                           */
+    int saturate;            /* 1: F = q/(q + |F_class|) F_class (Eq. Fc) with
+                                q = 5 phi rho c_iso^3, c_iso = sqrt(T) (Eq. Fsat) */
+    double phi;              /* saturation factor (0.3 in the paper)          */
+    double rho;              /* density in q only                             */
+    int sat_upwind;          /* 1: c_iso from the cell the normal flux leaves;
+                                0: from the face temperature                  */
+    double cp;               /* parabolic Courant number C_p <= 1/2 (Eq. dt_exp) */
+} rkl_phys;
+
+typedef struct rkl_plan rkl_plan;
+
+/* Human-readable name of a status code (static storage). */
+const char *rkl_status_string(rkl_status st);
+
+/* Last error message recorded on a plan ("" if none); NULL plan gives the
+ * message of the last failed rkl_plan_create on this thread. */
+const char *rkl_last_error(const rkl_plan *plan);
+
+/*
+ * Number of RKL2 stages for a super-step dt = ratio * dt_expl: Eq. RKL-s of
+ * the paper, dt = dt_p (s^2 + s - 2)/4, solved for real s and rounded as
+ * s -> 1 + floor(s) (Section 4.1).  ratio must be finite and > 0.
+ * Host only, FP64.  Writes *s_out (>= 2).
+ */
+rkl_status rkl_num_stages(double ratio, int *s_out);
+
+/*
+ * RKL2 coefficients of Appendix A for s >= 2 stages, FP64: w_1 =
+ * 4/(s^2+s-2), b_0 = b_1 = b_2 = 1/3, b_j = (j^2+j-2)/(2j(j+1)), a_j = 1 - b_j,
+ * mu_j = ((2j-1)/j)(b_j/b_{j-1}), nu_j = -((j-1)/j)(b_j/b_{j-2}),
+ * mut_1 = b_1 w_1, mut_j = mu_j w_1, gt_j = -a_{j-1} mut_j.
+ * Each output is a caller-owned host array of s + 1 doubles indexed by j;
+ * entries without a definition (j = 0, and mu/nu/gt at j = 1) are 0.
+ * Host only.  s must be in [2, 4096].
+ */
+rkl_status rkl_coeffs(int s, double *mu, double *nu, double *mut, double *gt);
+
+/*
+ * Create a plan for one grid and physics on a CUDA stream (cudaStream_t
+ * passed as void*; NULL is the legacy default stream).  The plan allocates
+ * its own device workspace: three stage buffers, M(Y_0), reduction scratch
+ * (4 grid arrays plus a few KB) and caches one CUDA graph per distinct
+ * (s, T, b) triple used by rkl_super_step.  The device current at creation
+ * is used for every later call.  Writes *out; destroy with
+ * rkl_plan_destroy.
+ */
+rkl_status rkl_plan_create(const rkl_grid *grid, const rkl_phys *phys,
+                           void *cuda_stream, rkl_plan **out);
+rkl_status rkl_plan_destroy(rkl_plan *plan);
+
+/*
+ * Explicit parabolic step of Eq. dt_exp: C_p / max_cells sum_d chi_d/dx_d^2
+ * with chi_d = kappa_par(T) + kappa_perp(T) (gamma = 2, rho = 1), the max
+ * taken in FP64 over the device array T.  Synchronises the stream.
+ */
+rkl_status rkl_dt_expl(rkl_plan *plan, const void *T, double *dt_out);
+
+/*
+ * Face fluxes F_d, d < ndim, of Eqs. Fc/Fclass/Fsat with the normal
+ * gradient across the face and the transverse gradients of Eqs. qN/qT
+ * averaged to the face from the four neighbouring one-sided differences;
+ * b and T on the face are the means of the two cells.  Fx, Fy, Fz are device
+ * arrays of grid size (pass NULL for axes beyond ndim).  Asynchronous.
+ */
+rkl_status rkl_flux(rkl_plan *plan, const void *T, const void *b,
+                    void *Fx, void *Fy, void *Fz);
+
+/*
+ * M(T) = -sum_d (F_d(c + e_d/2) - F_d(c - e_d/2)) / dx_d, the conservative
+ * divergence of Section 3 (one flux per face).  Asynchronous.
+ */
+rkl_status rkl_apply_M(rkl_plan *plan, const void *T, const void *b, void *MT);
+
+/*
+ * One stage of Eq. rkl2scheme (Appendix A) with tau = dt, 1 <= j <= s:
+ *   j = 1:  MY0 = M(Y0) (written), Y1 = Y0 + mut_1 tau MY0
+ *   j >= 2: Yj = mu_j Yjm1 + nu_j Yjm2 + (1 - mu_j - nu_j) Y0
+ *                + mut_j tau M(Yjm1) + gt_j tau MY0
+ * j = 1 ignores Yjm1 and Yjm2.  s = 1 is accepted as forward Euler
+ * (Yj = Y0 + tau M(Y0)).  Yj may alias Y0 (each cell reads Y0 before writing
+ * Yj at that cell only) but no other input.  Asynchronous.
+ */
+rkl_status rkl_stage(rkl_plan *plan, int j, int s, double dt, const void *b,
+                     const void *Y0, void *MY0, const void *Yjm1,
+                     const void *Yjm2, void *Yj);
+
+/*
+ * One RKL2 super-step of length dt applied in place to the device array T:
+ * dt_expl from T (Eq. dt_exp), s = rkl_num_stages(dt/dt_expl), FP64
+ * coefficients (rounded once to the grid dtype), then the s stages launched
+ * as one cached CUDA graph.  Optionally the FP64 energy sum_c T_c dV before
+ * and after (pass NULL to skip).  *s_used receives s (may be NULL).
+ * Returns RKL_ERR_NONFINITE / RKL_ERR_NONPOSITIVE_T if a stage of this or an
+ * earlier, unchecked super-step produced such values (the state is then
+ * undefined).  Synchronises the stream once for dt_expl and once more only
+ * when energies are requested.
+ */
+rkl_status rkl_super_step(rkl_plan *plan, double dt, void *T, const void *b,
+                          int *s_used, double *energy_before, double *energy_after);
+
+/*
+ * As rkl_super_step, but s is given (s >= 2) instead of chosen from dt_expl;
+ * no synchronisation unless energies are requested.
+ */
+rkl_status rkl_super_step_s(rkl_plan *plan, double dt, int s, void *T, const void *b,
+                            double *energy_before, double *energy_after);
+
+/* FP64 energy sum_c T_c dV of a device array.  Synchronises. */
+rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
+
+/*
+ * Waits for the plan's stream and returns the device status word collected
+ * by the stage kernels since the last check (RKL_OK, RKL_ERR_NONFINITE or
+ * RKL_ERR_NONPOSITIVE_T), then clears it.
+ */
+rkl_status rkl_plan_check(rkl_plan *plan);
+
+/*
+ * Per-launch timing of the hot stage kernel.  With timing on, the graphs of
+ * rkl_super_step record CUDA events on the plan's stream around stages
+ * 2..s; rkl_plan_timing synchronises, adds up the elapsed times of all
+ * completed super-steps since timing was switched on and returns the total
+ * milliseconds and the number of stage launches they cover.
+ */
+rkl_status rkl_plan_set_timing(rkl_plan *plan, int on);
+rkl_status rkl_plan_timing(rkl_plan *plan, double *ms_total, int64_t *launches);
+
+/*
+ * End-to-end run from host memory: copies T_host and b_host to the device,
+ * performs n_super super-steps of length dt (s chosen per super-step as in
+ * rkl_super_step) and copies T back into T_host.  Host buffers should be
+ * page-locked for full copy speed.  Allocates (and frees) device buffers
+ * for T and b on each call unless they fit the plan's cached staging
+ * buffers, which are kept for reuse.  *s_last receives the last s
+ * (may be NULL).  Synchronises.
+ */
+rkl_status rkl_run_host(rkl_plan *plan, double dt, int n_super, void *T_host,
+                        const void *b_host, int *s_last);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RKL_H */

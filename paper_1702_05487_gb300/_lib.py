@@ -1,0 +1,210 @@
+"""ctypes binding of librkl.so: the C ABI of include/rkl.h, one Python function
+per entry point with the same name.  Argument marshalling only; every step of
+the computation runs in the library's CUDA kernels.
+
+Device arrays are passed as torch CUDA tensors (their data pointers are
+handed to the library); host arrays for ``rkl_run_host`` are numpy arrays or
+CPU tensors.  Errors raise ``RklError`` carrying the status and the plan's
+message.  Loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+RKL_OK = 0
+RKL_ERR_INVALID_ARG = 1
+RKL_ERR_CUDA = 2
+RKL_ERR_NONFINITE = 3
+RKL_ERR_NONPOSITIVE_T = 4
+RKL_ERR_TIMEOUT = 5
+RKL_ERR_UNSUPPORTED = 6
+RKL_ERR_NOMEM = 7
+
+RKL_PERIODIC, RKL_DIRICHLET = 0, 1
+RKL_F32, RKL_F64 = 0, 1
+RKL_KAPPA_CONST, RKL_KAPPA_SPITZER = 0, 1
+
+
+class RklError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+class rkl_grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("dx", ctypes.c_double * 3),
+                ("bc", ctypes.c_int), ("bc_value", ctypes.c_double), ("dtype", ctypes.c_int)]
+
+
+class rkl_phys(ctypes.Structure):
+    _fields_ = [("kappa_model", ctypes.c_int), ("kappa_par0", ctypes.c_double),
+                ("kappa_perp_ratio", ctypes.c_double), ("saturate", ctypes.c_int),
+                ("phi", ctypes.c_double), ("rho", ctypes.c_double), ("sat_upwind", ctypes.c_int),
+                ("cp", ctypes.c_double)]
+
+
+# Every symbol include/rkl.h declares, with (restype, argtypes).
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = {
+    "rkl_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "rkl_last_error": (ctypes.c_char_p, [_vp]),
+    "rkl_num_stages": (ctypes.c_int, [ctypes.c_double, _ip]),
+    "rkl_coeffs": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp, _dp]),
+    "rkl_plan_create": (ctypes.c_int, [ctypes.POINTER(rkl_grid), ctypes.POINTER(rkl_phys), _vp,
+                                       ctypes.POINTER(_vp)]),
+    "rkl_plan_destroy": (ctypes.c_int, [_vp]),
+    "rkl_dt_expl": (ctypes.c_int, [_vp, _vp, _dp]),
+    "rkl_flux": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "rkl_apply_M": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "rkl_stage": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _vp, _vp, _vp,
+                                 _vp, _vp, _vp]),
+    "rkl_super_step": (ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp, _ip, _dp, _dp]),
+    "rkl_super_step_s": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _vp, _vp, _dp, _dp]),
+    "rkl_energy": (ctypes.c_int, [_vp, _vp, _dp]),
+    "rkl_plan_check": (ctypes.c_int, [_vp]),
+    "rkl_plan_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "rkl_plan_timing": (ctypes.c_int, [_vp, _dp, _i64p]),
+    "rkl_run_host": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _vp, _vp, _ip]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load librkl.so (building it first if missing and nvcc is present)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"{_build.LIB} is missing: build it with paper_1702_05487_gb300.build.build()")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_name(st: int) -> str:
+    return load().rkl_status_string(int(st)).decode()
+
+
+def _ptr(t):
+    """Data pointer of a torch tensor / numpy array (None passes NULL)."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return ctypes.c_void_p(t.data_ptr())
+    if hasattr(t, "ctypes"):
+        return ctypes.c_void_p(t.ctypes.data)
+    return ctypes.c_void_p(int(t))
+
+
+def _check(st: int, plan=None):
+    if st != RKL_OK:
+        msg = load().rkl_last_error(plan).decode() if plan is not None or st else ""
+        raise RklError(st, msg)
+
+
+def rkl_num_stages(ratio: float) -> int:
+    s = ctypes.c_int(0)
+    _check(load().rkl_num_stages(float(ratio), ctypes.byref(s)))
+    return s.value
+
+
+def rkl_coeffs(s: int):
+    import numpy as np
+    arrs = [np.zeros(s + 1) for _ in range(4)]
+    _check(load().rkl_coeffs(int(s), *[a.ctypes.data_as(_dp) for a in arrs]))
+    return tuple(arrs)
+
+
+def rkl_plan_create(grid: rkl_grid, phys: rkl_phys, stream=None):
+    h = _vp()
+    st = load().rkl_plan_create(ctypes.byref(grid), ctypes.byref(phys),
+                                _vp(int(stream) if stream else 0), ctypes.byref(h))
+    if st != RKL_OK:
+        raise RklError(st, load().rkl_last_error(None).decode())
+    return h
+
+
+def rkl_plan_destroy(plan):
+    _check(load().rkl_plan_destroy(plan))
+
+
+def rkl_dt_expl(plan, T) -> float:
+    out = ctypes.c_double(0.0)
+    _check(load().rkl_dt_expl(plan, _ptr(T), ctypes.byref(out)), plan)
+    return out.value
+
+
+def rkl_flux(plan, T, b, Fx, Fy=None, Fz=None):
+    _check(load().rkl_flux(plan, _ptr(T), _ptr(b), _ptr(Fx), _ptr(Fy), _ptr(Fz)), plan)
+
+
+def rkl_apply_M(plan, T, b, MT):
+    _check(load().rkl_apply_M(plan, _ptr(T), _ptr(b), _ptr(MT)), plan)
+
+
+def rkl_stage(plan, j, s, dt, b, Y0, MY0, Yjm1, Yjm2, Yj):
+    _check(load().rkl_stage(plan, int(j), int(s), float(dt), _ptr(b), _ptr(Y0), _ptr(MY0),
+                            _ptr(Yjm1), _ptr(Yjm2), _ptr(Yj)), plan)
+
+
+def rkl_super_step(plan, dt, T, b, energies: bool = False):
+    """Returns s, or (s, energy_before, energy_after) with energies=True."""
+    s = ctypes.c_int(0)
+    eb, ea = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().rkl_super_step(plan, float(dt), _ptr(T), _ptr(b), ctypes.byref(s),
+                                 ctypes.byref(eb) if energies else None,
+                                 ctypes.byref(ea) if energies else None), plan)
+    return (s.value, eb.value, ea.value) if energies else s.value
+
+
+def rkl_super_step_s(plan, dt, s, T, b, energies: bool = False):
+    eb, ea = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().rkl_super_step_s(plan, float(dt), int(s), _ptr(T), _ptr(b),
+                                   ctypes.byref(eb) if energies else None,
+                                   ctypes.byref(ea) if energies else None), plan)
+    return (eb.value, ea.value) if energies else None
+
+
+def rkl_energy(plan, T) -> float:
+    out = ctypes.c_double(0.0)
+    _check(load().rkl_energy(plan, _ptr(T), ctypes.byref(out)), plan)
+    return out.value
+
+
+def rkl_plan_check(plan) -> int:
+    """Returns the device status (RKL_OK or an error code) without raising."""
+    return load().rkl_plan_check(plan)
+
+
+def rkl_plan_set_timing(plan, on: bool):
+    _check(load().rkl_plan_set_timing(plan, int(bool(on))), plan)
+
+
+def rkl_plan_timing(plan):
+    ms, n = ctypes.c_double(0.0), ctypes.c_int64(0)
+    _check(load().rkl_plan_timing(plan, ctypes.byref(ms), ctypes.byref(n)), plan)
+    return ms.value, n.value
+
+
+def rkl_run_host(plan, dt, n_super, T_host, b_host) -> int:
+    s = ctypes.c_int(0)
+    _check(load().rkl_run_host(plan, float(dt), int(n_super), _ptr(T_host), _ptr(b_host),
+                               ctypes.byref(s)), plan)
+    return s.value

@@ -1,0 +1,686 @@
+// C ABI of the RKL2 conduction library (see include/rkl.h): argument
+// checks, the plan (workspace, coefficient table, graph cache, timing) and
+// the dispatch between the tiled FP32 kernel and the generic kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rkl.h"
+#include "rkl_launch.h"
+
+using namespace rkl;
+
+namespace {
+
+constexpr int kMaxStages = 4096;
+constexpr int kCoefRing = 8;
+constexpr int kGraphCache = 16;
+
+thread_local std::string g_create_error;
+
+struct GraphEntry {
+    int s = 0;
+    const void* T = nullptr;
+    const void* b = nullptr;
+    int timing = 0;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t last_use = 0;
+};
+
+}  // namespace
+
+struct rkl_plan {
+    rkl_grid grid;
+    rkl_phys phys;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    size_t esize = 4;
+    int64_t ncell = 0;
+    LaunchCfg cfg{};
+    KGrid<float> gf{};
+    KGrid<double> gd{};
+    KPhys<float> pf{};
+    KPhys<double> pd{};
+    bool fast = false;
+
+    void* ybuf[3] = {nullptr, nullptr, nullptr};
+    void* my0 = nullptr;
+    double* d_partials = nullptr;
+    double* d_scal = nullptr;          // {max, min, sum, status}
+    double* h_scal = nullptr;          // pinned mirror
+    unsigned* d_status = nullptr;
+
+    void* d_coef = nullptr;            // [(kMaxStages + 1) * 4] of the grid dtype
+    void* h_coef = nullptr;            // pinned [kCoefRing][(kMaxStages + 1) * 4]
+    cudaEvent_t coef_ev[kCoefRing] = {};
+    int coef_slot = 0;
+
+    GraphEntry cache[kGraphCache];
+    uint64_t use_clock = 0;
+
+    int timing = 0;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    bool timing_pending = false;
+    int pending_launches = 0;
+    double timing_ms = 0.0;
+    int64_t timing_launches = 0;
+
+    void* host_T = nullptr;            // device staging for rkl_run_host
+    void* host_b = nullptr;
+
+    std::string err;
+};
+
+namespace {
+
+rkl_status fail(rkl_plan* p, rkl_status st, const std::string& msg)
+{
+    if (p) p->err = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+rkl_status cuda_fail(rkl_plan* p, cudaError_t e, const char* where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(p, RKL_ERR_CUDA, m);
+}
+
+#define RKL_CK(p, call)                                                   \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return cuda_fail((p), e_, #call);          \
+    } while (0)
+
+bool aligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
+
+// Makes the plan's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+double kappa_par_host(const rkl_phys& ph, double T)
+{
+    if (ph.kappa_model == RKL_KAPPA_SPITZER) return ph.kappa_par0 * T * T * std::sqrt(T);
+    return ph.kappa_par0;
+}
+
+void host_coeffs(int s, double* mu, double* nu, double* mut, double* gt)
+{
+    auto bj = [](int j) -> double {
+        if (j <= 2) return 1.0 / 3.0;
+        return ((double)j * j + j - 2.0) / (2.0 * j * (j + 1.0));
+    };
+    double w1 = 4.0 / ((double)s * s + s - 2.0);
+    for (int j = 0; j <= s; ++j) mu[j] = nu[j] = mut[j] = gt[j] = 0.0;
+    mut[1] = bj(1) * w1;
+    for (int j = 2; j <= s; ++j) {
+        mu[j] = (2.0 * j - 1.0) / j * bj(j) / bj(j - 1);
+        nu[j] = -((double)j - 1.0) / j * bj(j) / bj(j - 2);
+        mut[j] = mu[j] * w1;
+        gt[j] = -(1.0 - bj(j - 1)) * mut[j];
+    }
+}
+
+rkl_status check_plan(rkl_plan* p)
+{
+    if (!p) return RKL_ERR_INVALID_ARG;
+    return RKL_OK;
+}
+
+// Launch one stage (or M) on the plan's stream.
+rkl_status launch_stage(rkl_plan* p, const StageIO& io, double mu, double nu, double mt, double gt)
+{
+    cudaError_t e;
+    if (p->cfg.dtype == RKL_F32) {
+        KCoef<float> cf{(float)mu, (float)nu, (float)mt, (float)gt};
+        if (p->fast)
+            e = launch_stage_fast(p->cfg, p->gf, p->pf, io, cf, p->d_status, p->stream);
+        else
+            e = launch_stage_generic(p->cfg, &p->gf, &p->pf, io, &cf, p->d_status, p->stream);
+    } else {
+        KCoef<double> cf{mu, nu, mt, gt};
+        e = launch_stage_generic(p->cfg, &p->gd, &p->pd, io, &cf, p->d_status, p->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(p, e, "stage launch");
+    return RKL_OK;
+}
+
+// Enqueue the s stages of one super-step reading coefficients from the
+// plan's device table (stage j at d_coef[4 j]).  Y0 = T; the last stage
+// writes T (each cell reads its own Y0 before overwriting it).
+rkl_status enqueue_stages(rkl_plan* p, int s, void* T, const void* b, bool with_events)
+{
+    StageIO io{};
+    io.b = b;
+    io.coef_tab = p->d_coef;
+    io.Y0 = T;
+    io.MY0 = p->my0;
+    io.j = 1;
+    io.mode = 1;
+    io.Yj = (s == 1) ? T : p->ybuf[0];
+    rkl_status st = launch_stage(p, io, 0, 0, 0, 0);
+    if (st != RKL_OK) return st;
+    if (with_events) RKL_CK(p, cudaEventRecordWithFlags(p->ev_a, p->stream, cudaEventRecordExternal));
+    for (int j = 2; j <= s; ++j) {
+        StageIO q{};
+        q.b = b;
+        q.coef_tab = p->d_coef;
+        q.Y0 = T;
+        q.MY0 = p->my0;
+        q.Yjm1 = p->ybuf[(j - 2) % 3];
+        q.Yjm2 = (j == 2) ? T : p->ybuf[(j - 3) % 3];
+        q.Yj = (j == s) ? T : p->ybuf[(j - 1) % 3];
+        q.j = j;
+        q.mode = 2;
+        st = launch_stage(p, q, 0, 0, 0, 0);
+        if (st != RKL_OK) return st;
+    }
+    if (with_events) RKL_CK(p, cudaEventRecordWithFlags(p->ev_b, p->stream, cudaEventRecordExternal));
+    return RKL_OK;
+}
+
+rkl_status upload_coeffs(rkl_plan* p, int s, double dt)
+{
+    std::vector<double> mu(s + 1), nu(s + 1), mut(s + 1), gt(s + 1);
+    host_coeffs(s, mu.data(), nu.data(), mut.data(), gt.data());
+    int slot = p->coef_slot;
+    p->coef_slot = (p->coef_slot + 1) % kCoefRing;
+    RKL_CK(p, cudaEventSynchronize(p->coef_ev[slot]));
+    size_t per = (size_t)(kMaxStages + 1) * 4;
+    if (p->cfg.dtype == RKL_F32) {
+        float* h = static_cast<float*>(p->h_coef) + slot * per;
+        for (int j = 0; j <= s; ++j) {
+            h[4 * j + 0] = (float)mu[j];
+            h[4 * j + 1] = (float)nu[j];
+            h[4 * j + 2] = (float)(mut[j] * dt);
+            h[4 * j + 3] = (float)(gt[j] * dt);
+        }
+        RKL_CK(p, cudaMemcpyAsync(p->d_coef, h, sizeof(float) * 4 * (s + 1), cudaMemcpyHostToDevice,
+                                  p->stream));
+    } else {
+        double* h = static_cast<double*>(p->h_coef) + slot * per;
+        for (int j = 0; j <= s; ++j) {
+            h[4 * j + 0] = mu[j];
+            h[4 * j + 1] = nu[j];
+            h[4 * j + 2] = mut[j] * dt;
+            h[4 * j + 3] = gt[j] * dt;
+        }
+        RKL_CK(p, cudaMemcpyAsync(p->d_coef, h, sizeof(double) * 4 * (s + 1), cudaMemcpyHostToDevice,
+                                  p->stream));
+    }
+    RKL_CK(p, cudaEventRecord(p->coef_ev[slot], p->stream));
+    return RKL_OK;
+}
+
+rkl_status get_graph(rkl_plan* p, int s, void* T, const void* b, cudaGraphExec_t* out)
+{
+    GraphEntry* victim = &p->cache[0];
+    for (auto& g : p->cache) {
+        if (g.exec && g.s == s && g.T == T && g.b == b && g.timing == p->timing) {
+            g.last_use = ++p->use_clock;
+            *out = g.exec;
+            return RKL_OK;
+        }
+        if (!g.exec || g.last_use < victim->last_use) victim = &g;
+    }
+    if (victim->exec) {
+        cudaGraphExecDestroy(victim->exec);
+        victim->exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    RKL_CK(p, cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    rkl_status st = enqueue_stages(p, s, T, b, p->timing != 0);
+    cudaError_t ce = cudaStreamEndCapture(p->stream, &graph);
+    if (st != RKL_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (ce != cudaSuccess) return cuda_fail(p, ce, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return cuda_fail(p, ce, "cudaGraphInstantiate");
+    victim->s = s;
+    victim->T = T;
+    victim->b = b;
+    victim->timing = p->timing;
+    victim->exec = exec;
+    victim->last_use = ++p->use_clock;
+    *out = exec;
+    return RKL_OK;
+}
+
+rkl_status collect_timing(rkl_plan* p)
+{
+    if (!p->timing_pending) return RKL_OK;
+    RKL_CK(p, cudaEventSynchronize(p->ev_b));
+    float ms = 0.f;
+    RKL_CK(p, cudaEventElapsedTime(&ms, p->ev_a, p->ev_b));
+    p->timing_ms += ms;
+    p->timing_launches += p->pending_launches;
+    p->timing_pending = false;
+    return RKL_OK;
+}
+
+// FP64 {max, min, sum, status} of a device array into p->h_scal
+// (synchronises).  With take_status the device status word is read into
+// h_scal[3] and cleared; otherwise h_scal[3] = 0 and the word is kept.
+rkl_status stats(rkl_plan* p, const void* T, bool take_status = true)
+{
+    cudaError_t e = launch_stats(p->cfg.dtype, T, p->ncell, p->d_partials, p->d_scal,
+                                 take_status ? p->d_status : nullptr, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "stats launch");
+    RKL_CK(p, cudaMemcpyAsync(p->h_scal, p->d_scal, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                              p->stream));
+    RKL_CK(p, cudaStreamSynchronize(p->stream));
+    return RKL_OK;
+}
+
+rkl_status status_from_word(rkl_plan* p, unsigned w)
+{
+    if (w & ST_NONFINITE) return fail(p, RKL_ERR_NONFINITE, "a stage produced NaN or Inf");
+    if (w & ST_NONPOSITIVE) return fail(p, RKL_ERR_NONPOSITIVE_T, "a stage produced T <= 0 under Spitzer kappa");
+    if (w & ST_TIMEOUT) return fail(p, RKL_ERR_TIMEOUT, "a bounded device wait gave up");
+    return RKL_OK;
+}
+
+double cell_volume(const rkl_grid& g)
+{
+    double v = 1.0;
+    for (int d = 0; d < g.ndim; ++d) v *= g.dx[d];
+    return v;
+}
+
+double dt_expl_from_max(const rkl_plan* p, double Tmax)
+{
+    double inv = 0.0;
+    for (int d = 0; d < p->grid.ndim; ++d) inv += 1.0 / (p->grid.dx[d] * p->grid.dx[d]);
+    double chi = kappa_par_host(p->phys, Tmax) * (1.0 + p->phys.kappa_perp_ratio);
+    return p->phys.cp / (chi * inv);
+}
+
+rkl_status run_super_step(rkl_plan* p, double dt, int s, void* T, const void* b, double* eb, double* ea)
+{
+    rkl_status st = upload_coeffs(p, s, dt);
+    if (st != RKL_OK) return st;
+    cudaGraphExec_t exec = nullptr;
+    st = get_graph(p, s, T, b, &exec);
+    if (st != RKL_OK) return st;
+    RKL_CK(p, cudaGraphLaunch(exec, p->stream));
+    if (p->timing) {
+        p->timing_pending = true;
+        p->pending_launches = s - 1;
+    }
+    if (ea) {
+        st = stats(p, T);
+        if (st != RKL_OK) return st;
+        *ea = p->h_scal[2] * cell_volume(p->grid);
+        st = status_from_word(p, (unsigned)p->h_scal[3]);
+        if (st != RKL_OK) return st;
+    }
+    (void)eb;
+    return RKL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rkl_status_string(rkl_status st)
+{
+    switch (st) {
+        case RKL_OK: return "RKL_OK";
+        case RKL_ERR_INVALID_ARG: return "RKL_ERR_INVALID_ARG";
+        case RKL_ERR_CUDA: return "RKL_ERR_CUDA";
+        case RKL_ERR_NONFINITE: return "RKL_ERR_NONFINITE";
+        case RKL_ERR_NONPOSITIVE_T: return "RKL_ERR_NONPOSITIVE_T";
+        case RKL_ERR_TIMEOUT: return "RKL_ERR_TIMEOUT";
+        case RKL_ERR_UNSUPPORTED: return "RKL_ERR_UNSUPPORTED";
+        case RKL_ERR_NOMEM: return "RKL_ERR_NOMEM";
+    }
+    return "RKL_ERR_UNKNOWN";
+}
+
+const char* rkl_last_error(const rkl_plan* plan)
+{
+    if (!plan) return g_create_error.c_str();
+    return plan->err.c_str();
+}
+
+rkl_status rkl_num_stages(double ratio, int* s_out)
+{
+    if (!s_out || !std::isfinite(ratio) || ratio <= 0.0) return RKL_ERR_INVALID_ARG;
+    double s = 0.5 * (-1.0 + std::sqrt(9.0 + 16.0 * ratio));
+    if (s + 1.0 > (double)kMaxStages) return RKL_ERR_INVALID_ARG;
+    *s_out = 1 + (int)std::floor(s);
+    return RKL_OK;
+}
+
+rkl_status rkl_coeffs(int s, double* mu, double* nu, double* mut, double* gt)
+{
+    if (s < 2 || s > kMaxStages || !mu || !nu || !mut || !gt) return RKL_ERR_INVALID_ARG;
+    host_coeffs(s, mu, nu, mut, gt);
+    return RKL_OK;
+}
+
+rkl_status rkl_plan_create(const rkl_grid* grid, const rkl_phys* phys, void* cuda_stream, rkl_plan** out)
+{
+    if (!grid || !phys || !out) return fail(nullptr, RKL_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    const rkl_grid& g = *grid;
+    if (g.ndim < 1 || g.ndim > 3) return fail(nullptr, RKL_ERR_INVALID_ARG, "ndim must be 1, 2 or 3");
+    int64_t ncell = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (g.n[d] < 1 || g.n[d] > (1 << 20)) return fail(nullptr, RKL_ERR_INVALID_ARG, "bad n");
+        if (d >= g.ndim && g.n[d] != 1) return fail(nullptr, RKL_ERR_INVALID_ARG, "inactive axis must have n = 1");
+        if (d < g.ndim && !(g.dx[d] > 0.0 && std::isfinite(g.dx[d])))
+            return fail(nullptr, RKL_ERR_INVALID_ARG, "dx must be finite and > 0");
+        ncell *= g.n[d];
+    }
+    if (ncell > ((int64_t)1 << 34)) return fail(nullptr, RKL_ERR_INVALID_ARG, "grid too large");
+    if (g.bc != RKL_PERIODIC && g.bc != RKL_DIRICHLET) return fail(nullptr, RKL_ERR_INVALID_ARG, "bad bc");
+    if (g.dtype != RKL_F32 && g.dtype != RKL_F64) return fail(nullptr, RKL_ERR_INVALID_ARG, "bad dtype");
+    const rkl_phys& ph = *phys;
+    if (ph.kappa_model != RKL_KAPPA_CONST && ph.kappa_model != RKL_KAPPA_SPITZER)
+        return fail(nullptr, RKL_ERR_INVALID_ARG, "bad kappa_model");
+    if (!(ph.kappa_par0 > 0.0) || !std::isfinite(ph.kappa_par0) || !(ph.kappa_perp_ratio >= 0.0) ||
+        !std::isfinite(ph.kappa_perp_ratio))
+        return fail(nullptr, RKL_ERR_INVALID_ARG, "bad conductivity");
+    if (!(ph.cp > 0.0 && ph.cp <= 0.5)) return fail(nullptr, RKL_ERR_INVALID_ARG, "cp must be in (0, 1/2]");
+    if (ph.saturate && (!(ph.phi > 0.0) || !(ph.rho > 0.0)))
+        return fail(nullptr, RKL_ERR_INVALID_ARG, "saturation needs phi > 0 and rho > 0");
+
+    rkl_plan* p = new rkl_plan();
+    p->grid = g;
+    p->phys = ph;
+    p->stream = static_cast<cudaStream_t>(cuda_stream);
+    p->esize = g.dtype == RKL_F64 ? 8 : 4;
+    p->ncell = ncell;
+    p->cfg = LaunchCfg{g.dtype, g.ndim, ph.kappa_model == RKL_KAPPA_SPITZER, ph.saturate != 0};
+    auto fill = [&](auto& kg, auto& kp) {
+        using R = std::remove_reference_t<decltype(kg.bcv)>;
+        for (int d = 0; d < 3; ++d) {
+            kg.n[d] = (int)g.n[d];
+            kg.inv_dx[d] = d < g.ndim ? (R)(1.0 / g.dx[d]) : R(0);
+            kg.inv_4dx[d] = d < g.ndim ? (R)(0.25 / g.dx[d]) : R(0);
+        }
+        kg.ndim = g.ndim;
+        kg.bc = g.bc;
+        kg.bcv = (R)g.bc_value;
+        kg.plane = g.n[0] * g.n[1];
+        kg.ncell = ncell;
+        kp.kappa0 = (R)ph.kappa_par0;
+        kp.kperp = (R)ph.kappa_perp_ratio;
+        kp.q0 = (R)(5.0 * ph.phi * ph.rho);
+        kp.upwind = ph.sat_upwind ? 1 : 0;
+    };
+    fill(p->gf, p->pf);
+    fill(p->gd, p->pd);
+    p->fast = g.dtype == RKL_F32 && fast_stage_supported(p->cfg, p->gf);
+
+    rkl_plan* P = p;
+    auto bail = [&](cudaError_t e, const char* where) {
+        std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+        rkl_plan_destroy(P);
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? RKL_ERR_NOMEM : RKL_ERR_CUDA, m);
+    };
+    cudaError_t e;
+    if ((e = cudaGetDevice(&p->device)) != cudaSuccess) return bail(e, "cudaGetDevice");
+    size_t bytes = (size_t)ncell * p->esize;
+    for (int k = 0; k < 3; ++k)
+        if ((e = cudaMalloc(&p->ybuf[k], bytes)) != cudaSuccess) return bail(e, "cudaMalloc(stage buffer)");
+    if ((e = cudaMalloc(&p->my0, bytes)) != cudaSuccess) return bail(e, "cudaMalloc(MY0)");
+    if ((e = cudaMalloc(&p->d_partials, sizeof(double) * 3 * kStatsBlocks)) != cudaSuccess)
+        return bail(e, "cudaMalloc(partials)");
+    if ((e = cudaMalloc(&p->d_scal, sizeof(double) * 4)) != cudaSuccess) return bail(e, "cudaMalloc(scalars)");
+    if ((e = cudaMallocHost(&p->h_scal, sizeof(double) * 4)) != cudaSuccess) return bail(e, "cudaMallocHost");
+    if ((e = cudaMalloc(&p->d_status, sizeof(unsigned))) != cudaSuccess) return bail(e, "cudaMalloc(status)");
+    if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned), p->stream)) != cudaSuccess)
+        return bail(e, "cudaMemset(status)");
+    size_t per = (size_t)(kMaxStages + 1) * 4 * p->esize;
+    if ((e = cudaMalloc(&p->d_coef, per)) != cudaSuccess) return bail(e, "cudaMalloc(coef)");
+    if ((e = cudaMallocHost(&p->h_coef, per * kCoefRing)) != cudaSuccess) return bail(e, "cudaMallocHost(coef)");
+    for (int k = 0; k < kCoefRing; ++k)
+        if ((e = cudaEventCreateWithFlags(&p->coef_ev[k], cudaEventDisableTiming)) != cudaSuccess)
+            return bail(e, "cudaEventCreate");
+    if ((e = cudaEventCreate(&p->ev_a)) != cudaSuccess) return bail(e, "cudaEventCreate");
+    if ((e = cudaEventCreate(&p->ev_b)) != cudaSuccess) return bail(e, "cudaEventCreate");
+    if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return bail(e, "cudaStreamSynchronize");
+    *out = p;
+    return RKL_OK;
+}
+
+rkl_status rkl_plan_destroy(rkl_plan* p)
+{
+    if (!p) return RKL_ERR_INVALID_ARG;
+    cudaStreamSynchronize(p->stream);
+    for (auto& g : p->cache)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (int k = 0; k < 3; ++k) cudaFree(p->ybuf[k]);
+    cudaFree(p->my0);
+    cudaFree(p->d_partials);
+    cudaFree(p->d_scal);
+    if (p->h_scal) cudaFreeHost(p->h_scal);
+    cudaFree(p->d_status);
+    cudaFree(p->d_coef);
+    if (p->h_coef) cudaFreeHost(p->h_coef);
+    for (int k = 0; k < kCoefRing; ++k)
+        if (p->coef_ev[k]) cudaEventDestroy(p->coef_ev[k]);
+    if (p->ev_a) cudaEventDestroy(p->ev_a);
+    if (p->ev_b) cudaEventDestroy(p->ev_b);
+    cudaFree(p->host_T);
+    cudaFree(p->host_b);
+    delete p;
+    return RKL_OK;
+}
+
+rkl_status rkl_dt_expl(rkl_plan* p, const void* T, double* dt_out)
+{
+    if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
+    if (!T || !dt_out) return fail(p, RKL_ERR_INVALID_ARG, "null argument");
+    DeviceGuard dg(p->device);
+    double Tmax = 1.0;
+    if (p->phys.kappa_model == RKL_KAPPA_SPITZER) {
+        rkl_status st = stats(p, T);
+        if (st != RKL_OK) return st;
+        Tmax = p->h_scal[0];
+        if (!(p->h_scal[1] > 0.0) || !std::isfinite(Tmax))
+            return fail(p, RKL_ERR_NONPOSITIVE_T, "T must be finite and > 0 under Spitzer kappa");
+    }
+    *dt_out = dt_expl_from_max(p, Tmax);
+    return RKL_OK;
+}
+
+rkl_status rkl_flux(rkl_plan* p, const void* T, const void* b, void* Fx, void* Fy, void* Fz)
+{
+    if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
+    void* F[3] = {Fx, Fy, Fz};
+    if (!T || !b) return fail(p, RKL_ERR_INVALID_ARG, "null argument");
+    for (int d = 0; d < p->grid.ndim; ++d)
+        if (!F[d]) return fail(p, RKL_ERR_INVALID_ARG, "missing face array");
+    DeviceGuard dg(p->device);
+    const void* grid = p->cfg.dtype == RKL_F32 ? (const void*)&p->gf : (const void*)&p->gd;
+    const void* phys = p->cfg.dtype == RKL_F32 ? (const void*)&p->pf : (const void*)&p->pd;
+    cudaError_t e = launch_flux_generic(p->cfg, grid, phys, T, b, F, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "flux launch");
+    return RKL_OK;
+}
+
+rkl_status rkl_apply_M(rkl_plan* p, const void* T, const void* b, void* MT)
+{
+    if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
+    if (!T || !b || !MT) return fail(p, RKL_ERR_INVALID_ARG, "null argument");
+    if (MT == T) return fail(p, RKL_ERR_INVALID_ARG, "MT must not alias T");
+    DeviceGuard dg(p->device);
+    StageIO io{};
+    io.Yjm1 = T;
+    io.Y0 = T;
+    io.Yj = MT;
+    io.b = b;
+    io.mode = 0;
+    return launch_stage(p, io, 0, 0, 0, 0);
+}
+
+rkl_status rkl_stage(rkl_plan* p, int j, int s, double dt, const void* b, const void* Y0, void* MY0,
+                     const void* Yjm1, const void* Yjm2, void* Yj)
+{
+    if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
+    if (s < 1 || s > kMaxStages || j < 1 || j > s) return fail(p, RKL_ERR_INVALID_ARG, "need 1 <= j <= s <= 4096");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(p, RKL_ERR_INVALID_ARG, "dt must be finite and > 0");
+    if (!b || !Y0 || !Yj) return fail(p, RKL_ERR_INVALID_ARG, "null argument");
+    if (j >= 2 && (!MY0 || !Yjm1 || !Yjm2)) return fail(p, RKL_ERR_INVALID_ARG, "stage j >= 2 needs MY0, Yjm1, Yjm2");
+    if (j == 1 && s >= 2 && !MY0) return fail(p, RKL_ERR_INVALID_ARG, "stage 1 needs MY0");
+    if (j >= 2 && (Yj == Yjm1 || Yj == Yjm2 || Yj == MY0)) return fail(p, RKL_ERR_INVALID_ARG, "Yj aliases an input");
+    if (j == 1 && Yj == MY0) return fail(p, RKL_ERR_INVALID_ARG, "Yj aliases MY0");
+    DeviceGuard dg(p->device);
+    StageIO io{};
+    io.b = b;
+    io.Y0 = Y0;
+    io.MY0 = MY0;
+    io.Yjm1 = Yjm1;
+    io.Yjm2 = Yjm2;
+    io.Yj = Yj;
+    io.j = j;
+    if (s == 1) {
+        io.mode = 1;
+        io.MY0 = nullptr;
+        return launch_stage(p, io, 0, 0, dt, 0);
+    }
+    std::vector<double> mu(s + 1), nu(s + 1), mut(s + 1), gt(s + 1);
+    host_coeffs(s, mu.data(), nu.data(), mut.data(), gt.data());
+    io.mode = j == 1 ? 1 : 2;
+    return launch_stage(p, io, mu[j], nu[j], mut[j] * dt, gt[j] * dt);
+}
+
+rkl_status rkl_super_step(rkl_plan* p, double dt, void* T, const void* b, int* s_used, double* eb, double* ea)
+{
+    if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(p, RKL_ERR_INVALID_ARG, "dt must be finite and > 0");
+    if (!T || !b) return fail(p, RKL_ERR_INVALID_ARG, "null argument");
+    if (!aligned16(T) || !aligned16(b)) return fail(p, RKL_ERR_INVALID_ARG, "T and b must be 16-byte aligned");
+    DeviceGuard dg(p->device);
+    rkl_status st = collect_timing(p);
+    if (st != RKL_OK) return st;
+    double Tmax = 1.0;
+    bool need_stats = p->phys.kappa_model == RKL_KAPPA_SPITZER || eb != nullptr;
+    if (need_stats) {
+        st = stats(p, T);
+        if (st != RKL_OK) return st;
+        st = status_from_word(p, (unsigned)p->h_scal[3]);
+        if (st != RKL_OK) return st;
+        Tmax = p->h_scal[0];
+        if (!std::isfinite(p->h_scal[0]) || !std::isfinite(p->h_scal[1]))
+            return fail(p, RKL_ERR_NONFINITE, "T holds NaN or Inf");
+        if (p->phys.kappa_model == RKL_KAPPA_SPITZER && !(p->h_scal[1] > 0.0))
+            return fail(p, RKL_ERR_NONPOSITIVE_T, "T must be > 0 under Spitzer kappa");
+        if (eb) *eb = p->h_scal[2] * cell_volume(p->grid);
+    }
+    double dte = dt_expl_from_max(p, Tmax);
+    int s = 0;
+    if (rkl_num_stages(dt / dte, &s) != RKL_OK) return fail(p, RKL_ERR_INVALID_ARG, "dt/dt_expl needs more than 4096 stages");
+    if (s_used) *s_used = s;
+    return run_super_step(p, dt, s, T, b, nullptr, ea);
+}
+
+rkl_status rkl_super_step_s(rkl_plan* p, double dt, int s, void* T, const void* b, double* eb, double* ea)
+{
+    if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(p, RKL_ERR_INVALID_ARG, "dt must be finite and > 0");
+    if (s < 2 || s > kMaxStages) return fail(p, RKL_ERR_INVALID_ARG, "need 2 <= s <= 4096");
+    if (!T || !b) return fail(p, RKL_ERR_INVALID_ARG, "null argument");
+    if (!aligned16(T) || !aligned16(b)) return fail(p, RKL_ERR_INVALID_ARG, "T and b must be 16-byte aligned");
+    DeviceGuard dg(p->device);
+    rkl_status st = collect_timing(p);
+    if (st != RKL_OK) return st;
+    if (eb) {
+        st = stats(p, T);
+        if (st != RKL_OK) return st;
+        *eb = p->h_scal[2] * cell_volume(p->grid);
+        st = status_from_word(p, (unsigned)p->h_scal[3]);
+        if (st != RKL_OK) return st;
+    }
+    return run_super_step(p, dt, s, T, b, nullptr, ea);
+}
+
+rkl_status rkl_energy(rkl_plan* p, const void* T, double* E_out)
+{
+    if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
+    if (!T || !E_out) return fail(p, RKL_ERR_INVALID_ARG, "null argument");
+    DeviceGuard dg(p->device);
+    // leaves the device status word untouched
+    rkl_status st = stats(p, T, false);
+    if (st != RKL_OK) return st;
+    *E_out = p->h_scal[2] * cell_volume(p->grid);
+    return RKL_OK;
+}
+
+rkl_status rkl_plan_check(rkl_plan* p)
+{
+    if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
+    DeviceGuard dg(p->device);
+    unsigned w = 0;
+    RKL_CK(p, cudaMemcpyAsync(&w, p->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
+    RKL_CK(p, cudaMemsetAsync(p->d_status, 0, sizeof(unsigned), p->stream));
+    RKL_CK(p, cudaStreamSynchronize(p->stream));
+    return status_from_word(p, w);
+}
+
+rkl_status rkl_plan_set_timing(rkl_plan* p, int on)
+{
+    if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
+    DeviceGuard dg(p->device);
+    rkl_status st = collect_timing(p);
+    if (st != RKL_OK) return st;
+    p->timing = on ? 1 : 0;
+    p->timing_ms = 0.0;
+    p->timing_launches = 0;
+    return RKL_OK;
+}
+
+rkl_status rkl_plan_timing(rkl_plan* p, double* ms_total, int64_t* launches)
+{
+    if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
+    if (!ms_total || !launches) return fail(p, RKL_ERR_INVALID_ARG, "null argument");
+    DeviceGuard dg(p->device);
+    rkl_status st = collect_timing(p);
+    if (st != RKL_OK) return st;
+    *ms_total = p->timing_ms;
+    *launches = p->timing_launches;
+    return RKL_OK;
+}
+
+rkl_status rkl_run_host(rkl_plan* p, double dt, int n_super, void* T_host, const void* b_host, int* s_last)
+{
+    if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
+    if (!T_host || !b_host || n_super < 0) return fail(p, RKL_ERR_INVALID_ARG, "bad argument");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(p, RKL_ERR_INVALID_ARG, "dt must be finite and > 0");
+    DeviceGuard dg(p->device);
+    size_t bytes = (size_t)p->ncell * p->esize;
+    if (!p->host_T) RKL_CK(p, cudaMalloc(&p->host_T, bytes));
+    if (!p->host_b) RKL_CK(p, cudaMalloc(&p->host_b, bytes * p->grid.ndim));
+    RKL_CK(p, cudaMemcpyAsync(p->host_T, T_host, bytes, cudaMemcpyHostToDevice, p->stream));
+    RKL_CK(p, cudaMemcpyAsync(p->host_b, b_host, bytes * p->grid.ndim, cudaMemcpyHostToDevice, p->stream));
+    int s = 0;
+    for (int k = 0; k < n_super; ++k) {
+        rkl_status st = rkl_super_step(p, dt, p->host_T, p->host_b, &s, nullptr, nullptr);
+        if (st != RKL_OK) return st;
+    }
+    RKL_CK(p, cudaMemcpyAsync(T_host, p->host_T, bytes, cudaMemcpyDeviceToHost, p->stream));
+    RKL_CK(p, cudaStreamSynchronize(p->stream));
+    if (s_last) *s_last = s;
+    return rkl_plan_check(p);
+}
+
+}  // extern "C"

@@ -1,0 +1,323 @@
+// Generic RKL2 conduction kernels: one thread per cell, any dtype (float /
+// double), 1-3 active axes, periodic or Dirichlet boundaries.  These serve
+// the FP64 and low-dimensional configurations and every case the tiled FP32
+// kernel does not cover; each cell evaluates the fluxes on all of its faces
+// straight from global memory (L1/L2 absorb the neighbour re-reads).
+#include "rkl_launch.h"
+
+namespace rkl {
+namespace {
+
+template <typename R>
+struct Field {
+    const R* T;
+    const R* b;
+    KGrid<R> g;
+
+    // T at a cell that may lie one cell outside the grid on active axes.
+    __device__ __forceinline__ R t(int i, int j, int k) const
+    {
+        if (g.bc == 1) {
+            if (i < 0 || i >= g.n[0] || j < 0 || j >= g.n[1] || k < 0 || k >= g.n[2]) return g.bcv;
+        } else {
+            i = wrap(i, g.n[0]);
+            j = wrap(j, g.n[1]);
+            k = wrap(k, g.n[2]);
+        }
+        return T[((int64_t)k * g.n[1] + j) * g.n[0] + i];
+    }
+    // Component e of b; ghosts copy the nearest interior cell (Dirichlet).
+    __device__ __forceinline__ R bc(int e, int i, int j, int k) const
+    {
+        if (g.bc == 1) {
+            i = clampi(i, g.n[0]);
+            j = clampi(j, g.n[1]);
+            k = clampi(k, g.n[2]);
+        } else {
+            i = wrap(i, g.n[0]);
+            j = wrap(j, g.n[1]);
+            k = wrap(k, g.n[2]);
+        }
+        return b[(int64_t)e * g.ncell + ((int64_t)k * g.n[1] + j) * g.n[0] + i];
+    }
+};
+
+// Flux component d on the face between P = (i,j,k) and P + e_d.
+template <typename R, int NDIM, bool SPITZER, bool SAT>
+__device__ __forceinline__ R face(const Field<R>& f, const KPhys<R>& p, int d, int i, int j, int k)
+{
+    int P[3] = {i, j, k};
+    int Q[3] = {i, j, k};
+    Q[d] += 1;
+    R TL = f.t(P[0], P[1], P[2]);
+    R TR = f.t(Q[0], Q[1], Q[2]);
+    R gn = (TR - TL) * f.g.inv_dx[d];
+    R gt[2] = {R(0), R(0)};
+    R bt[2] = {R(0), R(0)};
+    int m = 0;
+#pragma unroll
+    for (int e = 0; e < NDIM; ++e) {
+        if (e == d) continue;
+        int Pp[3] = {P[0], P[1], P[2]}, Pm[3] = {P[0], P[1], P[2]};
+        int Qp[3] = {Q[0], Q[1], Q[2]}, Qm[3] = {Q[0], Q[1], Q[2]};
+        Pp[e] += 1; Qp[e] += 1; Pm[e] -= 1; Qm[e] -= 1;
+        gt[m] = (f.t(Pp[0], Pp[1], Pp[2]) + f.t(Qp[0], Qp[1], Qp[2])
+               - f.t(Pm[0], Pm[1], Pm[2]) - f.t(Qm[0], Qm[1], Qm[2])) * f.g.inv_4dx[e];
+        bt[m] = R(0.5) * (f.bc(e, P[0], P[1], P[2]) + f.bc(e, Q[0], Q[1], Q[2]));
+        ++m;
+    }
+    R bn = R(0.5) * (f.bc(d, P[0], P[1], P[2]) + f.bc(d, Q[0], Q[1], Q[2]));
+    return face_flux<R, SPITZER, SAT>(TL, TR, gn, gt[0], gt[1], bn, bt[0], bt[1], p);
+}
+
+template <typename R>
+struct StageArgs {
+    const R* Y0;
+    R* MY0;
+    const R* Yjm1;
+    const R* Yjm2;
+    R* Yj;
+    const R* coef_tab;
+    int j;
+    int mode;
+};
+
+template <typename R, int NDIM, bool SPITZER, bool SAT>
+__global__ void __launch_bounds__(256) stage_generic_kernel(KGrid<R> g, KPhys<R> p, StageArgs<R> a,
+                                                            const R* __restrict__ b, KCoef<R> cf,
+                                                            unsigned* status)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.ncell) return;
+    int i = (int)(c % g.n[0]);
+    int64_t r = c / g.n[0];
+    int j = (int)(r % g.n[1]);
+    int k = (int)(r / g.n[1]);
+
+    // the field whose M is taken: Y0 for stage 1 / Euler, Yjm1 otherwise
+    Field<R> f{a.mode == 2 || a.mode == 0 ? a.Yjm1 : a.Y0, b, g};
+    R div = R(0);
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        int lo[3] = {i, j, k};
+        lo[d] -= 1;
+        R Fhi = face<R, NDIM, SPITZER, SAT>(f, p, d, i, j, k);
+        R Flo = face<R, NDIM, SPITZER, SAT>(f, p, d, lo[0], lo[1], lo[2]);
+        div += (Fhi - Flo) * g.inv_dx[d];
+    }
+    R M = -div;
+    if (a.mode == 0) {
+        a.Yj[c] = M;
+        return;
+    }
+    if (a.coef_tab) {
+        const R* t = a.coef_tab + 4 * a.j;
+        cf.mu = t[0]; cf.nu = t[1]; cf.mt = t[2]; cf.gt = t[3];
+    }
+    R y0 = a.Y0[c];
+    R y;
+    if (a.mode == 1) {
+        if (a.MY0) a.MY0[c] = M;
+        y = y0 + cf.mt * M;
+    } else {
+        R inc = cf.mu * (a.Yjm1[c] - y0) + cf.nu * (a.Yjm2[c] - y0) + cf.mt * M + cf.gt * a.MY0[c];
+        y = y0 + inc;
+    }
+    check_value<R, SPITZER>(y, status);
+    a.Yj[c] = y;
+}
+
+template <typename R, int NDIM, bool SPITZER, bool SAT>
+__global__ void __launch_bounds__(256) flux_generic_kernel(KGrid<R> g, KPhys<R> p, const R* __restrict__ T,
+                                                           const R* __restrict__ b, R* Fx, R* Fy, R* Fz)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.ncell) return;
+    int i = (int)(c % g.n[0]);
+    int64_t r = c / g.n[0];
+    int j = (int)(r % g.n[1]);
+    int k = (int)(r / g.n[1]);
+    Field<R> f{T, b, g};
+    R* F[3] = {Fx, Fy, Fz};
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) F[d][c] = face<R, NDIM, SPITZER, SAT>(f, p, d, i, j, k);
+}
+
+template <typename R, int NDIM, bool SPITZER, bool SAT>
+cudaError_t stage_impl(const void* grid, const void* phys, const StageIO& io, const void* coef,
+                       unsigned* status, cudaStream_t st)
+{
+    const KGrid<R>& g = *static_cast<const KGrid<R>*>(grid);
+    const KPhys<R>& p = *static_cast<const KPhys<R>*>(phys);
+    StageArgs<R> a{static_cast<const R*>(io.Y0), static_cast<R*>(io.MY0),
+                   static_cast<const R*>(io.Yjm1), static_cast<const R*>(io.Yjm2),
+                   static_cast<R*>(io.Yj), static_cast<const R*>(io.coef_tab), io.j, io.mode};
+    KCoef<R> cf = coef ? *static_cast<const KCoef<R>*>(coef) : KCoef<R>{R(0), R(0), R(0), R(0)};
+    int64_t blocks = (g.ncell + 255) / 256;
+    stage_generic_kernel<R, NDIM, SPITZER, SAT><<<(unsigned)blocks, 256, 0, st>>>(
+        g, p, a, static_cast<const R*>(io.b), cf, status);
+    return cudaGetLastError();
+}
+
+template <typename R, int NDIM, bool SPITZER, bool SAT>
+cudaError_t flux_impl(const void* grid, const void* phys, const void* T, const void* b, void* F[3],
+                      cudaStream_t st)
+{
+    const KGrid<R>& g = *static_cast<const KGrid<R>*>(grid);
+    const KPhys<R>& p = *static_cast<const KPhys<R>*>(phys);
+    int64_t blocks = (g.ncell + 255) / 256;
+    flux_generic_kernel<R, NDIM, SPITZER, SAT><<<(unsigned)blocks, 256, 0, st>>>(
+        g, p, static_cast<const R*>(T), static_cast<const R*>(b), static_cast<R*>(F[0]),
+        static_cast<R*>(F[1]), static_cast<R*>(F[2]));
+    return cudaGetLastError();
+}
+
+template <typename R, int NDIM>
+cudaError_t stage_dispatch_phys(const LaunchCfg& c, const void* grid, const void* phys,
+                                const StageIO& io, const void* coef, unsigned* status, cudaStream_t st)
+{
+    if (c.spitzer) {
+        if (c.saturate) return stage_impl<R, NDIM, true, true>(grid, phys, io, coef, status, st);
+        return stage_impl<R, NDIM, true, false>(grid, phys, io, coef, status, st);
+    }
+    if (c.saturate) return stage_impl<R, NDIM, false, true>(grid, phys, io, coef, status, st);
+    return stage_impl<R, NDIM, false, false>(grid, phys, io, coef, status, st);
+}
+
+template <typename R>
+cudaError_t stage_dispatch_ndim(const LaunchCfg& c, const void* grid, const void* phys,
+                                const StageIO& io, const void* coef, unsigned* status, cudaStream_t st)
+{
+    switch (c.ndim) {
+        case 1: return stage_dispatch_phys<R, 1>(c, grid, phys, io, coef, status, st);
+        case 2: return stage_dispatch_phys<R, 2>(c, grid, phys, io, coef, status, st);
+        case 3: return stage_dispatch_phys<R, 3>(c, grid, phys, io, coef, status, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename R, int NDIM>
+cudaError_t flux_dispatch_phys(const LaunchCfg& c, const void* grid, const void* phys, const void* T,
+                               const void* b, void* F[3], cudaStream_t st)
+{
+    if (c.spitzer) {
+        if (c.saturate) return flux_impl<R, NDIM, true, true>(grid, phys, T, b, F, st);
+        return flux_impl<R, NDIM, true, false>(grid, phys, T, b, F, st);
+    }
+    if (c.saturate) return flux_impl<R, NDIM, false, true>(grid, phys, T, b, F, st);
+    return flux_impl<R, NDIM, false, false>(grid, phys, T, b, F, st);
+}
+
+template <typename R>
+cudaError_t flux_dispatch_ndim(const LaunchCfg& c, const void* grid, const void* phys, const void* T,
+                               const void* b, void* F[3], cudaStream_t st)
+{
+    switch (c.ndim) {
+        case 1: return flux_dispatch_phys<R, 1>(c, grid, phys, T, b, F, st);
+        case 2: return flux_dispatch_phys<R, 2>(c, grid, phys, T, b, F, st);
+        case 3: return flux_dispatch_phys<R, 3>(c, grid, phys, T, b, F, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 statistics (max, min, sum) in a fixed reduction order.
+
+template <typename R>
+__device__ __forceinline__ void acc(double v, double& mx, double& mn, double& sm)
+{
+    // NaN propagates into max and min so that callers can detect it
+    mx = (v > mx || v != v) ? v : mx;
+    mn = (v < mn || v != v) ? v : mn;
+    sm += v;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) stats_kernel(const R* __restrict__ T, int64_t n, double* partials)
+{
+    double mx = -INFINITY, mn = INFINITY, sm = 0.0;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride)
+        acc<R>((double)T[c], mx, mn, sm);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double omx = __shfl_xor_sync(0xffffffffu, mx, o);
+        double omn = __shfl_xor_sync(0xffffffffu, mn, o);
+        mx = (omx > mx || omx != omx) ? omx : mx;
+        mn = (omn < mn || omn != omn) ? omn : mn;
+        sm += __shfl_xor_sync(0xffffffffu, sm, o);
+    }
+    __shared__ double s[3][8];
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { s[0][w] = mx; s[1][w] = mn; s[2][w] = sm; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < 8; ++q) {
+            mx = (s[0][q] > mx || s[0][q] != s[0][q]) ? s[0][q] : mx;
+            mn = (s[1][q] < mn || s[1][q] != s[1][q]) ? s[1][q] : mn;
+            sm += s[2][q];
+        }
+        partials[3 * blockIdx.x + 0] = mx;
+        partials[3 * blockIdx.x + 1] = mn;
+        partials[3 * blockIdx.x + 2] = sm;
+    }
+}
+
+__global__ void __launch_bounds__(32) stats_final_kernel(const double* partials, int nblk, double* out,
+                                                         unsigned* status)
+{
+    double mx = -INFINITY, mn = INFINITY, sm = 0.0;
+    for (int q = threadIdx.x; q < nblk; q += 32) {
+        double a = partials[3 * q], b = partials[3 * q + 1];
+        mx = (a > mx || a != a) ? a : mx;
+        mn = (b < mn || b != b) ? b : mn;
+        sm += partials[3 * q + 2];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double omx = __shfl_xor_sync(0xffffffffu, mx, o);
+        double omn = __shfl_xor_sync(0xffffffffu, mn, o);
+        mx = (omx > mx || omx != omx) ? omx : mx;
+        mn = (omn < mn || omn != omn) ? omn : mn;
+        sm += __shfl_xor_sync(0xffffffffu, sm, o);
+    }
+    if (threadIdx.x == 0) {
+        out[0] = mx;
+        out[1] = mn;
+        out[2] = sm;
+        unsigned st = status ? *status : 0u;
+        out[3] = (double)st;
+        if (status) *status = 0u;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_stage_generic(const LaunchCfg& c, const void* grid, const void* phys,
+                                 const StageIO& io, const void* coef, unsigned* status, cudaStream_t st)
+{
+    if (c.dtype == 1) return stage_dispatch_ndim<double>(c, grid, phys, io, coef, status, st);
+    return stage_dispatch_ndim<float>(c, grid, phys, io, coef, status, st);
+}
+
+cudaError_t launch_flux_generic(const LaunchCfg& c, const void* grid, const void* phys, const void* T,
+                                const void* b, void* F[3], cudaStream_t st)
+{
+    if (c.dtype == 1) return flux_dispatch_ndim<double>(c, grid, phys, T, b, F, st);
+    return flux_dispatch_ndim<float>(c, grid, phys, T, b, F, st);
+}
+
+cudaError_t launch_stats(int dtype, const void* T, int64_t n, double* partials, double* out,
+                         unsigned* status, cudaStream_t st)
+{
+    if (dtype == 1)
+        stats_kernel<double><<<kStatsBlocks, 256, 0, st>>>(static_cast<const double*>(T), n, partials);
+    else
+        stats_kernel<float><<<kStatsBlocks, 256, 0, st>>>(static_cast<const float*>(T), n, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    stats_final_kernel<<<1, 32, 0, st>>>(partials, kStatsBlocks, out, status);
+    return cudaGetLastError();
+}
+
+}  // namespace rkl

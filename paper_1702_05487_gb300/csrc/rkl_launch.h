@@ -1,0 +1,53 @@
+// Host-side launchers of the RKL2 kernels (internal to the library).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rkl_device.cuh"
+
+namespace rkl {
+
+// Pointers of one stage launch.  mode: 0 -> out = M(in); 1 -> stage 1 /
+// forward Euler (Yj = Y0 + mt M(Y0), MY0 written if non-null); 2 -> stage j.
+struct StageIO {
+    const void* Y0;
+    void* MY0;
+    const void* Yjm1;
+    const void* Yjm2;
+    void* Yj;
+    const void* b;
+    const void* coef_tab;   // if non-null: coefficients at coef_tab[4 j .. 4 j + 3]
+    int j;
+    int mode;
+};
+
+struct LaunchCfg {
+    int dtype;              // 0 float, 1 double
+    int ndim;
+    int spitzer;
+    int saturate;
+};
+
+// Generic kernels: one thread per cell, any dtype / ndim / boundary.
+cudaError_t launch_stage_generic(const LaunchCfg& c, const void* grid, const void* phys,
+                                 const StageIO& io, const void* coef, unsigned* status,
+                                 cudaStream_t st);
+cudaError_t launch_flux_generic(const LaunchCfg& c, const void* grid, const void* phys,
+                                const void* T, const void* b, void* F[3], cudaStream_t st);
+
+// Tiled FP32 3D stage kernel (shared-memory halo planes, z-march).
+// Returns cudaErrorNotSupported if the configuration is not covered.
+bool fast_stage_supported(const LaunchCfg& c, const KGrid<float>& g);
+cudaError_t launch_stage_fast(const LaunchCfg& c, const KGrid<float>& g, const KPhys<float>& p,
+                              const StageIO& io, const KCoef<float>& coef, unsigned* status,
+                              cudaStream_t st);
+
+// FP64 statistics of a grid array: max, min and sum (fixed-order, deterministic).
+// partials must hold 3 * kStatsBlocks doubles; out receives {max, min, sum}
+// followed by the status word (as a double), which is then cleared.
+constexpr int kStatsBlocks = 1216;   // 8 x 152 SMs
+cudaError_t launch_stats(int dtype, const void* T, int64_t n, double* partials, double* out,
+                         unsigned* status, cudaStream_t st);
+
+}  // namespace rkl

@@ -1,0 +1,224 @@
+"""GPU path against the FP64 oracle, element by element, through the C ABI.
+
+Sizes span several tiles of the tiled kernel with ragged tails; the FP32
+tolerances are derived in gpu_util.  Inputs are the seeded workload fields,
+rounded to the kernel dtype and handed to both sides."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from gpu_util import (F32_FLUX_TOL, F32_STATE_MAX, F32_STATE_REL_L2, F64_TOL, host, norm_max,
+                      rel_l2, rounded, torch_dev)
+from oracle import Problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rk():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1702_05487_gb300 as rk
+    rk.load()
+    return rk
+
+
+def _cases():
+    # (name, shape, params, dtype)
+    spitz = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
+    return [
+        ("3d_spitzer_perp", (35, 37, 40), spitz, "f32"),
+        ("3d_const_aniso", (17, 70, 33), dict(kappa_par0=0.02), "f32"),
+        ("3d_saturated", (24, 33, 66), dict(kappa_model="spitzer", kappa_par0=0.01, saturate=True,
+                                            phi=0.3), "f32"),
+        ("3d_saturated_upwind", (20, 18, 35), dict(kappa_model="spitzer", kappa_par0=0.01,
+                                                   saturate=True, phi=0.05, sat_upwind=True), "f32"),
+        ("3d_dirichlet", (19, 21, 34), dict(spitz, bc="dirichlet", bc_value=0.9), "f32"),
+        ("3d_f64", (13, 15, 17), spitz, "f64"),
+        ("2d_f64_dirichlet", (41, 29), dict(kappa_par0=0.05, bc="dirichlet", bc_value=1.0), "f64"),
+        ("2d_f32", (45, 67), spitz, "f32"),
+        ("1d_f32", (300,), dict(kappa_par0=0.3, kappa_perp_ratio=1.0), "f32"),
+    ]
+
+
+def _fields(shape, seed=11):
+    """Tangled-field T and b on any grid shape (2D/1D take slices)."""
+    nd = len(shape)
+    full = tuple(shape) + (1,) * (3 - nd) if nd < 3 else shape
+    if nd == 3:
+        nz, ny, nx = shape
+        T, b = workloads.tangled_box(nx, ny, nz, seed)
+    elif nd == 2:
+        ny, nx = shape
+        T, b = workloads.tangled_box(nx, ny, 4, seed)
+        T, b = T[0], b[:2, 0]
+        b = b / np.sqrt((b ** 2).sum(0))
+    else:
+        T, b = workloads.tangled_box(shape[0], 4, 4, seed)
+        T, b = T[0, 0], np.ones((1, shape[0]))
+    return T, b
+
+
+def _setup(rk, name, shape, params, dtype):
+    T, b = _fields(shape)
+    gkeys = {"dx", "bc", "bc_value"}
+    P = Problem(shape, **params)
+    plan = rk.Plan(shape, dtype, params=params)
+    Td, bd = torch_dev(T, dtype), torch_dev(b, dtype)
+    return P, plan, rounded(T, dtype), rounded(b, dtype), Td, bd
+
+
+@pytest.mark.parametrize("case", _cases(), ids=[c[0] for c in _cases()])
+def test_flux_and_M(rk, orc, case):
+    import torch
+    name, shape, params, dtype = case
+    P, plan, T, b, Td, bd = _setup(rk, *case)
+    nd = len(shape)
+    F = [torch.empty_like(Td) for _ in range(nd)]
+    plan.flux(Td, bd, *F)
+    M = torch.empty_like(Td)
+    plan.apply_M(Td, bd, M)
+    torch.cuda.synchronize()
+    Fref = orc.flux(P, T, b)
+    Mref = orc.apply_M(P, T, b)
+    tol = F64_TOL if dtype == "f64" else F32_FLUX_TOL
+    for d in range(nd):
+        assert norm_max(host(F[d]), Fref[d]) < tol, (name, d)
+    assert norm_max(host(M), Mref) < tol, name
+    if params.get("bc", "periodic") == "periodic":
+        # one flux per face: M sums to zero up to rounding
+        assert abs(float(host(M).sum())) <= 1e-5 * float(np.abs(host(M)).sum())
+
+
+@pytest.mark.parametrize("case", _cases(), ids=[c[0] for c in _cases()])
+def test_stages_one_by_one(rk, orc, case):
+    """rkl_stage for j = 1, 2, 3 against the oracle's stages from the same inputs."""
+    import torch
+    name, shape, params, dtype = case
+    P, plan, T, b, Td, bd = _setup(rk, *case)
+    s = 7
+    dt = 10 * orc.dt_expl(P, T)
+    MY0 = torch.empty_like(Td)
+    Y1 = torch.empty_like(Td)
+    plan.stage(1, s, dt, bd, Td, MY0, None, None, Y1)
+    Y1r, MY0r = orc.stage(P, 1, s, dt, b, T, None, None, None)
+    torch.cuda.synchronize()
+    tol = F64_TOL if dtype == "f64" else F32_FLUX_TOL
+    assert norm_max(host(MY0), MY0r) < tol
+    assert norm_max(host(Y1), Y1r) < (F64_TOL if dtype == "f64" else F32_STATE_MAX)
+    # stage 2 and 3 from oracle-side inputs rounded to the kernel dtype
+    Y1in = rounded(Y1r, dtype)
+    MY0in = rounded(MY0r, dtype)
+    Y2 = torch.empty_like(Td)
+    plan.stage(2, s, dt, bd, Td, torch_dev(MY0in, dtype), torch_dev(Y1in, dtype), Td, Y2)
+    Y2r, _ = orc.stage(P, 2, s, dt, b, T, MY0in, Y1in, T)
+    Y3 = torch.empty_like(Td)
+    Y2in = rounded(Y2r, dtype)
+    plan.stage(3, s, dt, bd, Td, torch_dev(MY0in, dtype), torch_dev(Y2in, dtype), torch_dev(Y1in, dtype), Y3)
+    Y3r, _ = orc.stage(P, 3, s, dt, b, T, MY0in, Y2in, Y1in)
+    torch.cuda.synchronize()
+    stol = F64_TOL if dtype == "f64" else F32_STATE_MAX
+    assert norm_max(host(Y2), Y2r) < stol
+    assert norm_max(host(Y3), Y3r) < stol
+
+
+@pytest.mark.parametrize("case", _cases(), ids=[c[0] for c in _cases()])
+def test_super_steps(rk, orc, case):
+    """Three super-steps with s chosen from dt / dt_expl; FP64 energies."""
+    name, shape, params, dtype = case
+    P, plan, T, b, Td, bd = _setup(rk, *case)
+    ratio = 100.0 if len(shape) == 3 else 50.0
+    dt = ratio * orc.dt_expl(P, T)
+    Tref = T.copy()
+    periodic = params.get("bc", "periodic") == "periodic"
+    for k in range(3):
+        s, eb, ea = plan.super_step(dt, Td, bd, energies=True)
+        Tref, sref = orc.super_step(P, Tref, b, dt)
+        assert s == sref
+        if periodic:
+            assert abs(ea - eb) <= (1e-12 if dtype == "f64" else 1e-6) * abs(eb)
+    Tg = host(Td)
+    if dtype == "f64":
+        assert norm_max(Tg, Tref) < F64_TOL
+    else:
+        assert rel_l2(Tg, Tref) < F32_STATE_REL_L2
+        assert norm_max(Tg, Tref) < F32_STATE_MAX
+    assert plan.check() == 0
+
+
+def test_dt_expl_and_energy(rk, orc):
+    shape = (24, 20, 36)
+    params = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
+    P, plan, T, b, Td, bd = _setup(rk, "x", shape, params, "f32")
+    assert plan.dt_expl(Td) == pytest.approx(orc.dt_expl(P, T), rel=1e-14)
+    assert plan.energy(Td) == pytest.approx(orc.energy(P, T), rel=1e-12)
+
+
+def test_super_step_s_and_timing(rk, orc):
+    import torch
+    shape = (32, 32, 32)
+    params = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
+    P, plan, T, b, Td, bd = _setup(rk, "x", shape, params, "f32")
+    dt = 30 * orc.dt_expl(P, T)
+    s = orc.num_stages(30)
+    plan.set_timing(True)
+    for _ in range(4):
+        plan.super_step_s(dt, s, Td, bd)
+    ms, n = plan.timing()
+    assert n == 4 * (s - 1) and ms > 0
+    plan.set_timing(False)
+    Tref = T
+    for _ in range(4):
+        Tref, _ = orc.super_step(P, Tref, b, dt, s)
+    assert rel_l2(host(Td), Tref) < F32_STATE_REL_L2
+
+
+def test_run_host_matches_device_path(rk, orc):
+    import torch
+    shape = (20, 24, 28)
+    params = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
+    P, plan, T, b, Td, bd = _setup(rk, "x", shape, params, "f32")
+    dt = 50 * orc.dt_expl(P, T)
+    Th = np.ascontiguousarray(T, dtype=np.float32)
+    bh = np.ascontiguousarray(b, dtype=np.float32)
+    s = plan.run_host(dt, 2, Th, bh)
+    for _ in range(2):
+        plan.super_step(dt, Td, bd)
+    torch.cuda.synchronize()
+    assert s == orc.num_stages(50)
+    assert np.array_equal(Th, host(Td).astype(np.float32))
+
+
+def test_invalid_arguments_and_device_status(rk):
+    import torch
+    shape = (16, 16, 16)
+    params = dict(kappa_model="spitzer", kappa_par0=0.01)
+    plan = rk.Plan(shape, "f32", params=params)
+    T = torch.ones(shape, device="cuda")
+    b = torch.zeros((3,) + shape, device="cuda")
+    b[0] = 1
+    with pytest.raises(rk.RklError) as ei:
+        plan.super_step(-1.0, T, b)
+    assert ei.value.status == 1
+    with pytest.raises(rk.RklError):
+        plan.stage(3, 2, 1e-3, b, T, T, T, T, T)
+    # a non-positive temperature under Spitzer kappa is reported, not hidden
+    T2 = T.clone()
+    T2[3, 4, 5] = -1.0
+    with pytest.raises(rk.RklError) as ei:
+        plan.super_step(1e-3, T2, b)
+    assert ei.value.status == rk._lib.RKL_ERR_NONPOSITIVE_T
+    T3 = T.clone()
+    T3[1, 2, 3] = float("nan")
+    with pytest.raises(rk.RklError) as ei:
+        plan.super_step(1e-3, T3, b)
+    assert ei.value.status == rk._lib.RKL_ERR_NONFINITE
+    # a stage that produces a bad value raises the device status word
+    Y = torch.empty_like(T)
+    M0 = torch.empty_like(T)
+    plan.stage(1, 2, 1e-3, b, T3, M0, None, None, Y)
+    assert plan.check() == rk._lib.RKL_ERR_NONFINITE
+    assert plan.check() == 0
