@@ -34,7 +34,8 @@ struct GraphEntry {
 struct rkl_plan {
     rkl_grid grid;
     rkl_phys phys;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;     // caller's stream: all work runs here
+    cudaStream_t cap = nullptr;        // private stream used only to capture graphs
     int device = 0;
     size_t esize = 4;
     int64_t ncell = 0;
@@ -139,19 +140,21 @@ rkl_status check_plan(rkl_plan* p)
     return RKL_OK;
 }
 
-// Launch one stage (or M) on the plan's stream.
-rkl_status launch_stage(rkl_plan* p, const StageIO& io, double mu, double nu, double mt, double gt)
+// Launch one stage (or M) on stream st (the plan's stream, or the capture
+// stream while a graph is being recorded).
+rkl_status launch_stage(rkl_plan* p, const StageIO& io, double mu, double nu, double mt, double gt,
+                        cudaStream_t st)
 {
     cudaError_t e;
     if (p->cfg.dtype == RKL_F32) {
         KCoef<float> cf{(float)mu, (float)nu, (float)mt, (float)gt};
         if (p->fast)
-            e = launch_stage_fast(p->cfg, p->gf, p->pf, io, cf, p->d_status, p->stream);
+            e = launch_stage_fast(p->cfg, p->gf, p->pf, io, cf, p->d_status, st);
         else
-            e = launch_stage_generic(p->cfg, &p->gf, &p->pf, io, &cf, p->d_status, p->stream);
+            e = launch_stage_generic(p->cfg, &p->gf, &p->pf, io, &cf, p->d_status, st);
     } else {
         KCoef<double> cf{mu, nu, mt, gt};
-        e = launch_stage_generic(p->cfg, &p->gd, &p->pd, io, &cf, p->d_status, p->stream);
+        e = launch_stage_generic(p->cfg, &p->gd, &p->pd, io, &cf, p->d_status, st);
     }
     if (e != cudaSuccess) return cuda_fail(p, e, "stage launch");
     return RKL_OK;
@@ -160,7 +163,7 @@ rkl_status launch_stage(rkl_plan* p, const StageIO& io, double mu, double nu, do
 // Enqueue the s stages of one super-step reading coefficients from the
 // plan's device table (stage j at d_coef[4 j]).  Y0 = T; the last stage
 // writes T (each cell reads its own Y0 before overwriting it).
-rkl_status enqueue_stages(rkl_plan* p, int s, void* T, const void* b, bool with_events)
+rkl_status enqueue_stages(rkl_plan* p, int s, void* T, const void* b, bool with_events, cudaStream_t cs)
 {
     StageIO io{};
     io.b = b;
@@ -170,9 +173,9 @@ rkl_status enqueue_stages(rkl_plan* p, int s, void* T, const void* b, bool with_
     io.j = 1;
     io.mode = 1;
     io.Yj = (s == 1) ? T : p->ybuf[0];
-    rkl_status st = launch_stage(p, io, 0, 0, 0, 0);
+    rkl_status st = launch_stage(p, io, 0, 0, 0, 0, cs);
     if (st != RKL_OK) return st;
-    if (with_events) RKL_CK(p, cudaEventRecordWithFlags(p->ev_a, p->stream, cudaEventRecordExternal));
+    if (with_events) RKL_CK(p, cudaEventRecordWithFlags(p->ev_a, cs, cudaEventRecordExternal));
     for (int j = 2; j <= s; ++j) {
         StageIO q{};
         q.b = b;
@@ -184,10 +187,10 @@ rkl_status enqueue_stages(rkl_plan* p, int s, void* T, const void* b, bool with_
         q.Yj = (j == s) ? T : p->ybuf[(j - 1) % 3];
         q.j = j;
         q.mode = 2;
-        st = launch_stage(p, q, 0, 0, 0, 0);
+        st = launch_stage(p, q, 0, 0, 0, 0, cs);
         if (st != RKL_OK) return st;
     }
-    if (with_events) RKL_CK(p, cudaEventRecordWithFlags(p->ev_b, p->stream, cudaEventRecordExternal));
+    if (with_events) RKL_CK(p, cudaEventRecordWithFlags(p->ev_b, cs, cudaEventRecordExternal));
     return RKL_OK;
 }
 
@@ -240,9 +243,9 @@ rkl_status get_graph(rkl_plan* p, int s, void* T, const void* b, cudaGraphExec_t
         victim->exec = nullptr;
     }
     cudaGraph_t graph = nullptr;
-    RKL_CK(p, cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
-    rkl_status st = enqueue_stages(p, s, T, b, p->timing != 0);
-    cudaError_t ce = cudaStreamEndCapture(p->stream, &graph);
+    RKL_CK(p, cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+    rkl_status st = enqueue_stages(p, s, T, b, p->timing != 0, p->cap);
+    cudaError_t ce = cudaStreamEndCapture(p->cap, &graph);
     if (st != RKL_OK) {
         if (graph) cudaGraphDestroy(graph);
         return st;
@@ -438,6 +441,8 @@ rkl_status rkl_plan_create(const rkl_grid* grid, const rkl_phys* phys, void* cud
     };
     cudaError_t e;
     if ((e = cudaGetDevice(&p->device)) != cudaSuccess) return bail(e, "cudaGetDevice");
+    if ((e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(e, "cudaStreamCreate");
     size_t bytes = (size_t)ncell * p->esize;
     for (int k = 0; k < 3; ++k)
         if ((e = cudaMalloc(&p->ybuf[k], bytes)) != cudaSuccess) return bail(e, "cudaMalloc(stage buffer)");
@@ -480,6 +485,7 @@ rkl_status rkl_plan_destroy(rkl_plan* p)
         if (p->coef_ev[k]) cudaEventDestroy(p->coef_ev[k]);
     if (p->ev_a) cudaEventDestroy(p->ev_a);
     if (p->ev_b) cudaEventDestroy(p->ev_b);
+    if (p->cap) cudaStreamDestroy(p->cap);
     cudaFree(p->host_T);
     cudaFree(p->host_b);
     delete p;
@@ -530,7 +536,7 @@ rkl_status rkl_apply_M(rkl_plan* p, const void* T, const void* b, void* MT)
     io.Yj = MT;
     io.b = b;
     io.mode = 0;
-    return launch_stage(p, io, 0, 0, 0, 0);
+    return launch_stage(p, io, 0, 0, 0, 0, p->stream);
 }
 
 rkl_status rkl_stage(rkl_plan* p, int j, int s, double dt, const void* b, const void* Y0, void* MY0,
@@ -556,12 +562,12 @@ rkl_status rkl_stage(rkl_plan* p, int j, int s, double dt, const void* b, const 
     if (s == 1) {
         io.mode = 1;
         io.MY0 = nullptr;
-        return launch_stage(p, io, 0, 0, dt, 0);
+        return launch_stage(p, io, 0, 0, dt, 0, p->stream);
     }
     std::vector<double> mu(s + 1), nu(s + 1), mut(s + 1), gt(s + 1);
     host_coeffs(s, mu.data(), nu.data(), mut.data(), gt.data());
     io.mode = j == 1 ? 1 : 2;
-    return launch_stage(p, io, mu[j], nu[j], mut[j] * dt, gt[j] * dt);
+    return launch_stage(p, io, mu[j], nu[j], mut[j] * dt, gt[j] * dt, p->stream);
 }
 
 rkl_status rkl_super_step(rkl_plan* p, double dt, void* T, const void* b, int* s_used, double* eb, double* ea)
