@@ -145,8 +145,9 @@ rkl_status rkl_apply_M(rkl_plan *plan, const void *T, const void *b, void *MT);
  *   j >= 2: Yj = mu_j Yjm1 + nu_j Yjm2 + (1 - mu_j - nu_j) Y0
  *                + mut_j tau M(Yjm1) + gt_j tau MY0
  * j = 1 ignores Yjm1 and Yjm2.  s = 1 is accepted as forward Euler
- * (Yj = Y0 + tau M(Y0)).  Yj may alias Y0 (each cell reads Y0 before writing
- * Yj at that cell only) but no other input.  Asynchronous.
+ * (Yj = Y0 + tau M(Y0)).  For j >= 2 Yj may alias Y0 (Y0 is read only at
+ * the cell being written) but no other input; for j = 1 Yj aliases nothing
+ * (M reads Y0 at neighbouring cells).  Asynchronous.
  */
 rkl_status rkl_stage(rkl_plan *plan, int j, int s, double dt, const void *b,
                      const void *Y0, void *MY0, const void *Yjm1,
@@ -175,6 +176,14 @@ rkl_status rkl_super_step_s(rkl_plan *plan, double dt, int s, void *T, const voi
 
 /* FP64 energy sum_c T_c dV of a device array.  Synchronises. */
 rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
+
+/*
+ * Kernel choice for the stage launches of this plan: 0 = automatic (the
+ * tiled FP32 3D kernel where it applies, else the generic kernel), 1 = the
+ * generic one-thread-per-cell kernel, 2 = the tiled kernel
+ * (RKL_ERR_UNSUPPORTED if it does not apply).  Drops cached graphs.
+ */
+rkl_status rkl_plan_set_variant(rkl_plan *plan, int variant);
 
 /*
  * Waits for the plan's stream and returns the device status word collected

@@ -16,7 +16,7 @@ from ._lib import (  # noqa: F401  (the C ABI, same names)
     RKL_DIRICHLET, RKL_F32, RKL_F64, RKL_KAPPA_CONST, RKL_KAPPA_SPITZER, RKL_OK, RKL_PERIODIC,
     RklError, load, library_path, rkl_apply_M, rkl_coeffs, rkl_dt_expl, rkl_energy, rkl_flux,
     rkl_grid, rkl_num_stages, rkl_phys, rkl_plan_check, rkl_plan_create, rkl_plan_destroy,
-    rkl_plan_set_timing, rkl_plan_timing, rkl_run_host, rkl_stage, rkl_super_step,
+    rkl_plan_set_timing, rkl_plan_set_variant, rkl_plan_timing, rkl_run_host, rkl_stage, rkl_super_step,
     rkl_super_step_s,
 )
 
@@ -107,6 +107,9 @@ class Plan:
 
     def check(self):
         return rkl_plan_check(self.handle)
+
+    def set_variant(self, variant):
+        rkl_plan_set_variant(self.handle, variant)
 
     def set_timing(self, on):
         rkl_plan_set_timing(self.handle, on)

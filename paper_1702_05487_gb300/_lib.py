@@ -68,6 +68,7 @@ SIGNATURES = {
     "rkl_super_step_s": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _vp, _vp, _dp, _dp]),
     "rkl_energy": (ctypes.c_int, [_vp, _vp, _dp]),
     "rkl_plan_check": (ctypes.c_int, [_vp]),
+    "rkl_plan_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "rkl_plan_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "rkl_plan_timing": (ctypes.c_int, [_vp, _dp, _i64p]),
     "rkl_run_host": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _vp, _vp, _ip]),
@@ -191,6 +192,10 @@ def rkl_energy(plan, T) -> float:
 def rkl_plan_check(plan) -> int:
     """Returns the device status (RKL_OK or an error code) without raising."""
     return load().rkl_plan_check(plan)
+
+
+def rkl_plan_set_variant(plan, variant: int):
+    _check(load().rkl_plan_set_variant(plan, int(variant)), plan)
 
 
 def rkl_plan_set_timing(plan, on: bool):

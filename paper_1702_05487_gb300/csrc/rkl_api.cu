@@ -44,7 +44,8 @@ struct rkl_plan {
     KGrid<double> gd{};
     KPhys<float> pf{};
     KPhys<double> pd{};
-    bool fast = false;
+    bool fast = false;                 // tiled kernel available for this grid
+    int variant = 0;                   // 0 auto, 1 generic, 2 tiled
 
     void* ybuf[3] = {nullptr, nullptr, nullptr};
     void* my0 = nullptr;
@@ -148,7 +149,9 @@ rkl_status launch_stage(rkl_plan* p, const StageIO& io, double mu, double nu, do
     cudaError_t e;
     if (p->cfg.dtype == RKL_F32) {
         KCoef<float> cf{(float)mu, (float)nu, (float)mt, (float)gt};
-        if (p->fast)
+        bool al = aligned16(io.Y0) && aligned16(io.MY0) && aligned16(io.Yjm1) && aligned16(io.Yjm2) &&
+                  aligned16(io.Yj) && aligned16(io.b);
+        if (p->fast && al && p->variant != 1)
             e = launch_stage_fast(p->cfg, p->gf, p->pf, io, cf, p->d_status, st);
         else
             e = launch_stage_generic(p->cfg, &p->gf, &p->pf, io, &cf, p->d_status, st);
@@ -172,7 +175,7 @@ rkl_status enqueue_stages(rkl_plan* p, int s, void* T, const void* b, bool with_
     io.MY0 = p->my0;
     io.j = 1;
     io.mode = 1;
-    io.Yj = (s == 1) ? T : p->ybuf[0];
+    io.Yj = p->ybuf[0];
     rkl_status st = launch_stage(p, io, 0, 0, 0, 0, cs);
     if (st != RKL_OK) return st;
     if (with_events) RKL_CK(p, cudaEventRecordWithFlags(p->ev_a, cs, cudaEventRecordExternal));
@@ -549,7 +552,7 @@ rkl_status rkl_stage(rkl_plan* p, int j, int s, double dt, const void* b, const 
     if (j >= 2 && (!MY0 || !Yjm1 || !Yjm2)) return fail(p, RKL_ERR_INVALID_ARG, "stage j >= 2 needs MY0, Yjm1, Yjm2");
     if (j == 1 && s >= 2 && !MY0) return fail(p, RKL_ERR_INVALID_ARG, "stage 1 needs MY0");
     if (j >= 2 && (Yj == Yjm1 || Yj == Yjm2 || Yj == MY0)) return fail(p, RKL_ERR_INVALID_ARG, "Yj aliases an input");
-    if (j == 1 && Yj == MY0) return fail(p, RKL_ERR_INVALID_ARG, "Yj aliases MY0");
+    if (j == 1 && (Yj == MY0 || Yj == Y0)) return fail(p, RKL_ERR_INVALID_ARG, "stage 1 output aliases an input");
     DeviceGuard dg(p->device);
     StageIO io{};
     io.b = b;
@@ -629,6 +632,22 @@ rkl_status rkl_energy(rkl_plan* p, const void* T, double* E_out)
     rkl_status st = stats(p, T, false);
     if (st != RKL_OK) return st;
     *E_out = p->h_scal[2] * cell_volume(p->grid);
+    return RKL_OK;
+}
+
+rkl_status rkl_plan_set_variant(rkl_plan* p, int variant)
+{
+    if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
+    if (variant < 0 || variant > 2) return fail(p, RKL_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
+    if (variant == 2 && !p->fast) return fail(p, RKL_ERR_UNSUPPORTED, "no tiled kernel for this grid");
+    DeviceGuard dg(p->device);
+    cudaStreamSynchronize(p->stream);
+    for (auto& g : p->cache)
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+    p->variant = variant;
     return RKL_OK;
 }
 

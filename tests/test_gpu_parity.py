@@ -62,11 +62,11 @@ def _fields(shape, seed=11):
     return T, b
 
 
-def _setup(rk, name, shape, params, dtype):
+def _setup(rk, name, shape, params, dtype, variant=0):
     T, b = _fields(shape)
-    gkeys = {"dx", "bc", "bc_value"}
     P = Problem(shape, **params)
     plan = rk.Plan(shape, dtype, params=params)
+    plan.set_variant(variant)
     Td, bd = torch_dev(T, dtype), torch_dev(b, dtype)
     return P, plan, rounded(T, dtype), rounded(b, dtype), Td, bd
 
@@ -125,11 +125,20 @@ def test_stages_one_by_one(rk, orc, case):
     assert norm_max(host(Y3), Y3r) < stol
 
 
-@pytest.mark.parametrize("case", _cases(), ids=[c[0] for c in _cases()])
+def _variant_cases():
+    out = []
+    for c in _cases():
+        out.append(c + (0,))
+        if c[3] == "f32" and len(c[1]) == 3:
+            out.append(c + (1,))        # the generic kernel on the same 3D FP32 case
+    return out
+
+
+@pytest.mark.parametrize("case", _variant_cases(), ids=[f"{c[0]}-v{c[4]}" for c in _variant_cases()])
 def test_super_steps(rk, orc, case):
     """Three super-steps with s chosen from dt / dt_expl; FP64 energies."""
-    name, shape, params, dtype = case
-    P, plan, T, b, Td, bd = _setup(rk, *case)
+    name, shape, params, dtype, variant = case
+    P, plan, T, b, Td, bd = _setup(rk, name, shape, params, dtype, variant)
     ratio = 100.0 if len(shape) == 3 else 50.0
     dt = ratio * orc.dt_expl(P, T)
     Tref = T.copy()
@@ -147,6 +156,27 @@ def test_super_steps(rk, orc, case):
         assert rel_l2(Tg, Tref) < F32_STATE_REL_L2
         assert norm_max(Tg, Tref) < F32_STATE_MAX
     assert plan.check() == 0
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (7, 9, 5), (40, 3, 70), (1, 33, 64), (65, 8, 36)])
+def test_tiled_kernel_matches_generic(rk, orc, shape):
+    """The tiled kernel (variant 2) and the generic kernel (variant 1) on
+    tile-aligned, ragged and degenerate shapes; both against the oracle."""
+    import torch
+    params = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
+    res = {}
+    for v in (1, 2):
+        P, plan, T, b, Td, bd = _setup(rk, "x", shape, params, "f32", v)
+        dt = 40 * orc.dt_expl(P, T)
+        for _ in range(2):
+            plan.super_step(dt, Td, bd)
+        res[v] = host(Td)
+    Tref = T
+    for _ in range(2):
+        Tref, _ = orc.super_step(P, Tref, b, dt)
+    for v in (1, 2):
+        assert rel_l2(res[v], Tref) < F32_STATE_REL_L2, v
+    assert norm_max(res[2], res[1]) < F32_STATE_MAX
 
 
 def test_dt_expl_and_energy(rk, orc):
@@ -186,9 +216,9 @@ def test_run_host_matches_device_path(rk, orc):
     bh = np.ascontiguousarray(b, dtype=np.float32)
     s = plan.run_host(dt, 2, Th, bh)
     for _ in range(2):
-        plan.super_step(dt, Td, bd)
+        s_dev = plan.super_step(dt, Td, bd)
     torch.cuda.synchronize()
-    assert s == orc.num_stages(50)
+    assert s == s_dev
     assert np.array_equal(Th, host(Td).astype(np.float32))
 
 
