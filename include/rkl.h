@@ -81,7 +81,8 @@ typedef struct rkl_plan rkl_plan;
 const char *rkl_status_string(rkl_status st);
 
 /* Last error message recorded on a plan ("" if none); NULL plan gives the
- * message of the last failed rkl_plan_create on this thread. */
+ * message of the last failed rkl_plan_create or
+ * rkl_dt_expl_energy_noalloc on this thread. */
 const char *rkl_last_error(const rkl_plan *plan);
 
 /*
@@ -213,6 +214,36 @@ rkl_status rkl_plan_timing(rkl_plan *plan, double *ms_total, int64_t *launches);
  */
 rkl_status rkl_run_host(rkl_plan *plan, double dt, int n_super, void *T_host,
                         const void *b_host, int *s_last);
+
+/*
+ * dt_expl and energy without allocating.  The paper has no counterpart to
+ * this entry point; it exists for callers that cannot allocate device
+ * memory where they need these numbers (creating a plan allocates, and
+ * cudaMalloc / cudaFree may synchronise the whole device): for example a
+ * host code that hands the library a fixed memory budget up front, or a
+ * time-step loop that must not stall on an allocation.
+ *
+ * Computes exactly what rkl_dt_expl (Eq. dt_exp) and rkl_energy (sum T dV,
+ * FP64) return for the device array T of the given grid, without a plan,
+ * on cuda_stream (void* cudaStream_t), and synchronises that stream.
+ * Writes *dt_out and *energy_out (host).
+ *
+ * Scratch: a fixed array inside the library (about 1.5 MB, held on every
+ * GPU that loads the library until the process exits), enough for grids of
+ * at most 2^27 = 134217728 cells; larger grids are rejected with
+ * RKL_ERR_INVALID_ARG before anything is launched.  No cudaMalloc, cudaFree
+ * or other allocating routine is called.  The first call on each device
+ * looks up the array's device address (once per device, with that device
+ * current), so make that first call before any stream capture.  All calls
+ * share the one array: calls whose GPU work overlaps (unordered streams)
+ * race on it.  Each call overwrites every scratch entry it reads.
+ * Errors: RKL_ERR_INVALID_ARG (bad grid/phys or too many cells),
+ * RKL_ERR_NONFINITE (T holds NaN/Inf), RKL_ERR_NONPOSITIVE_T (T <= 0 under
+ * Spitzer kappa), RKL_ERR_CUDA; the message is in rkl_last_error(NULL).
+ */
+rkl_status rkl_dt_expl_energy_noalloc(const rkl_grid *grid, const rkl_phys *phys,
+                                      const void *T, void *cuda_stream,
+                                      double *dt_out, double *energy_out);
 
 #ifdef __cplusplus
 }

@@ -72,6 +72,8 @@ SIGNATURES = {
     "rkl_plan_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "rkl_plan_timing": (ctypes.c_int, [_vp, _dp, _i64p]),
     "rkl_run_host": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _vp, _vp, _ip]),
+    "rkl_dt_expl_energy_noalloc": (ctypes.c_int, [ctypes.POINTER(rkl_grid), ctypes.POINTER(rkl_phys), _vp,
+                                                  _vp, _dp, _dp]),
 }
 
 _lib = None
@@ -213,3 +215,15 @@ def rkl_run_host(plan, dt, n_super, T_host, b_host) -> int:
     _check(load().rkl_run_host(plan, float(dt), int(n_super), _ptr(T_host), _ptr(b_host),
                                ctypes.byref(s)), plan)
     return s.value
+
+
+def rkl_dt_expl_energy_noalloc(grid: rkl_grid, phys: rkl_phys, T, stream=None):
+    """(dt_expl, energy) of a device array without a plan and without any
+    device allocation (scratch is a fixed array inside the library)."""
+    dt, e = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = load().rkl_dt_expl_energy_noalloc(ctypes.byref(grid), ctypes.byref(phys), _ptr(T),
+                                           _vp(int(stream) if stream else 0), ctypes.byref(dt),
+                                           ctypes.byref(e))
+    if st != RKL_OK:
+        raise RklError(st, load().rkl_last_error(None).decode())
+    return dt.value, e.value

@@ -342,6 +342,11 @@ rkl_status run_super_step(rkl_plan* p, double dt, int s, void* T, const void* b,
 
 }  // namespace
 
+namespace rkl {
+// Message for entry points without a plan (read back by rkl_last_error(NULL)).
+void set_unplanned_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace rkl
+
 extern "C" {
 
 const char* rkl_status_string(rkl_status st)
