@@ -180,11 +180,17 @@ rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
 
 /*
  * Kernel choice for the stage launches of this plan: 0 = automatic (the
- * tiled FP32 3D kernel where it applies, else the generic kernel), 1 = the
- * generic one-thread-per-cell kernel, 2 = the tiled kernel
- * (RKL_ERR_UNSUPPORTED if it does not apply).  Drops cached graphs.
+ * paired-cell kernel where it applies, else the tiled kernel, else the
+ * generic kernel), 1 = the generic one-thread-per-cell kernel, 2 = the
+ * tiled FP32 3D kernel (32 x 8 tiles, one cell per thread), 3 and 4 = the
+ * paired-cell FP32 3D kernel (64 x 8 tiles, two cells per thread in packed
+ * f32x2 arithmetic; needs nx % 4 == 0) built for 2 (variant 3) or 3
+ * (variant 4) resident CTAs per SM.  RKL_ERR_UNSUPPORTED if the kernel
+ * does not apply to the grid.  nzchunk = planes per CTA of the paired-cell
+ * kernel (<= 0: 32).  Drops cached graphs.  Results of all kernels agree
+ * within FP32 rounding.
  */
-rkl_status rkl_plan_set_variant(rkl_plan *plan, int variant);
+rkl_status rkl_plan_set_variant(rkl_plan *plan, int variant, int nzchunk);
 
 /*
  * Waits for the plan's stream and returns the device status word collected
@@ -214,6 +220,66 @@ rkl_status rkl_plan_timing(rkl_plan *plan, double *ms_total, int64_t *launches);
  */
 rkl_status rkl_run_host(rkl_plan *plan, double dt, int n_super, void *T_host,
                         const void *b_host, int *s_last);
+
+/* ------------------------------------------------------------------------
+ * Ensembles: many independent 3D FP32 problems advanced together, each with
+ * its own grid, conductivity, super-step and stage count (Eq. RKL-s per
+ * problem), sharing kappa_model and the saturation flag.  Problem p's cells
+ * live at [off[p], off[p+1]) of one caller-owned device array T_all and its
+ * three b planes at [3 off[p], 3 off[p+1]) of b_all (rkl_ensemble_layout
+ * gives off).  The ensemble owns the stage buffers (4 floats per cell).
+ */
+typedef struct rkl_ensemble rkl_ensemble;
+
+/* grids[p], phys[p] for p < nprob; every grid 3D, RKL_F32, nx % 4 == 0. */
+rkl_status rkl_ensemble_create(int nprob, const rkl_grid *grids, const rkl_phys *phys,
+                               void *cuda_stream, rkl_ensemble **out);
+rkl_status rkl_ensemble_destroy(rkl_ensemble *ens);
+const char *rkl_ensemble_last_error(const rkl_ensemble *ens);
+
+/* Writes nprob + 1 cell offsets (multiples of 4) into cell_offsets. */
+rkl_status rkl_ensemble_layout(const rkl_ensemble *ens, int64_t *cell_offsets);
+
+/*
+ * Schedule of rkl_ensemble_super_step: persistent = 1 runs every stage of
+ * every problem in one persistent launch (work items (problem, stage, tile)
+ * in stage-major order; a tile of stage j waits, with a bounded spin, until
+ * all tiles of stage j-1 of its problem are done); persistent = 0 launches
+ * one kernel per problem and stage.  nzchunk = planes per tile (<= 0: 32).
+ */
+rkl_status rkl_ensemble_set_schedule(rkl_ensemble *ens, int persistent, int nzchunk);
+
+/*
+ * One RKL2 super-step of every problem: dt[p] is problem p's super-step
+ * (host array); s_p = rkl_num_stages(dt[p] / dt_expl_p) with dt_expl_p from
+ * problem p's current T (FP64 per-problem maxima, one synchronisation).
+ * T_all is updated in place.  s_used (host, nprob ints) may be NULL.
+ * Errors detected by earlier super-steps (NaN, T <= 0, a timed-out wait)
+ * are returned here or by rkl_ensemble_check.
+ */
+rkl_status rkl_ensemble_super_step(rkl_ensemble *ens, const double *dt, void *T_all,
+                                   const void *b_all, int *s_used);
+
+/* Waits for the stream; returns and clears the device status word. */
+rkl_status rkl_ensemble_check(rkl_ensemble *ens);
+
+/*
+ * Autotuner: times one super-step of every candidate schedule (persistent
+ * with nzchunk 8, 16, 32; per-launch with 16, 32) on a scratch copy of
+ * T_all (T_all itself is not changed), keeps the fastest and returns it.
+ * Allocates and frees one T_all-sized scratch array.
+ */
+rkl_status rkl_ensemble_autotune(rkl_ensemble *ens, const double *dt, const void *T_all,
+                                 const void *b_all, int *persistent_out, int *nzchunk_out,
+                                 double *ms_out);
+
+/*
+ * Failure-detection self-test of the persistent kernel: launches it on a
+ * work list whose dependency can never be met, with a short spin limit;
+ * the kernel must give up, raise the timeout bit and return.  Writes
+ * RKL_ERR_TIMEOUT to *status_out when the bounded wait worked.
+ */
+rkl_status rkl_ensemble_selftest_timeout(rkl_ensemble *ens, int *status_out);
 
 /*
  * dt_expl and energy without allocating.  The paper has no counterpart to

@@ -108,8 +108,8 @@ class Plan:
     def check(self):
         return rkl_plan_check(self.handle)
 
-    def set_variant(self, variant):
-        rkl_plan_set_variant(self.handle, variant)
+    def set_variant(self, variant, nzchunk=0):
+        rkl_plan_set_variant(self.handle, variant, nzchunk)
 
     def set_timing(self, on):
         rkl_plan_set_timing(self.handle, on)
@@ -119,3 +119,57 @@ class Plan:
 
     def run_host(self, dt, n_super, T_host, b_host):
         return rkl_run_host(self.handle, dt, n_super, T_host, b_host)
+
+
+class Ensemble:
+    """One rkl_ensemble: ``problems`` is a list of (shape, params) pairs with
+    C-order 3D shapes and make_grid / make_phys keyword arguments."""
+
+    def __init__(self, problems, stream=None):
+        import torch
+        from . import _lib
+        gkeys = {"dx", "bc", "bc_value"}
+        grids, physs = [], []
+        for shape, prm in problems:
+            prm = dict(prm or {})
+            grids.append(make_grid(shape, dtype="f32", **{k: v for k, v in prm.items() if k in gkeys}))
+            physs.append(make_phys(**{k: v for k, v in prm.items() if k not in gkeys}))
+        self.shapes = [tuple(s) for s, _ in problems]
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._lib = _lib
+        self.handle = _lib.rkl_ensemble_create(grids, physs, self.stream.cuda_stream)
+        self.offsets = _lib.rkl_ensemble_layout(self.handle, len(problems))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            self._lib.rkl_ensemble_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def views(self, T_all, b_all):
+        """Per-problem views (T_p, b_p) into the concatenated arrays."""
+        out = []
+        for p, shape in enumerate(self.shapes):
+            o0, o1 = self.offsets[p], self.offsets[p + 1]
+            out.append((T_all[o0:o1].view(shape), b_all[3 * o0:3 * o1].view((3,) + shape)))
+        return out
+
+    def set_schedule(self, persistent, nzchunk=0):
+        self._lib.rkl_ensemble_set_schedule(self.handle, persistent, nzchunk)
+
+    def super_step(self, dt, T_all, b_all):
+        return self._lib.rkl_ensemble_super_step(self.handle, dt, T_all, b_all)
+
+    def check(self):
+        return self._lib.rkl_ensemble_check(self.handle)
+
+    def autotune(self, dt, T_all, b_all):
+        return self._lib.rkl_ensemble_autotune(self.handle, dt, T_all, b_all)
+
+    def selftest_timeout(self):
+        return self._lib.rkl_ensemble_selftest_timeout(self.handle)

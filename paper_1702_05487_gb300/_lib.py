@@ -68,12 +68,22 @@ SIGNATURES = {
     "rkl_super_step_s": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _vp, _vp, _dp, _dp]),
     "rkl_energy": (ctypes.c_int, [_vp, _vp, _dp]),
     "rkl_plan_check": (ctypes.c_int, [_vp]),
-    "rkl_plan_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "rkl_plan_set_variant": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "rkl_plan_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "rkl_plan_timing": (ctypes.c_int, [_vp, _dp, _i64p]),
     "rkl_run_host": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _vp, _vp, _ip]),
     "rkl_dt_expl_energy_noalloc": (ctypes.c_int, [ctypes.POINTER(rkl_grid), ctypes.POINTER(rkl_phys), _vp,
                                                   _vp, _dp, _dp]),
+    "rkl_ensemble_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(rkl_grid), ctypes.POINTER(rkl_phys), _vp,
+                                           ctypes.POINTER(_vp)]),
+    "rkl_ensemble_destroy": (ctypes.c_int, [_vp]),
+    "rkl_ensemble_last_error": (ctypes.c_char_p, [_vp]),
+    "rkl_ensemble_layout": (ctypes.c_int, [_vp, _i64p]),
+    "rkl_ensemble_set_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "rkl_ensemble_super_step": (ctypes.c_int, [_vp, _dp, _vp, _vp, _ip]),
+    "rkl_ensemble_check": (ctypes.c_int, [_vp]),
+    "rkl_ensemble_autotune": (ctypes.c_int, [_vp, _dp, _vp, _vp, _ip, _ip, _dp]),
+    "rkl_ensemble_selftest_timeout": (ctypes.c_int, [_vp, _ip]),
 }
 
 _lib = None
@@ -196,8 +206,8 @@ def rkl_plan_check(plan) -> int:
     return load().rkl_plan_check(plan)
 
 
-def rkl_plan_set_variant(plan, variant: int):
-    _check(load().rkl_plan_set_variant(plan, int(variant)), plan)
+def rkl_plan_set_variant(plan, variant: int, nzchunk: int = 0):
+    _check(load().rkl_plan_set_variant(plan, int(variant), int(nzchunk)), plan)
 
 
 def rkl_plan_set_timing(plan, on: bool):
@@ -227,3 +237,61 @@ def rkl_dt_expl_energy_noalloc(grid: rkl_grid, phys: rkl_phys, T, stream=None):
     if st != RKL_OK:
         raise RklError(st, load().rkl_last_error(None).decode())
     return dt.value, e.value
+
+
+def _echeck(st: int, ens):
+    if st != RKL_OK:
+        raise RklError(st, load().rkl_ensemble_last_error(ens).decode())
+
+
+def rkl_ensemble_create(grids, physs, stream=None):
+    n = len(grids)
+    ga = (rkl_grid * n)(*grids)
+    pa = (rkl_phys * n)(*physs)
+    h = _vp()
+    st = load().rkl_ensemble_create(n, ga, pa, _vp(int(stream) if stream else 0), ctypes.byref(h))
+    if st != RKL_OK:
+        raise RklError(st, load().rkl_last_error(None).decode())
+    return h
+
+
+def rkl_ensemble_destroy(ens):
+    _echeck(load().rkl_ensemble_destroy(ens), None)
+
+
+def rkl_ensemble_layout(ens, nprob: int):
+    out = (ctypes.c_int64 * (nprob + 1))()
+    _echeck(load().rkl_ensemble_layout(ens, out), ens)
+    return list(out)
+
+
+def rkl_ensemble_set_schedule(ens, persistent: bool, nzchunk: int = 0):
+    _echeck(load().rkl_ensemble_set_schedule(ens, int(bool(persistent)), int(nzchunk)), ens)
+
+
+def rkl_ensemble_super_step(ens, dt, T_all, b_all):
+    """dt: sequence of per-problem super-steps; returns the list of s used."""
+    n = len(dt)
+    dts = (ctypes.c_double * n)(*[float(v) for v in dt])
+    s = (ctypes.c_int * n)()
+    _echeck(load().rkl_ensemble_super_step(ens, dts, _ptr(T_all), _ptr(b_all), s), ens)
+    return list(s)
+
+
+def rkl_ensemble_check(ens) -> int:
+    return load().rkl_ensemble_check(ens)
+
+
+def rkl_ensemble_autotune(ens, dt, T_all, b_all):
+    n = len(dt)
+    dts = (ctypes.c_double * n)(*[float(v) for v in dt])
+    pers, nz, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    _echeck(load().rkl_ensemble_autotune(ens, dts, _ptr(T_all), _ptr(b_all), ctypes.byref(pers),
+                                         ctypes.byref(nz), ctypes.byref(ms)), ens)
+    return pers.value, nz.value, ms.value
+
+
+def rkl_ensemble_selftest_timeout(ens) -> int:
+    out = ctypes.c_int(0)
+    _echeck(load().rkl_ensemble_selftest_timeout(ens, ctypes.byref(out)), ens)
+    return out.value

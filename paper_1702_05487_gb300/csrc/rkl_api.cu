@@ -45,7 +45,9 @@ struct rkl_plan {
     KPhys<float> pf{};
     KPhys<double> pd{};
     bool fast = false;                 // tiled kernel available for this grid
-    int variant = 0;                   // 0 auto, 1 generic, 2 tiled
+    bool x2ok = false;                 // paired-cell kernel available for this grid
+    int variant = 0;                   // 0 auto, 1 generic, 2 tiled, 3/4 paired-cell (2/3 CTAs per SM)
+    int nzchunk = 32;                  // planes per CTA of the paired-cell kernel
 
     void* ybuf[3] = {nullptr, nullptr, nullptr};
     void* my0 = nullptr;
@@ -151,7 +153,10 @@ rkl_status launch_stage(rkl_plan* p, const StageIO& io, double mu, double nu, do
         KCoef<float> cf{(float)mu, (float)nu, (float)mt, (float)gt};
         bool al = aligned16(io.Y0) && aligned16(io.MY0) && aligned16(io.Yjm1) && aligned16(io.Yjm2) &&
                   aligned16(io.Yj) && aligned16(io.b);
-        if (p->fast && al && p->variant != 1)
+        if (p->x2ok && al && (p->variant == 0 || p->variant == 3 || p->variant == 4))
+            e = launch_stage_x2(p->cfg, p->gf, p->pf, io, cf, p->d_status, p->nzchunk,
+                                p->variant == 3 ? 2 : 3, st);
+        else if (p->fast && al && (p->variant == 0 || p->variant == 2))
             e = launch_stage_fast(p->cfg, p->gf, p->pf, io, cf, p->d_status, st);
         else
             e = launch_stage_generic(p->cfg, &p->gf, &p->pf, io, &cf, p->d_status, st);
@@ -440,6 +445,7 @@ rkl_status rkl_plan_create(const rkl_grid* grid, const rkl_phys* phys, void* cud
     fill(p->gf, p->pf);
     fill(p->gd, p->pd);
     p->fast = g.dtype == RKL_F32 && fast_stage_supported(p->cfg, p->gf);
+    p->x2ok = g.dtype == RKL_F32 && x2_stage_supported(p->cfg, p->gf);
 
     rkl_plan* P = p;
     auto bail = [&](cudaError_t e, const char* where) {
@@ -640,11 +646,15 @@ rkl_status rkl_energy(rkl_plan* p, const void* T, double* E_out)
     return RKL_OK;
 }
 
-rkl_status rkl_plan_set_variant(rkl_plan* p, int variant)
+rkl_status rkl_plan_set_variant(rkl_plan* p, int variant, int nzchunk)
 {
     if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
-    if (variant < 0 || variant > 2) return fail(p, RKL_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
+    if (variant < 0 || variant > 4) return fail(p, RKL_ERR_INVALID_ARG, "variant must be 0 to 4");
+    if (nzchunk > 4096) return fail(p, RKL_ERR_INVALID_ARG, "nzchunk must be <= 4096");
     if (variant == 2 && !p->fast) return fail(p, RKL_ERR_UNSUPPORTED, "no tiled kernel for this grid");
+    if ((variant == 3 || variant == 4) && !p->x2ok)
+        return fail(p, RKL_ERR_UNSUPPORTED, "no paired-cell kernel for this grid");
+    p->nzchunk = nzchunk > 0 ? nzchunk : 32;
     DeviceGuard dg(p->device);
     cudaStreamSynchronize(p->stream);
     for (auto& g : p->cache)

@@ -42,12 +42,28 @@ struct KCoef {
     R mu, nu, mt, gt;
 };
 
+// Square root and quotient of the flux formula.  FP64 uses the correctly
+// rounded operations; FP32 uses the hardware approximations of the PTX ISA
+// (sqrt.approx.f32 and div.full.f32, a few ulp), which keeps the stencil's
+// instruction count down and stays far inside the FP32 tolerance.
 template <typename R>
 __device__ __forceinline__ R dsqrt(R x);
 template <>
-__device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+__device__ __forceinline__ float dsqrt<float>(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 template <>
 __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
+
+template <typename R>
+__device__ __forceinline__ R ddiv(R a, R b);
+template <>
+__device__ __forceinline__ float ddiv<float>(float a, float b) { return __fdividef(a, b); }
+template <>
+__device__ __forceinline__ double ddiv<double>(double a, double b) { return a / b; }
 
 // Parallel conductivity at temperature T.
 template <typename R, bool SPITZER>
@@ -81,7 +97,7 @@ __device__ __forceinline__ R face_flux(R TL, R TR, R gn, R g1, R g2,
         R Fmag = dsqrt<R>(Fn * Fn + F1 * F1 + F2 * F2);
         R Tq = p.upwind ? (Fn >= R(0) ? TL : TR) : Tf;
         R q = p.q0 * Tq * dsqrt<R>(Tq);
-        Fn = q / (q + Fmag) * Fn;
+        Fn = ddiv<R>(q, q + Fmag) * Fn;
     }
     return Fn;
 }

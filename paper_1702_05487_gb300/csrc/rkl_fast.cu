@@ -69,106 +69,175 @@ struct Smem {
     float Fy[2][TY + 1][TX];
 };
 
-// Stage the bundle of plane kk (T and b with halo; Y arrays if withY).
-template <int MODE>
-__device__ __forceinline__ void load_bundle(Smem& sm, const KGrid<float>& g, const FastArgs& a, int kk,
-                                            int tslot, int bslot, int yslot, bool withY, int i0, int j0,
-                                            bool fastx)
+// Plane bookkeeping of one bundle: element offsets of the T plane and of
+// the b plane (they differ only for Dirichlet ghost planes, where T is the
+// ghost value and b copies the nearest interior plane).
+struct PlaneOff {
+    int64_t t, b;
+    bool zghost;
+};
+
+__device__ __forceinline__ PlaneOff plane_offsets(const KGrid<float>& g, int kk)
 {
-    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const int tid = threadIdx.x;
-    const bool dir = g.bc == 1;
-    bool zghost = false;
+    const int nz = g.n[2];
+    PlaneOff o{0, 0, false};
     int kz = kk, kzb = kk;
     if (kk < 0 || kk >= nz) {
-        if (dir) {
-            zghost = true;
-            kzb = kk < 0 ? 0 : nz - 1;
+        if (g.bc == 1) {
+            o.zghost = true;
+            kz = kzb = kk < 0 ? 0 : nz - 1;
         } else {
             kz = kzb = pmod(kk, nz);
         }
     }
-    const int64_t plane_off = (int64_t)kz * ny * nx;
-    const int64_t bplane_off = (int64_t)kzb * ny * nx;
-    float* dT = sm.T[tslot];
-    if (fastx) {
-        // 4 arrays x (10 rows x 8 chunks of 16 B + 20 halo columns of 4 B)
-        for (int t = tid; t < 4 * 100; t += NTHREADS) {
-            int arr = t / 100, r = t % 100;
-            float* dst = arr == 0 ? dT : sm.B[bslot][arr - 1];
-            const float* base = arr == 0 ? a.Tin : a.b + (int64_t)(arr - 1) * g.ncell;
-            int iy, ix;
-            bool chunk = r < 80;
-            if (chunk) { iy = r / 8 - 1; ix = (r % 8) * 4; }
-            else { r -= 80; iy = r / 2 - 1; ix = (r & 1) ? TX : -1; }
-            int gy = j0 + iy;
-            bool yghost = false;
-            if (gy < 0 || gy >= ny) {
-                if (dir) { yghost = true; gy = gy < 0 ? 0 : ny - 1; }
-                else gy = pmod(gy, ny);
-            }
-            int gx = i0 + ix;
-            bool xghost = false;
-            if (gx < 0 || gx >= nx) {
-                if (dir) { xghost = true; gx = gx < 0 ? 0 : nx - 1; }
-                else gx = pmod(gx, nx);
-            }
-            float* d = dst + off(iy, ix);
-            if (arr == 0) {
-                if (zghost || yghost || xghost) {
-                    d[0] = g.bcv;
-                    if (chunk) { d[1] = g.bcv; d[2] = g.bcv; d[3] = g.bcv; }
-                    continue;
-                }
-                const float* s = base + plane_off + (int64_t)gy * nx + gx;
-                if (chunk) cp16(d, s); else cp4(d, s);
-            } else {
-                const float* s = base + bplane_off + (int64_t)gy * nx + gx;
-                if (chunk) cp16(d, s); else cp4(d, s);
-            }
-        }
-        if (withY && MODE == 2) {
-            for (int t = tid; t < 3 * 64; t += NTHREADS) {
-                int arr = t / 64, r = t % 64;
-                int iy = r / 8, ix = (r % 8) * 4;
-                const float* base = arr == 0 ? a.Y0 : (arr == 1 ? a.Yjm2 : a.MY0in);
-                const float* s = base + plane_off + (int64_t)(j0 + iy) * nx + i0 + ix;
-                cp16(&sm.Y[yslot][arr][iy * TX + ix], s);
-            }
-        }
+    o.t = (int64_t)kz * g.plane;
+    o.b = (int64_t)kzb * g.plane;
+    return o;
+}
+
+// Copy tasks of the full-tile path, fixed per thread for the whole z-march.
+// A bundle is 4 arrays (T, bx, by, bz) x (10 rows x 8 chunks of 16 B + 20
+// halo cells of 4 B) = 400 tasks, plus 3 x 64 chunks of Y0, Y_{j-2}, M(Y0).
+// Thread t owns T/b tasks t and t + 256 and Y task t (t < 192).
+enum : unsigned { TK_VALID = 1u, TK_CHUNK = 2u, TK_T = 4u, TK_GHOST = 8u, TK_BCAST = 16u };
+struct Task {
+    const float* src;   // element address in plane 0 (the bundle's plane offset is added)
+    unsigned dst;       // shared-memory byte address in slot 0
+    unsigned flags;
+};
+
+__device__ __forceinline__ Task make_tb_task(const Smem& sm, const KGrid<float>& g, const FastArgs& a, int t,
+                                             int i0, int j0)
+{
+    Task k{nullptr, 0u, 0u};
+    if (t >= 400) return k;
+    const int nx = g.n[0], ny = g.n[1];
+    const bool dir = g.bc == 1;
+    int arr = t / 100, r = t % 100;
+    int iy, ix;
+    bool chunk = r < 80;
+    if (chunk) { iy = r / 8 - 1; ix = (r % 8) * 4; }
+    else { r -= 80; iy = r / 2 - 1; ix = (r & 1) ? TX : -1; }
+    int gy = j0 + iy, gx = i0 + ix;
+    bool ghost = false;
+    if (gy < 0 || gy >= ny) {
+        if (dir) { ghost = true; gy = gy < 0 ? 0 : ny - 1; } else gy = pmod(gy, ny);
+    }
+    bool xghost = false;
+    if (gx < 0 || gx >= nx) {
+        if (dir) { ghost = xghost = true; gx = gx < 0 ? 0 : nx - 1; } else gx = pmod(gx, nx);
+    }
+    const int64_t row = (int64_t)gy * nx + gx;
+    k.flags = TK_VALID | (chunk ? TK_CHUNK : 0u);
+    if (arr == 0) {
+        k.flags |= TK_T | (ghost ? TK_GHOST : 0u);
+        k.src = a.Tin + row;
+        k.dst = smem_u32(&sm.T[0][off(iy, ix)]);
     } else {
-        // ragged tile: element by element with wrap / ghost per element
-        for (int t = tid; t < 4 * ROWS * (TX + 2); t += NTHREADS) {
-            int arr = t / (ROWS * (TX + 2)), r = t % (ROWS * (TX + 2));
-            int iy = r / (TX + 2) - 1, ix = r % (TX + 2) - 1;
-            float* dst = arr == 0 ? dT : sm.B[bslot][arr - 1];
-            const float* base = arr == 0 ? a.Tin : a.b + (int64_t)(arr - 1) * g.ncell;
-            int gy = j0 + iy, gx = i0 + ix;
-            bool ghost = zghost;
-            if (gy < 0 || gy >= ny) {
-                if (dir) { ghost = true; gy = gy < 0 ? 0 : ny - 1; } else gy = pmod(gy, ny);
-            }
-            if (gx < 0 || gx >= nx) {
-                if (dir) { ghost = true; gx = gx < 0 ? 0 : nx - 1; } else gx = pmod(gx, nx);
-            }
-            float* d = dst + off(iy, ix);
-            if (arr == 0) {
-                if (ghost) { *d = g.bcv; continue; }
-                cp4(d, base + plane_off + (int64_t)gy * nx + gx);
-            } else {
-                cp4(d, base + bplane_off + (int64_t)gy * nx + gx);
-            }
+        // Dirichlet: b past the x edge repeats the nearest interior cell
+        k.flags |= xghost ? TK_BCAST : 0u;
+        k.src = a.b + (int64_t)(arr - 1) * g.ncell + row;
+        k.dst = smem_u32(&sm.B[0][arr - 1][off(iy, ix)]);
+    }
+    return k;
+}
+
+template <int MODE>
+__device__ __forceinline__ Task make_y_task(const Smem& sm, const KGrid<float>& g, const FastArgs& a, int t,
+                                            int i0, int j0)
+{
+    Task k{nullptr, 0u, 0u};
+    if (MODE != 2 || t >= 192) return k;
+    int arr = t / 64, r = t % 64;
+    int iy = r / 8, ix = (r % 8) * 4;
+    // a 16-byte chunk lies wholly inside or wholly outside the grid (nx % 4 == 0)
+    if (j0 + iy >= g.n[1] || i0 + ix >= g.n[0]) return k;
+    const float* base = arr == 0 ? a.Y0 : (arr == 1 ? a.Yjm2 : a.MY0in);
+    k.src = base + (int64_t)(j0 + iy) * g.n[0] + i0 + ix;
+    k.dst = smem_u32(&sm.Y[0][arr][iy * TX + ix]);
+    k.flags = TK_VALID | TK_CHUNK;
+    return k;
+}
+
+__device__ __forceinline__ void st_shared(unsigned d, float v) { asm volatile("st.shared.f32 [%0], %1;\n" ::"r"(d), "f"(v)); }
+__device__ __forceinline__ void st_shared4(unsigned d, float v)
+{
+    asm volatile("st.shared.v4.f32 [%0], {%1, %1, %1, %1};\n" ::"r"(d), "f"(v));
+}
+__device__ __forceinline__ void cp16a(unsigned d, const void* s)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(s));
+}
+__device__ __forceinline__ void cp4a(unsigned d, const void* s)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(s));
+}
+
+__device__ __forceinline__ void issue_tb(const Task& k, const PlaneOff& po, unsigned tslot_bytes,
+                                         unsigned bslot_bytes, float bcv)
+{
+    if (!(k.flags & TK_VALID)) return;
+    const bool isT = k.flags & TK_T;
+    const unsigned d = k.dst + (isT ? tslot_bytes : bslot_bytes);
+    if (isT && (po.zghost || (k.flags & TK_GHOST))) {
+        if (k.flags & TK_CHUNK) st_shared4(d, bcv); else st_shared(d, bcv);
+        return;
+    }
+    const float* s = k.src + (isT ? po.t : po.b);
+    if (k.flags & TK_BCAST) {
+        const float v = __ldcg(s);
+        if (k.flags & TK_CHUNK) st_shared4(d, v); else st_shared(d, v);
+        return;
+    }
+    if (k.flags & TK_CHUNK) cp16a(d, s); else cp4a(d, s);
+}
+
+__device__ __forceinline__ void issue_y(const Task& k, int64_t poff, unsigned yslot_bytes)
+{
+    if (k.flags & TK_VALID) cp16a(k.dst + yslot_bytes, k.src + poff);
+}
+
+// Rows not 16-byte aligned (nx % 4 != 0):
+// stage the bundle of plane kk element by element with wrap / ghost per element.
+template <int MODE>
+__device__ __forceinline__ void load_bundle_ragged(Smem& sm, const KGrid<float>& g, const FastArgs& a, int kk,
+                                                   int tslot, int bslot, int yslot, bool withY, int i0, int j0)
+{
+    const int nx = g.n[0], ny = g.n[1];
+    const int tid = threadIdx.x;
+    const bool dir = g.bc == 1;
+    const PlaneOff po = plane_offsets(g, kk);
+    float* dT = sm.T[tslot];
+    for (int t = tid; t < 4 * ROWS * (TX + 2); t += NTHREADS) {
+        int arr = t / (ROWS * (TX + 2)), r = t % (ROWS * (TX + 2));
+        int iy = r / (TX + 2) - 1, ix = r % (TX + 2) - 1;
+        float* dst = arr == 0 ? dT : sm.B[bslot][arr - 1];
+        const float* base = arr == 0 ? a.Tin : a.b + (int64_t)(arr - 1) * g.ncell;
+        int gy = j0 + iy, gx = i0 + ix;
+        bool ghost = po.zghost;
+        if (gy < 0 || gy >= ny) {
+            if (dir) { ghost = true; gy = gy < 0 ? 0 : ny - 1; } else gy = pmod(gy, ny);
         }
-        if (withY && MODE == 2) {
-            for (int t = tid; t < 3 * NTHREADS; t += NTHREADS) {
-                int arr = t / NTHREADS, r = t % NTHREADS;
-                int iy = r / TX, ix = r % TX;
-                int gy = j0 + iy, gx = i0 + ix;
-                float* d = &sm.Y[yslot][arr][r];
-                if (gy >= ny || gx >= nx) { *d = 0.f; continue; }
-                const float* base = arr == 0 ? a.Y0 : (arr == 1 ? a.Yjm2 : a.MY0in);
-                cp4(d, base + plane_off + (int64_t)gy * nx + gx);
-            }
+        if (gx < 0 || gx >= nx) {
+            if (dir) { ghost = true; gx = gx < 0 ? 0 : nx - 1; } else gx = pmod(gx, nx);
+        }
+        float* d = dst + off(iy, ix);
+        if (arr == 0) {
+            if (ghost) { *d = g.bcv; continue; }
+            cp4(d, base + po.t + (int64_t)gy * nx + gx);
+        } else {
+            cp4(d, base + po.b + (int64_t)gy * nx + gx);
+        }
+    }
+    if (withY && MODE == 2) {
+        for (int t = tid; t < 3 * NTHREADS; t += NTHREADS) {
+            int arr = t / NTHREADS, r = t % NTHREADS;
+            int iy = r / TX, ix = r % TX;
+            int gy = j0 + iy, gx = i0 + ix;
+            float* d = &sm.Y[yslot][arr][r];
+            if (gy >= ny || gx >= nx) { *d = 0.f; continue; }
+            const float* base = arr == 0 ? a.Y0 : (arr == 1 ? a.Yjm2 : a.MY0in);
+            cp4(d, base + po.t + (int64_t)gy * nx + gx);
         }
     }
 }
@@ -261,7 +330,9 @@ stage_fast_kernel(KGrid<float> g, KPhys<float> p, FastArgs a, KCoef<float> cf, u
     const int z0 = blockIdx.z * NZC;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int nzc = min(NZC, nz - z0);
-    const bool fastx = (i0 + TX <= nx) && (j0 + TY <= ny) && ((nx & 3) == 0);
+    // 16-byte chunks need rows that start on a 16-byte boundary; partially
+    // filled tiles are fine (chunks past the edge wrap or hold ghosts whole)
+    const bool fastx = (nx & 3) == 0;
 
     if (MODE != 0 && a.coef_tab) {
         const float* t = a.coef_tab + 4 * a.j;
@@ -273,11 +344,30 @@ stage_fast_kernel(KGrid<float> g, KPhys<float> p, FastArgs a, KCoef<float> cf, u
     auto bslot = [](int q) { return (q + 1) % 3; };
     auto yslot = [](int q) { return (q + 3) % 3; };
 
-    load_bundle<MODE>(sm, g, a, z0 - 1, tslot(-1), bslot(-1), 0, false, i0, j0, fastx);
+    Task tk0{nullptr, 0u, 0u}, tk1{nullptr, 0u, 0u}, tky{nullptr, 0u, 0u};
+    if (fastx) {
+        tk0 = make_tb_task(sm, g, a, tid, i0, j0);
+        tk1 = make_tb_task(sm, g, a, tid + NTHREADS, i0, j0);
+        tky = make_y_task<MODE>(sm, g, a, tid, i0, j0);
+    }
+    auto load = [&](int q, bool withY) {
+        if (fastx) {
+            const PlaneOff po = plane_offsets(g, z0 + q);
+            const unsigned ts = (unsigned)(tslot(q) * PLANE * 4);
+            const unsigned bs = (unsigned)(bslot(q) * 3 * PLANE * 4);
+            issue_tb(tk0, po, ts, bs, g.bcv);
+            issue_tb(tk1, po, ts, bs, g.bcv);
+            if (withY) issue_y(tky, po.t, (unsigned)(yslot(q) * 3 * NTHREADS * 4));
+        } else {
+            load_bundle_ragged<MODE>(sm, g, a, z0 + q, tslot(q), bslot(q), yslot(q), withY, i0, j0);
+        }
+    };
+
+    load(-1, false);
     cp_commit();
-    load_bundle<MODE>(sm, g, a, z0, tslot(0), bslot(0), yslot(0), true, i0, j0, fastx);
+    load(0, true);
     cp_commit();
-    if (nzc >= 1) load_bundle<MODE>(sm, g, a, z0 + 1, tslot(1), bslot(1), yslot(1), nzc > 1, i0, j0, fastx);
+    load(1, nzc > 1);
     cp_commit();
     cp_wait<0>();
     __syncthreads();
@@ -294,9 +384,7 @@ stage_fast_kernel(KGrid<float> g, KPhys<float> p, FastArgs a, KCoef<float> cf, u
     const bool inside = (i0 + ix < nx) && (j0 + iy < ny);
     for (int q = 0; q < nzc; ++q) {
         // prefetch bundle q + 2 (T and b are needed up to q = nzc)
-        if (q + 2 <= nzc)
-            load_bundle<MODE>(sm, g, a, z0 + q + 2, tslot(q + 2), bslot(q + 2), yslot(q + 2), q + 2 < nzc,
-                              i0, j0, fastx);
+        if (q + 2 <= nzc) load(q + 2, q + 2 < nzc);
         cp_commit();
         cp_wait<1>();
         __syncthreads();

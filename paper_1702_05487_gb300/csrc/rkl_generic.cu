@@ -320,4 +320,81 @@ cudaError_t launch_stats(int dtype, const void* T, int64_t n, double* partials, 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Segmented FP64 statistics of the problems of an ensemble: block c folds
+// chunk c (cells [cstart[c], cstart[c] + clen[c]) of one problem), then one
+// warp per problem folds that problem's chunks pchunk[p] .. pchunk[p+1]-1.
+
+namespace {
+
+__global__ void __launch_bounds__(256) seg_stats_kernel(const float* __restrict__ T, const int64_t* cstart,
+                                                        const int* clen, double* partials)
+{
+    double mx = -INFINITY, mn = INFINITY, sm = 0.0;
+    const int64_t s0 = cstart[blockIdx.x];
+    const int len = clen[blockIdx.x];
+    for (int i = threadIdx.x; i < len; i += blockDim.x) acc<float>((double)T[s0 + i], mx, mn, sm);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double omx = __shfl_xor_sync(0xffffffffu, mx, o);
+        double omn = __shfl_xor_sync(0xffffffffu, mn, o);
+        mx = (omx > mx || omx != omx) ? omx : mx;
+        mn = (omn < mn || omn != omn) ? omn : mn;
+        sm += __shfl_xor_sync(0xffffffffu, sm, o);
+    }
+    __shared__ double s[3][8];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s[0][w] = mx; s[1][w] = mn; s[2][w] = sm; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < 8; ++q) {
+            mx = (s[0][q] > mx || s[0][q] != s[0][q]) ? s[0][q] : mx;
+            mn = (s[1][q] < mn || s[1][q] != s[1][q]) ? s[1][q] : mn;
+            sm += s[2][q];
+        }
+        partials[3 * blockIdx.x + 0] = mx;
+        partials[3 * blockIdx.x + 1] = mn;
+        partials[3 * blockIdx.x + 2] = sm;
+    }
+}
+
+__global__ void seg_stats_final_kernel(const double* partials, const int* pchunk, int nprob, double* out)
+{
+    const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int l = threadIdx.x & 31;
+    if (p >= nprob) return;
+    double mx = -INFINITY, mn = INFINITY, sm = 0.0;
+    for (int q = pchunk[p] + l; q < pchunk[p + 1]; q += 32) {
+        double a = partials[3 * q], b = partials[3 * q + 1];
+        mx = (a > mx || a != a) ? a : mx;
+        mn = (b < mn || b != b) ? b : mn;
+        sm += partials[3 * q + 2];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double omx = __shfl_xor_sync(0xffffffffu, mx, o);
+        double omn = __shfl_xor_sync(0xffffffffu, mn, o);
+        mx = (omx > mx || omx != omx) ? omx : mx;
+        mn = (omn < mn || omn != omn) ? omn : mn;
+        sm += __shfl_xor_sync(0xffffffffu, sm, o);
+    }
+    if (l == 0) {
+        out[3 * p + 0] = mx;
+        out[3 * p + 1] = mn;
+        out[3 * p + 2] = sm;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_stats_segmented(const float* T, const int64_t* cstart, const int* clen, int nchunk,
+                                   const int* pchunk, int nprob, double* partials, double* out, cudaStream_t st)
+{
+    seg_stats_kernel<<<nchunk, 256, 0, st>>>(T, cstart, clen, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    seg_stats_final_kernel<<<(nprob + 7) / 8, 256, 0, st>>>(partials, pchunk, nprob, out);
+    return cudaGetLastError();
+}
+
 }  // namespace rkl

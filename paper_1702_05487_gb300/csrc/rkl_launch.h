@@ -43,11 +43,25 @@ cudaError_t launch_stage_fast(const LaunchCfg& c, const KGrid<float>& g, const K
                               const StageIO& io, const KCoef<float>& coef, unsigned* status,
                               cudaStream_t st);
 
+// Paired-cell FP32 3D stage kernel (packed f32x2 arithmetic, 64 x 8 tiles,
+// nzchunk planes per CTA, occupancy 2 or 3 CTAs per SM).  Needs nx % 4 == 0
+// and 16-byte aligned arrays.
+bool x2_stage_supported(const LaunchCfg& c, const KGrid<float>& g);
+cudaError_t launch_stage_x2(const LaunchCfg& c, const KGrid<float>& g, const KPhys<float>& p, const StageIO& io,
+                            const KCoef<float>& coef, unsigned* status, int nzchunk, int occupancy,
+                            cudaStream_t st);
+
 // FP64 statistics of a grid array: max, min and sum (fixed-order, deterministic).
 // partials must hold 3 * kStatsBlocks doubles; out receives {max, min, sum}
 // followed by the status word (as a double), which is then cleared.
 constexpr int kStatsBlocks = 1216;   // 8 x 152 SMs
 cudaError_t launch_stats(int dtype, const void* T, int64_t n, double* partials, double* out,
                          unsigned* status, cudaStream_t st);
+
+// FP64 {max, min, sum} per problem of an ensemble (FP32 data), from a chunk
+// table: chunk c covers cells [cstart[c], cstart[c] + clen[c]); problem p
+// owns chunks pchunk[p] .. pchunk[p+1]-1.  out receives 3 doubles per problem.
+cudaError_t launch_stats_segmented(const float* T, const int64_t* cstart, const int* clen, int nchunk,
+                                   const int* pchunk, int nprob, double* partials, double* out, cudaStream_t st);
 
 }  // namespace rkl

@@ -1,0 +1,671 @@
+// Paired-cell FP32 3D stage kernel for the RKL2 conduction super-step.
+//
+// Same z-march and plane-bundle pipeline as the tiled kernel, but each
+// thread owns two neighbouring cells in x (columns 2l, 2l + 1 of a 64 x 8
+// tile) and evaluates their faces, divergence and recurrence with the packed
+// FP32 pair instructions of sm_100+ (add/sub/mul/fma .f32x2), so one
+// instruction serves both cells.  Shared-memory reads are 64-bit pairs.
+// The x-face below a pair comes from the lane to the left by a warp shuffle
+// (lane 0 from the tile's boundary faces), the y-face below from the row
+// below through shared memory, the z-face below from the previous plane.
+//
+// The per-tile body (tile_x2) is also the work item of the persistent
+// ensemble kernel (rkl_ensemble.cu).
+#include "rkl_launch.h"
+#include "rkl_x2.cuh"
+
+namespace rkl {
+namespace x2 {
+
+// --------------------------------------------------------------------------
+// packed FP32 pair arithmetic
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    unsigned long long r, x = *reinterpret_cast<unsigned long long*>(&a),
+                          y = *reinterpret_cast<unsigned long long*>(&b);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+    return *reinterpret_cast<float2*>(&r);
+}
+__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 sqrt2(float2 a) { return make_float2(dsqrt<float>(a.x), dsqrt<float>(a.y)); }
+
+// Normal flux on a pair of faces (the packed form of face_flux).
+template <bool SP, bool SAT>
+__device__ __forceinline__ float2 face2(float2 TL, float2 TR, float2 gn, float2 g1, float2 g2, float2 bn, float2 b1,
+                                        float2 b2, const KPhys<float>& p)
+{
+    const float2 Tf = mul2(bc2(0.5f), add2(TL, TR));
+    float2 nk;                                    // -kappa_par at the face
+    if (SP) nk = mul2(mul2(bc2(-p.kappa0), mul2(Tf, Tf)), sqrt2(Tf));
+    else nk = bc2(-p.kappa0);
+    const float2 nkp = mul2(bc2(p.kperp), nk);    // -kappa_perp
+    const float2 bdg = fma2(bn, gn, fma2(b1, g1, mul2(b2, g2)));
+    float2 Fn = fma2(mul2(nk, bn), bdg, mul2(nkp, gn));
+    if (SAT) {
+        const float2 F1 = fma2(mul2(nk, b1), bdg, mul2(nkp, g1));
+        const float2 F2 = fma2(mul2(nk, b2), bdg, mul2(nkp, g2));
+        const float2 F2s = fma2(Fn, Fn, fma2(F1, F1, mul2(F2, F2)));
+        const float2 Fmag = sqrt2(F2s);
+        float2 Tq = Tf;
+        if (p.upwind) {
+            Tq.x = Fn.x >= 0.f ? TL.x : TR.x;
+            Tq.y = Fn.y >= 0.f ? TL.y : TR.y;
+        }
+        const float2 q = mul2(mul2(bc2(p.q0), Tq), sqrt2(Tq));
+        const float2 den = add2(q, Fmag);
+        Fn = make_float2(ddiv<float>(q.x, den.x) * Fn.x, ddiv<float>(q.y, den.y) * Fn.y);
+    }
+    return Fn;
+}
+
+// --------------------------------------------------------------------------
+// shared memory and copies
+
+__device__ __forceinline__ int off(int r, int c) { return (r + 1) * SXS + c + 4; }
+
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp16(unsigned d, const void* s)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(s));
+}
+__device__ __forceinline__ void st4(unsigned d, float v)
+{
+    asm volatile("st.shared.v4.f32 [%0], {%1, %1, %1, %1};\n" ::"r"(d), "f"(v));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ int pmod(int v, int n)
+{
+    int r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+
+// Copy tasks fixed per thread for the whole tile: a bundle is T and b
+// (4 arrays x 10 rows x 18 chunks of 16 B, halo ring included) plus Y0,
+// Y_{j-2}, M(Y0) (3 arrays x 8 rows x 16 chunks).  Rows must start on a
+// 16-byte boundary (nx % 4 == 0); chunks past the grid edge wrap
+// (periodic), hold the ghost value (Dirichlet T) or are skipped (Y).
+enum : unsigned { TK_VALID = 1u, TK_T = 2u, TK_GHOST = 4u, TK_Y = 8u, TK_BCAST = 16u };
+struct Task {
+    const float* src;     // chunk address in plane 0
+    unsigned dst;         // smem byte address in slot 0
+    unsigned flags;
+};
+constexpr int kTB = 4 * ROWS * CPR;          // 720
+constexpr int kY = 3 * TY * (TX / 4);        // 384
+constexpr int kTasks = kTB + kY;             // 1104
+constexpr int kSlots = (kTasks + NTHREADS - 1) / NTHREADS;   // 5
+
+template <int MODE>
+__device__ __forceinline__ Task make_task(const Smem& sm, const KGrid<float>& g, const FastArgs& a, int t, int i0,
+                                          int j0)
+{
+    Task k{nullptr, 0u, 0u};
+    const int nx = g.n[0], ny = g.n[1];
+    if (t < kTB) {
+        const int arr = t / (ROWS * CPR), r = t % (ROWS * CPR);
+        const int row = r / CPR - 1, c = (r % CPR) * 4 - 4;
+        int gy = j0 + row, gx = i0 + c;
+        bool ghost = false;
+        if (gy < 0 || gy >= ny) {
+            if (g.bc == 1) { ghost = true; gy = gy < 0 ? 0 : ny - 1; } else gy = pmod(gy, ny);
+        }
+        bool xghost = false;
+        if (gx < 0 || gx >= nx) {
+            // Dirichlet: a chunk past the x edge is ghosts only; b there
+            // repeats the nearest interior cell (broadcast of one element)
+            if (g.bc == 1) { ghost = xghost = true; gx = gx < 0 ? 0 : nx - 1; } else gx = pmod(gx, nx);
+        }
+        const int64_t rowoff = (int64_t)gy * nx + gx;
+        k.flags = TK_VALID;
+        if (arr == 0) {
+            k.flags |= TK_T | (ghost ? TK_GHOST : 0u);
+            k.src = a.Tin + rowoff;
+            k.dst = smem_u32(&sm.T[0][off(row, c)]);
+        } else {
+            k.flags |= xghost ? TK_BCAST : 0u;
+            k.src = a.b + (int64_t)(arr - 1) * g.ncell + rowoff;
+            k.dst = smem_u32(&sm.B[0][arr - 1][off(row, c)]);
+        }
+        return k;
+    }
+    t -= kTB;
+    if (MODE != 2 || t >= kY) return k;
+    const int arr = t / (TY * (TX / 4)), r = t % (TY * (TX / 4));
+    const int row = r / (TX / 4), c = (r % (TX / 4)) * 4;
+    if (j0 + row >= ny || i0 + c >= nx) return k;
+    const float* base = arr == 0 ? a.Y0 : (arr == 1 ? a.Yjm2 : a.MY0in);
+    k.src = base + (int64_t)(j0 + row) * nx + i0 + c;
+    k.dst = smem_u32(&sm.Y[0][arr][row * TX + c]);
+    k.flags = TK_VALID | TK_Y;
+    return k;
+}
+
+struct PlaneOff {
+    int64_t t, b;
+    bool zghost;
+};
+
+__device__ __forceinline__ PlaneOff plane_offsets(const KGrid<float>& g, int kk)
+{
+    const int nz = g.n[2];
+    PlaneOff o{0, 0, false};
+    int kz = kk;
+    if (kk < 0 || kk >= nz) {
+        if (g.bc == 1) { o.zghost = true; kz = kk < 0 ? 0 : nz - 1; }
+        else kz = pmod(kk, nz);
+    }
+    o.t = o.b = (int64_t)kz * g.plane;
+    return o;
+}
+
+__device__ __forceinline__ void issue(const Task& k, const PlaneOff& po, unsigned ts, unsigned bs, unsigned ys,
+                                      bool withY, float bcv)
+{
+    const unsigned f = k.flags;
+    if (!(f & TK_VALID)) return;
+    if (f & TK_Y) {
+        if (withY) cp16(k.dst + ys, k.src + po.t);
+        return;
+    }
+    if (f & TK_T) {
+        if (po.zghost || (f & TK_GHOST)) st4(k.dst + ts, bcv);
+        else cp16(k.dst + ts, k.src + po.t);
+        return;
+    }
+    if (f & TK_BCAST) st4(k.dst + bs, __ldcg(k.src + po.b));
+    else cp16(k.dst + bs, k.src + po.b);
+}
+
+// --------------------------------------------------------------------------
+// per-plane quantities of a thread's cell pair
+
+// Quantities carried from one plane to the next (needed by the z-face and
+// the z-differences): T of the pair, of column 2l+2 and one row up, the
+// pair's centred x/y differences (unscaled) and b.
+struct QZ {
+    float2 To;        // T at columns (2l, 2l+1)
+    float Tr;         // T at column 2l+2
+    float2 TU;        // T one row up
+    float2 gxo, gyo;  // centred differences at the pair
+    float2 bo[3];     // b at the pair
+};
+
+// Quantities of the current plane needed only by its x- and y-faces
+// (read at the start of the plane's step, not carried).
+struct QXY {
+    float2 gyR;       // centred y-differences at (2l+1, 2l+2)
+    float2 gxU;       // centred x-differences one row up
+    float bR[3];      // b at column 2l+2
+    float2 bU[3];     // b one row up
+};
+
+__device__ __forceinline__ QZ read_qz(const Smem& sm, int ts, int bs, int c, int r)
+{
+    const float* T = sm.T[ts];
+    QZ q;
+    const float2 Tc = lds2(&T[off(r, c)]);
+    const float2 Tl = lds2(&T[off(r, c - 2)]);
+    const float2 Trr = lds2(&T[off(r, c + 2)]);
+    const float2 Tu = lds2(&T[off(r + 1, c)]);
+    const float2 Td = lds2(&T[off(r - 1, c)]);
+    q.To = Tc;
+    q.Tr = Trr.x;
+    q.TU = Tu;
+    q.gxo = sub2(make_float2(Tc.y, Trr.x), make_float2(Tl.y, Tc.x));
+    q.gyo = sub2(Tu, Td);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) q.bo[e] = lds2(&sm.B[bs][e][off(r, c)]);
+    return q;
+}
+
+__device__ __forceinline__ QXY read_qxy(const Smem& sm, int ts, int bs, int c, int r, const QZ& z)
+{
+    const float* T = sm.T[ts];
+    QXY q;
+    const float2 Td = lds2(&T[off(r - 1, c)]);
+    const float2 Tur = lds2(&T[off(r + 1, c + 2)]);
+    const float2 Tdr = lds2(&T[off(r - 1, c + 2)]);
+    const float2 Tul = lds2(&T[off(r + 1, c - 2)]);
+    q.gyR = sub2(make_float2(z.TU.y, Tur.x), make_float2(Td.y, Tdr.x));
+    q.gxU = sub2(make_float2(z.TU.y, Tur.x), make_float2(Tul.y, z.TU.x));
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const float* B = sm.B[bs][e];
+        q.bR[e] = B[off(r, c + 2)];
+        q.bU[e] = lds2(&B[off(r + 1, c)]);
+    }
+    return q;
+}
+
+// Boundary faces of the tile, straight from smem: the y-face pair between
+// row -1 and row 0 at columns (c, c+1), and the x-face between columns -1
+// and 0 at row r.
+template <bool SP, bool SAT>
+__device__ __forceinline__ float2 low_yface2(const Smem& sm, const KGrid<float>& g, const KPhys<float>& p, int tm,
+                                             int tc, int tp, int bs, int c)
+{
+    const float* T = sm.T[tc];
+    const float2 TL = lds2(&T[off(-1, c)]), TR = lds2(&T[off(0, c)]);
+    const float2 Ll = lds2(&T[off(-1, c - 2)]), Lr = lds2(&T[off(-1, c + 2)]);
+    const float2 Rl = lds2(&T[off(0, c - 2)]), Rr = lds2(&T[off(0, c + 2)]);
+    const float2 gxL = sub2(make_float2(TL.y, Lr.x), make_float2(Ll.y, TL.x));
+    const float2 gxR = sub2(make_float2(TR.y, Rr.x), make_float2(Rl.y, TR.x));
+    const float2 gzL = sub2(lds2(&sm.T[tp][off(-1, c)]), lds2(&sm.T[tm][off(-1, c)]));
+    const float2 gzR = sub2(lds2(&sm.T[tp][off(0, c)]), lds2(&sm.T[tm][off(0, c)]));
+    float2 b[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e)
+        b[e] = mul2(bc2(0.5f), add2(lds2(&sm.B[bs][e][off(-1, c)]), lds2(&sm.B[bs][e][off(0, c)])));
+    return face2<SP, SAT>(TL, TR, mul2(sub2(TR, TL), bc2(g.inv_dx[1])), mul2(add2(gxL, gxR), bc2(g.inv_4dx[0])),
+                          mul2(add2(gzL, gzR), bc2(g.inv_4dx[2])), b[1], b[0], b[2], p);
+}
+
+template <bool SP, bool SAT>
+__device__ __forceinline__ float low_xface(const Smem& sm, const KGrid<float>& g, const KPhys<float>& p, int tm,
+                                           int tc, int tp, int bs, int r)
+{
+    const float* T = sm.T[tc];
+    const float TL = T[off(r, -1)], TR = T[off(r, 0)];
+    const float gyL = T[off(r + 1, -1)] - T[off(r - 1, -1)];
+    const float gyR = T[off(r + 1, 0)] - T[off(r - 1, 0)];
+    const float gzL = sm.T[tp][off(r, -1)] - sm.T[tm][off(r, -1)];
+    const float gzR = sm.T[tp][off(r, 0)] - sm.T[tm][off(r, 0)];
+    float b[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) b[e] = 0.5f * (sm.B[bs][e][off(r, -1)] + sm.B[bs][e][off(r, 0)]);
+    return face_flux<float, SP, SAT>(TL, TR, (TR - TL) * g.inv_dx[0], (gyL + gyR) * g.inv_4dx[1],
+                                     (gzL + gzR) * g.inv_4dx[2], b[0], b[1], b[2], p);
+}
+
+}  // namespace x2
+
+// --------------------------------------------------------------------------
+// one tile: columns [i0, i0 + 64), rows [j0, j0 + 8), planes [z0, z0 + nzc)
+
+template <bool SP, bool SAT, int MODE>
+__device__ __forceinline__ void tile_x2(x2::Smem& sm, const KGrid<float>& g, const KPhys<float>& p,
+                                        const x2::FastArgs& a, KCoef<float> cf, unsigned* status, int i0, int j0,
+                                        int z0, int nzc)
+{
+    using namespace x2;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int r = tid >> 5;
+    const int c = 2 * lane;
+    const int nx = g.n[0], ny = g.n[1];
+
+    if (MODE != 0 && a.coef_tab) {
+        const float* t = a.coef_tab + 4 * a.j;
+        cf.mu = t[0]; cf.nu = t[1]; cf.mt = t[2]; cf.gt = t[3];
+    }
+
+    Task tk[kSlots];
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) tk[s] = make_task<MODE>(sm, g, a, tid + s * NTHREADS, i0, j0);
+
+    auto tslot = [](int q) { return (q + 1) & 3; };
+    auto bslot = [](int q) { return (q + 1) % 3; };
+    auto yslot = [](int q) { return (q + 3) % 3; };
+    auto load = [&](int q, bool withY) {
+        const PlaneOff po = plane_offsets(g, z0 + q);
+        const unsigned ts = (unsigned)(tslot(q) * PLANE * 4);
+        const unsigned bs = (unsigned)(bslot(q) * 3 * PLANE * 4);
+        const unsigned ys = (unsigned)(yslot(q) * 3 * TY * TX * 4);
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) issue(tk[s], po, ts, bs, ys, withY, g.bcv);
+    };
+
+    load(-1, false);
+    cp_commit();
+    load(0, true);
+    cp_commit();
+    load(1, nzc > 1);
+    cp_commit();
+    cp_wait<0>();
+    __syncthreads();
+
+    const float2 idx2 = bc2(g.inv_dx[0]), idy2 = bc2(g.inv_dx[1]), idz2 = bc2(g.inv_dx[2]);
+    const float2 i4x = bc2(g.inv_4dx[0]), i4y = bc2(g.inv_4dx[1]), i4z = bc2(g.inv_4dx[2]);
+    const float2 half = bc2(0.5f);
+
+    QZ A = read_qz(sm, tslot(-1), bslot(-1), c, r);
+    QZ B = read_qz(sm, tslot(0), bslot(0), c, r);
+    float2 Fz_lo = face2<SP, SAT>(A.To, B.To, mul2(sub2(B.To, A.To), idz2), mul2(add2(A.gxo, B.gxo), i4x),
+                                  mul2(add2(A.gyo, B.gyo), i4y), mul2(half, add2(A.bo[2], B.bo[2])),
+                                  mul2(half, add2(A.bo[0], B.bo[0])), mul2(half, add2(A.bo[1], B.bo[1])), p);
+    float2 TmO = A.To, TmU = A.TU;
+    float TmR = A.Tr;
+
+    const bool in0 = (j0 + r < ny) && (i0 + c < nx);   // nx % 4 == 0: both cells or none
+    int64_t cbase = ((int64_t)z0 * ny + (j0 + r)) * nx + (i0 + c);
+
+    // one plane: cur holds plane q, nxt receives plane q + 1
+    auto step = [&](int q, QZ& cur, QZ& nxt) {
+        if (q + 2 <= nzc) load(q + 2, q + 2 < nzc);
+        cp_commit();
+        cp_wait<1>();
+        __syncthreads();
+
+        const float2 TmRp = make_float2(TmO.y, TmR);
+        const QXY cx = read_qxy(sm, tslot(q), bslot(q), c, r, cur);
+        nxt = read_qz(sm, tslot(q + 1), bslot(q + 1), c, r);
+        const float2 gzo = sub2(nxt.To, TmO);
+        const float2 TRn = make_float2(nxt.To.y, nxt.Tr);
+        const float2 gzR = sub2(TRn, TmRp);
+        const float2 gzU = sub2(nxt.TU, TmU);
+        const float2 TR = make_float2(cur.To.y, cur.Tr);
+
+        // +x faces of the pair
+        const float2 Fx = face2<SP, SAT>(
+            cur.To, TR, mul2(sub2(TR, cur.To), idx2), mul2(add2(cur.gyo, cx.gyR), i4y), mul2(add2(gzo, gzR), i4z),
+            mul2(half, add2(cur.bo[0], make_float2(cur.bo[0].y, cx.bR[0]))),
+            mul2(half, add2(cur.bo[1], make_float2(cur.bo[1].y, cx.bR[1]))),
+            mul2(half, add2(cur.bo[2], make_float2(cur.bo[2].y, cx.bR[2]))), p);
+        // +y faces
+        const float2 Fy = face2<SP, SAT>(cur.To, cur.TU, mul2(sub2(cur.TU, cur.To), idy2),
+                                         mul2(add2(cur.gxo, cx.gxU), i4x), mul2(add2(gzo, gzU), i4z),
+                                         mul2(half, add2(cur.bo[1], cx.bU[1])), mul2(half, add2(cur.bo[0], cx.bU[0])),
+                                         mul2(half, add2(cur.bo[2], cx.bU[2])), p);
+        // +z faces
+        const float2 Fz = face2<SP, SAT>(cur.To, nxt.To, mul2(sub2(nxt.To, cur.To), idz2),
+                                         mul2(add2(cur.gxo, nxt.gxo), i4x), mul2(add2(cur.gyo, nxt.gyo), i4y),
+                                         mul2(half, add2(cur.bo[2], nxt.bo[2])), mul2(half, add2(cur.bo[0], nxt.bo[0])),
+                                         mul2(half, add2(cur.bo[1], nxt.bo[1])), p);
+
+        const int par = q & 1;
+        if (r == 0) {
+            *reinterpret_cast<float2*>(&sm.Fy[par][0][c]) =
+                low_yface2<SP, SAT>(sm, g, p, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), c);
+        } else if (r == 1 && lane < TY) {
+            sm.FxLo[par][lane] = low_xface<SP, SAT>(sm, g, p, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), lane);
+        }
+        float2 y0v = bc2(0.f), yjm2v = bc2(0.f), my0v = bc2(0.f);
+        if (MODE == 2) {
+            const int ys = yslot(q);
+            y0v = lds2(&sm.Y[ys][0][r * TX + c]);
+            yjm2v = lds2(&sm.Y[ys][1][r * TX + c]);
+            my0v = lds2(&sm.Y[ys][2][r * TX + c]);
+        }
+        *reinterpret_cast<float2*>(&sm.Fy[par][r + 1][c]) = Fy;
+        const float fxl = __shfl_up_sync(0xffffffffu, Fx.y, 1);
+        __syncthreads();
+
+        const float2 Fx_lo = make_float2(lane == 0 ? sm.FxLo[par][r] : fxl, Fx.x);
+        const float2 Fy_lo = lds2(&sm.Fy[par][r][c]);
+        const float2 div = fma2(sub2(Fx, Fx_lo), idx2, fma2(sub2(Fy, Fy_lo), idy2, mul2(sub2(Fz, Fz_lo), idz2)));
+        const float2 M = mul2(bc2(-1.f), div);
+        if (in0) {
+            float2* out = reinterpret_cast<float2*>(a.out + cbase);
+            if (MODE == 0) {
+                *out = M;
+            } else if (MODE == 1) {
+                if (a.MY0out) *reinterpret_cast<float2*>(a.MY0out + cbase) = M;
+                const float2 y = fma2(bc2(cf.mt), M, cur.To);
+                check_value<float, SP>(y.x, status);
+                check_value<float, SP>(y.y, status);
+                *out = y;
+            } else {
+                const float2 inc = fma2(bc2(cf.mu), sub2(cur.To, y0v),
+                                        fma2(bc2(cf.nu), sub2(yjm2v, y0v), fma2(bc2(cf.mt), M, mul2(bc2(cf.gt), my0v))));
+                const float2 y = add2(y0v, inc);
+                check_value<float, SP>(y.x, status);
+                check_value<float, SP>(y.y, status);
+                *out = y;
+            }
+        }
+        cbase += g.plane;
+        Fz_lo = Fz;
+        TmO = cur.To;
+        TmR = cur.Tr;
+        TmU = cur.TU;
+    };
+
+    int q = 0;
+    for (; q + 1 < nzc; q += 2) {
+        step(q, B, A);
+        step(q + 1, A, B);
+    }
+    if (q < nzc) step(q, B, A);
+    cp_wait<0>();
+    __syncthreads();
+}
+
+namespace {
+
+// OCC = resident CTAs per SM the register budget is sized for (2: up to 128
+// registers, no spills; 3: up to 80 registers, a few spilled words).
+template <bool SP, bool SAT, int MODE, int OCC>
+__global__ void __launch_bounds__(x2::NTHREADS, OCC)
+stage_x2_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf, unsigned* status, int nzchunk)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    x2::Smem& sm = *reinterpret_cast<x2::Smem*>(smem_raw);
+    const int i0 = blockIdx.x * x2::TX;
+    const int j0 = blockIdx.y * x2::TY;
+    const int z0 = blockIdx.z * nzchunk;
+    const int nzc = min(nzchunk, g.n[2] - z0);
+    tile_x2<SP, SAT, MODE>(sm, g, p, a, cf, status, i0, j0, z0, nzc);
+}
+
+template <bool SP, bool SAT, int MODE, int OCC>
+cudaError_t launch3(const KGrid<float>& g, const KPhys<float>& p, const x2::FastArgs& a, const KCoef<float>& cf,
+                    unsigned* status, int nzchunk, cudaStream_t st)
+{
+    const int smem = (int)sizeof(x2::Smem);
+    static bool attr_set = false;       // the attribute is per function, set once
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(stage_x2_kernel<SP, SAT, MODE, OCC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    dim3 grid((g.n[0] + x2::TX - 1) / x2::TX, (g.n[1] + x2::TY - 1) / x2::TY, (g.n[2] + nzchunk - 1) / nzchunk);
+    stage_x2_kernel<SP, SAT, MODE, OCC><<<grid, x2::NTHREADS, smem, st>>>(g, p, a, cf, status, nzchunk);
+    return cudaGetLastError();
+}
+
+template <bool SP, bool SAT, int OCC>
+cudaError_t launch_mode(int mode, const KGrid<float>& g, const KPhys<float>& p, const x2::FastArgs& a,
+                        const KCoef<float>& cf, unsigned* status, int nzchunk, cudaStream_t st)
+{
+    if (mode == 0) return launch3<SP, SAT, 0, OCC>(g, p, a, cf, status, nzchunk, st);
+    if (mode == 1) return launch3<SP, SAT, 1, OCC>(g, p, a, cf, status, nzchunk, st);
+    return launch3<SP, SAT, 2, OCC>(g, p, a, cf, status, nzchunk, st);
+}
+
+template <int OCC>
+cudaError_t launch_phys(const LaunchCfg& c, int mode, const KGrid<float>& g, const KPhys<float>& p,
+                        const x2::FastArgs& a, const KCoef<float>& cf, unsigned* status, int nzchunk, cudaStream_t st)
+{
+    if (c.spitzer) {
+        if (c.saturate) return launch_mode<true, true, OCC>(mode, g, p, a, cf, status, nzchunk, st);
+        return launch_mode<true, false, OCC>(mode, g, p, a, cf, status, nzchunk, st);
+    }
+    if (c.saturate) return launch_mode<false, true, OCC>(mode, g, p, a, cf, status, nzchunk, st);
+    return launch_mode<false, false, OCC>(mode, g, p, a, cf, status, nzchunk, st);
+}
+
+}  // namespace
+
+bool x2_stage_supported(const LaunchCfg& c, const KGrid<float>& g)
+{
+    return c.dtype == 0 && c.ndim == 3 && (g.n[0] % 4) == 0;
+}
+
+x2::FastArgs x2_args(const StageIO& io)
+{
+    x2::FastArgs a;
+    a.Tin = static_cast<const float*>(io.mode == 1 ? io.Y0 : io.Yjm1);
+    a.b = static_cast<const float*>(io.b);
+    a.Y0 = static_cast<const float*>(io.Y0);
+    a.Yjm2 = static_cast<const float*>(io.Yjm2);
+    a.MY0in = static_cast<const float*>(io.MY0);
+    a.MY0out = io.mode == 1 ? static_cast<float*>(io.MY0) : nullptr;
+    a.out = static_cast<float*>(io.Yj);
+    a.coef_tab = static_cast<const float*>(io.coef_tab);
+    a.j = io.j;
+    return a;
+}
+
+cudaError_t launch_stage_x2(const LaunchCfg& c, const KGrid<float>& g, const KPhys<float>& p, const StageIO& io,
+                            const KCoef<float>& coef, unsigned* status, int nzchunk, int occupancy, cudaStream_t st)
+{
+    const x2::FastArgs a = x2_args(io);
+    if (nzchunk < 1) nzchunk = 32;
+    if (occupancy == 3) return launch_phys<3>(c, io.mode, g, p, a, coef, status, nzchunk, st);
+    return launch_phys<2>(c, io.mode, g, p, a, coef, status, nzchunk, st);
+}
+
+// --------------------------------------------------------------------------
+// Persistent ensemble kernel: one launch advances every problem of an
+// ensemble by one super-step.  Work items (problem, stage, tile) are
+// claimed in a fixed stage-major order from a global counter; before a tile
+// of stage j of problem p runs, the CTA waits until all tiles of stage j-1
+// of p are done (a per-problem counter).  Every item a CTA waits on was
+// claimed earlier by a CTA that is already running and never waits on a
+// later item, so the schedule cannot deadlock; each wait is still bounded
+// and ends with ST_TIMEOUT and an abort flag that stops the other CTAs.
+
+namespace {
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <bool SP, bool SAT>
+__global__ void __launch_bounds__(x2::NTHREADS, 2)
+ensemble_x2_kernel(const x2::EnsProb* __restrict__ probs, const x2::EnsSeg* __restrict__ segs, int nseg,
+                   int total, int* work, unsigned* done, unsigned* status, int* abort_flag, long long spin_limit)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    x2::Smem& sm = *reinterpret_cast<x2::Smem*>(smem_raw);
+    __shared__ int s_go, s_p, s_j, s_tile;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int go = 1;
+            const int it = atomicAdd(work, 1);
+            if (it >= total || *reinterpret_cast<volatile int*>(abort_flag)) {
+                go = 0;
+            } else {
+                int lo = 0, hi = nseg - 1;                 // last segment with first <= it
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (segs[mid].first <= it) lo = mid; else hi = mid - 1;
+                }
+                const x2::EnsSeg sg = segs[lo];
+                const unsigned target = (unsigned)((sg.j - 1) * probs[sg.p].ntiles);
+                long long n = 0;
+                while (ld_acquire(&done[sg.p]) < target) {
+                    if (++n > spin_limit || *reinterpret_cast<volatile int*>(abort_flag)) {
+                        atomicOr(status, ST_TIMEOUT);
+                        atomicExch(abort_flag, 1);
+                        go = 0;
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+                s_p = sg.p;
+                s_j = sg.j;
+                s_tile = it - sg.first;
+            }
+            s_go = go;
+        }
+        __syncthreads();
+        if (!s_go) break;
+        const x2::EnsProb& d = probs[s_p];
+        const int j = s_j, tile = s_tile;
+        const int bx = tile % d.tx, by = (tile / d.tx) % d.ty, bz = tile / (d.tx * d.ty);
+        const int z0 = bz * d.nzchunk;
+        const int nzc = min(d.nzchunk, d.g.n[2] - z0);
+        x2::FastArgs a;
+        a.b = d.b;
+        a.Y0 = d.T;
+        a.coef_tab = d.coef;
+        a.j = j;
+        KCoef<float> cf{0.f, 0.f, 0.f, 0.f};
+        if (j == 1) {
+            a.Tin = d.T;
+            a.Yjm2 = nullptr;
+            a.MY0in = nullptr;
+            a.MY0out = d.my0;
+            a.out = d.buf[0];
+            tile_x2<SP, SAT, 1>(sm, d.g, d.p, a, cf, status, bx * x2::TX, by * x2::TY, z0, nzc);
+        } else {
+            a.Tin = d.buf[(j - 2) % 3];
+            a.Yjm2 = j == 2 ? d.T : d.buf[(j - 3) % 3];
+            a.MY0in = d.my0;
+            a.MY0out = nullptr;
+            a.out = j == d.s ? d.T : d.buf[(j - 1) % 3];
+            tile_x2<SP, SAT, 2>(sm, d.g, d.p, a, cf, status, bx * x2::TX, by * x2::TY, z0, nzc);
+        }
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&done[s_p], 1u);
+        }
+    }
+}
+
+template <bool SP, bool SAT>
+cudaError_t ensemble_launch_t(const x2::EnsProb* probs, const x2::EnsSeg* segs, int nseg, int total, int* work,
+                              unsigned* done, unsigned* status, int* abort_flag, long long spin_limit, int grid,
+                              cudaStream_t st)
+{
+    const int smem = (int)sizeof(x2::Smem);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(ensemble_x2_kernel<SP, SAT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (grid <= 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ensemble_x2_kernel<SP, SAT>,
+                                                                      x2::NTHREADS, smem);
+        if (e != cudaSuccess) return e;
+        grid = sms * (per > 0 ? per : 1);
+    }
+    if (grid > total) grid = total > 0 ? total : 1;
+    ensemble_x2_kernel<SP, SAT><<<grid, x2::NTHREADS, smem, st>>>(probs, segs, nseg, total, work, done, status,
+                                                                   abort_flag, spin_limit);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_ensemble_x2(bool spitzer, bool saturate, const x2::EnsProb* probs, const x2::EnsSeg* segs,
+                               int nseg, int total, int* work, unsigned* done, unsigned* status, int* abort_flag,
+                               long long spin_limit, int grid, cudaStream_t st)
+{
+    if (spitzer) {
+        if (saturate)
+            return ensemble_launch_t<true, true>(probs, segs, nseg, total, work, done, status, abort_flag, spin_limit,
+                                                 grid, st);
+        return ensemble_launch_t<true, false>(probs, segs, nseg, total, work, done, status, abort_flag, spin_limit,
+                                              grid, st);
+    }
+    if (saturate)
+        return ensemble_launch_t<false, true>(probs, segs, nseg, total, work, done, status, abort_flag, spin_limit,
+                                              grid, st);
+    return ensemble_launch_t<false, false>(probs, segs, nseg, total, work, done, status, abort_flag, spin_limit,
+                                           grid, st);
+}
+
+}  // namespace rkl

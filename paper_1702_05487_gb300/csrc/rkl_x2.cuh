@@ -1,0 +1,67 @@
+// Layout shared by the paired-cell stage kernel and the persistent ensemble
+// kernel: tile geometry, kernel arguments and the shared-memory bundle ring.
+#pragma once
+
+#include "rkl_device.cuh"
+
+namespace rkl {
+namespace x2 {
+
+constexpr int TX = 64;                  // tile columns: 32 lanes x 2 cells
+constexpr int TY = 8;                   // tile rows: one warp per row
+constexpr int NTHREADS = 32 * TY;
+constexpr int SXS = 72;                 // smem row: halo chunk (4), 64 interior, halo chunk (4)
+constexpr int CPR = SXS / 4;            // 16-byte chunks per smem row
+constexpr int ROWS = TY + 2;
+constexpr int PLANE = ROWS * SXS;
+
+struct FastArgs {
+    const float* Tin;       // field whose M is taken (Y_{j-1}, or Y_0 at stage 1)
+    const float* b;         // [3][ncell]
+    const float* Y0;
+    const float* Yjm2;
+    const float* MY0in;
+    float* MY0out;          // stage 1 only
+    float* out;             // Y_j, or M(T) in mode 0
+    const float* coef_tab;  // if non-null: stage coefficients at coef_tab[4 j]
+    int j;
+};
+
+struct Smem {
+    float T[4][PLANE];              // Y_{j-1} planes q-1, q, q+1 and the one in flight
+    float B[3][3][PLANE];           // b planes q, q+1 and the one in flight
+    float Y[3][3][TY * TX];         // Y0, Y_{j-2}, M(Y0) of planes q, q+1, in flight
+    float Fy[2][TY + 1][TX];        // y-face fluxes (row 0: the tile's lower boundary)
+    float FxLo[2][TY];              // x-faces on the tile's left boundary
+};
+
+// One problem of an ensemble as the persistent kernel sees it.
+struct EnsProb {
+    KGrid<float> g;
+    KPhys<float> p;
+    float* T;               // Y_0 and the result (caller's array)
+    const float* b;         // [3][ncell] (caller's array)
+    float* buf[3];          // rotating stage buffers (ensemble workspace)
+    float* my0;             // M(Y_0)
+    const float* coef;      // this super-step's table, stage j at coef[4 j]
+    int s;                  // stages this super-step
+    int tx, ty, tz, ntiles; // tiles in x, y and z-chunks
+    int nzchunk;
+};
+
+// A run of work items: the tiles of stage j of problem p, items
+// [first, first + count) in the global order.
+struct EnsSeg {
+    int first;
+    int p;
+    int j;
+    int count;
+};
+
+}  // namespace x2
+
+cudaError_t launch_ensemble_x2(bool spitzer, bool saturate, const x2::EnsProb* probs, const x2::EnsSeg* segs,
+                               int nseg, int total, int* work, unsigned* done, unsigned* status, int* abort_flag,
+                               long long spin_limit, int grid, cudaStream_t st);
+
+}  // namespace rkl

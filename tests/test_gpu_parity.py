@@ -131,6 +131,15 @@ def _variant_cases():
         out.append(c + (0,))
         if c[3] == "f32" and len(c[1]) == 3:
             out.append(c + (1,))        # the generic kernel on the same 3D FP32 case
+            out.append(c + (2,))        # the tiled one-cell-per-thread kernel
+    # grids with nx % 4 == 0 (the paired-cell kernel) and Dirichlet partial tiles
+    spitz = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
+    sat = dict(kappa_model="spitzer", kappa_par0=0.01, saturate=True, phi=0.3)
+    for v in (2, 3, 4):
+        out.append(("3d_x4_dirichlet", (21, 19, 36), dict(spitz, bc="dirichlet", bc_value=0.9), "f32", v))
+        out.append(("3d_x4_sat", (18, 26, 68), sat, "f32", v))
+        out.append(("3d_x4_sat_upwind", (10, 9, 132), dict(sat, phi=0.05, sat_upwind=True), "f32", v))
+        out.append(("3d_x4_const", (33, 17, 44), dict(kappa_par0=0.02, kappa_perp_ratio=0.1), "f32", v))
     return out
 
 
@@ -158,15 +167,20 @@ def test_super_steps(rk, orc, case):
     assert plan.check() == 0
 
 
-@pytest.mark.parametrize("shape", [(32, 32, 32), (7, 9, 5), (40, 3, 70), (1, 33, 64), (65, 8, 36)])
-def test_tiled_kernel_matches_generic(rk, orc, shape):
-    """The tiled kernel (variant 2) and the generic kernel (variant 1) on
-    tile-aligned, ragged and degenerate shapes; both against the oracle."""
-    import torch
+@pytest.mark.parametrize("shape,nzchunk", [((32, 32, 32), 0), ((7, 9, 5), 0), ((40, 3, 70), 0),
+                                           ((1, 33, 64), 0), ((65, 8, 36), 0), ((37, 24, 128), 5),
+                                           ((64, 16, 64), 64), ((9, 40, 4), 2), ((3, 8, 200), 1)])
+def test_tiled_kernels_match_generic(rk, orc, shape, nzchunk):
+    """The tiled kernels (variants 2 and 3, the latter when nx % 4 == 0,
+    with several z-chunk lengths) and the generic kernel (variant 1) on
+    tile-aligned, ragged and degenerate shapes; all against the oracle."""
     params = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
+    variants = (1, 2, 3, 4) if shape[2] % 4 == 0 else (1, 2)
     res = {}
-    for v in (1, 2):
+    for v in variants:
         P, plan, T, b, Td, bd = _setup(rk, "x", shape, params, "f32", v)
+        if v >= 3:
+            plan.set_variant(v, nzchunk)
         dt = 40 * orc.dt_expl(P, T)
         for _ in range(2):
             plan.super_step(dt, Td, bd)
@@ -174,9 +188,9 @@ def test_tiled_kernel_matches_generic(rk, orc, shape):
     Tref = T
     for _ in range(2):
         Tref, _ = orc.super_step(P, Tref, b, dt)
-    for v in (1, 2):
+    for v in variants:
         assert rel_l2(res[v], Tref) < F32_STATE_REL_L2, v
-    assert norm_max(res[2], res[1]) < F32_STATE_MAX
+        assert norm_max(res[v], res[1]) < F32_STATE_MAX, v
 
 
 def test_dt_expl_and_energy(rk, orc):

@@ -30,6 +30,7 @@ import math
 from dataclasses import dataclass
 
 import numpy as np
+import scipy.fft
 
 KMIN, KMAX = 2, 8
 SPECTRAL_SLOPE = -17.0 / 3.0     # |A_k|^2 ~ k^slope
@@ -74,7 +75,7 @@ def _synth(nx: int, ny: int, nz: int, ks: np.ndarray, coef: np.ndarray) -> np.nd
     spec = np.zeros((nz, ny, nx), dtype=np.complex128)
     np.add.at(spec, (kz, ky, kx), c)
     np.add.at(spec, ((-ks[:, 2]) % nz, (-ks[:, 1]) % ny, (-ks[:, 0]) % nx), np.conj(c))
-    return np.fft.ifftn(spec).real * (nx * ny * nz)
+    return scipy.fft.ifftn(spec, workers=-1).real * (nx * ny * nz)
 
 
 def tangled_b(n: int, seed: int = 2) -> np.ndarray:
