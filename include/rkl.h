@@ -281,6 +281,60 @@ rkl_status rkl_ensemble_autotune(rkl_ensemble *ens, const double *dt, const void
  */
 rkl_status rkl_ensemble_selftest_timeout(rkl_ensemble *ens, int *status_out);
 
+/* ------------------------------------------------------------------------
+ * Learned surrogate of one super-step (no counterpart in the paper; the
+ * RKL2 super-step above is its fallback and the judge of its error).
+ * Network: 6 periodic 3x3x3 convolutions, channels 6 -> 32 -> 32 -> 32 ->
+ * 32 -> 32 -> 3, ReLU between layers, BF16 weights and activations with
+ * FP32 accumulation on tensor cores.  Inputs per cell: T - 1, b_x, b_y,
+ * b_z, log10(kappa_par(T) / 0.01), (dt/dt_expl) / 100.  The three output
+ * channels are face fluxes G_d and the predicted increment is
+ *   dT = -head_scale * sum_d (G_d(c) - G_d(c - e_d)) / dx_d,
+ * a conservative divergence, so sum dT = 0 (exact energy conservation up
+ * to rounding).  Patch: D x H x W periodic cells with D % 4 == H % 8 ==
+ * W % 16 == 0.  Layer l has weights [27][cout][cin] (offset o = ((dz+1) 3 +
+ * dy+1) 3 + dx+1, channels padded: layer 0 cin 16 (6 used), layer 5 cout 16
+ * (3 used), padded entries must stay 0) and bias [cout]; FP32 masters on
+ * the device, Adam moments kept per parameter.  All device work runs on
+ * the stream given at creation; rkl_sur_super_step also uses the plan's
+ * stream, which must be the same stream.
+ */
+typedef struct rkl_surrogate rkl_surrogate;
+
+rkl_status rkl_sur_layer_shape(int layer, int *cout, int *cin);
+rkl_status rkl_sur_create(int D, int H, int W, const double *dx, void *cuda_stream,
+                          rkl_surrogate **out);
+rkl_status rkl_sur_destroy(rkl_surrogate *sur);
+const char *rkl_sur_last_error(const rkl_surrogate *sur);
+/* host <-> device copies of layer parameters (w: 27*cout*cin floats, b: cout) */
+rkl_status rkl_sur_set_params(rkl_surrogate *sur, int layer, const float *w, const float *b);
+rkl_status rkl_sur_get_params(rkl_surrogate *sur, int layer, float *w, float *b);
+/* gradients of the last rkl_sur_backward / rkl_sur_train_step */
+rkl_status rkl_sur_get_grads(rkl_surrogate *sur, int layer, float *gw, float *gb);
+/* input channels from device arrays T [cells] and b [3][cells] */
+rkl_status rkl_sur_features(rkl_surrogate *sur, const void *T, const void *b, double kappa_par0,
+                            int spitzer, double dt_over_dtexpl);
+/* forward pass; the increment dT goes to dT_out (device floats) if not NULL */
+rkl_status rkl_sur_forward(rkl_surrogate *sur, double head_scale, void *dT_out);
+/* MSE loss 0.5 mean((dT - target)^2) of the last forward and all gradients */
+rkl_status rkl_sur_backward(rkl_surrogate *sur, const void *target, double *loss);
+/* one Adam step on every parameter (bias-corrected, step counter kept) */
+rkl_status rkl_sur_adam(rkl_surrogate *sur, double lr, double beta1, double beta2, double eps);
+/* forward + backward + Adam (beta1 0.9, beta2 0.999, eps 1e-8) */
+rkl_status rkl_sur_train_step(rkl_surrogate *sur, double head_scale, const void *target, double lr,
+                              double *loss);
+/*
+ * One super-step of length dt with the surrogate: predicts dT, computes the
+ * trapezoidal-rule residual rho = ||dT - (dt/2)(M(T) + M(T + dT))|| / ||dT||
+ * (two applications of M), accepts T + dT if rho <= threshold, otherwise
+ * runs rkl_super_step (the fallback).  *accepted, *residual, *s_used (0
+ * when accepted) are written.  The plan must describe the same periodic 3D
+ * FP32 patch.
+ */
+rkl_status rkl_sur_super_step(rkl_surrogate *sur, rkl_plan *plan, double dt, void *T,
+                              const void *b, double head_scale, double threshold,
+                              int *accepted, double *residual, int *s_used);
+
 /*
  * dt_expl and energy without allocating.  The paper has no counterpart to
  * this entry point; it exists for callers that cannot allocate device

@@ -58,6 +58,13 @@ def conv3d_grad_weight(gy, x):
     return gw, gy.sum(axis=(1, 2, 3))
 
 
+def features(T, b, kappa0, spitzer, ratio):
+    """Network input channels [6][z][y][x]: T - 1, b_x, b_y, b_z,
+    log10(kappa_par(T) / 0.01), (dt / dt_expl) / 100."""
+    kap = kappa0 * T ** 2.5 if spitzer else np.full_like(T, kappa0)
+    return np.stack([T - 1.0, b[0], b[1], b[2], np.log10(kap) + 2.0, np.full_like(T, ratio / 100.0)])
+
+
 def flux_divergence(G, tau, dx):
     """dT = -tau * sum_d (G_d[c] - G_d[c - e_d]) / dx_d for G = [Gx, Gy, Gz]
     (G_d at cell c is the flux on face c + e_d / 2), periodic."""

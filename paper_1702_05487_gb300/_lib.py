@@ -84,6 +84,20 @@ SIGNATURES = {
     "rkl_ensemble_check": (ctypes.c_int, [_vp]),
     "rkl_ensemble_autotune": (ctypes.c_int, [_vp, _dp, _vp, _vp, _ip, _ip, _dp]),
     "rkl_ensemble_selftest_timeout": (ctypes.c_int, [_vp, _ip]),
+    "rkl_sur_layer_shape": (ctypes.c_int, [ctypes.c_int, _ip, _ip]),
+    "rkl_sur_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _vp, ctypes.POINTER(_vp)]),
+    "rkl_sur_destroy": (ctypes.c_int, [_vp]),
+    "rkl_sur_last_error": (ctypes.c_char_p, [_vp]),
+    "rkl_sur_set_params": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "rkl_sur_get_params": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "rkl_sur_get_grads": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "rkl_sur_features": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_double]),
+    "rkl_sur_forward": (ctypes.c_int, [_vp, ctypes.c_double, _vp]),
+    "rkl_sur_backward": (ctypes.c_int, [_vp, _vp, _dp]),
+    "rkl_sur_adam": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    "rkl_sur_train_step": (ctypes.c_int, [_vp, ctypes.c_double, _vp, ctypes.c_double, _dp]),
+    "rkl_sur_super_step": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, ctypes.c_double, ctypes.c_double,
+                                          _ip, _dp, _ip]),
 }
 
 _lib = None
@@ -295,3 +309,82 @@ def rkl_ensemble_selftest_timeout(ens) -> int:
     out = ctypes.c_int(0)
     _echeck(load().rkl_ensemble_selftest_timeout(ens, ctypes.byref(out)), ens)
     return out.value
+
+
+def _scheck(st: int, sur):
+    if st != RKL_OK:
+        raise RklError(st, load().rkl_sur_last_error(sur).decode())
+
+
+def rkl_sur_layer_shape(layer: int):
+    co, ci = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().rkl_sur_layer_shape(int(layer), ctypes.byref(co), ctypes.byref(ci)))
+    return co.value, ci.value
+
+
+def rkl_sur_create(D, H, W, dx, stream=None):
+    dxa = (ctypes.c_double * 3)(*[float(v) for v in dx])
+    h = _vp()
+    st = load().rkl_sur_create(int(D), int(H), int(W), dxa, _vp(int(stream) if stream else 0), ctypes.byref(h))
+    if st != RKL_OK:
+        raise RklError(st, load().rkl_last_error(None).decode())
+    return h
+
+
+def rkl_sur_destroy(sur):
+    _scheck(load().rkl_sur_destroy(sur), None)
+
+
+def rkl_sur_set_params(sur, layer, w, b):
+    """w, b: contiguous float32 numpy arrays ([27][cout][cin], [cout])."""
+    _scheck(load().rkl_sur_set_params(sur, int(layer), _ptr(w), _ptr(b)), sur)
+
+
+def rkl_sur_get_params(sur, layer):
+    import numpy as np
+    co, ci = rkl_sur_layer_shape(layer)
+    w = np.zeros((27, co, ci), dtype=np.float32)
+    b = np.zeros(co, dtype=np.float32)
+    _scheck(load().rkl_sur_get_params(sur, int(layer), _ptr(w), _ptr(b)), sur)
+    return w, b
+
+
+def rkl_sur_get_grads(sur, layer):
+    import numpy as np
+    co, ci = rkl_sur_layer_shape(layer)
+    w = np.zeros((27, co, ci), dtype=np.float32)
+    b = np.zeros(co, dtype=np.float32)
+    _scheck(load().rkl_sur_get_grads(sur, int(layer), _ptr(w), _ptr(b)), sur)
+    return w, b
+
+
+def rkl_sur_features(sur, T, b, kappa_par0, spitzer, ratio):
+    _scheck(load().rkl_sur_features(sur, _ptr(T), _ptr(b), float(kappa_par0), int(bool(spitzer)), float(ratio)), sur)
+
+
+def rkl_sur_forward(sur, head_scale, dT_out=None):
+    _scheck(load().rkl_sur_forward(sur, float(head_scale), _ptr(dT_out)), sur)
+
+
+def rkl_sur_backward(sur, target) -> float:
+    loss = ctypes.c_double(0.0)
+    _scheck(load().rkl_sur_backward(sur, _ptr(target), ctypes.byref(loss)), sur)
+    return loss.value
+
+
+def rkl_sur_adam(sur, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    _scheck(load().rkl_sur_adam(sur, float(lr), float(beta1), float(beta2), float(eps)), sur)
+
+
+def rkl_sur_train_step(sur, head_scale, target, lr) -> float:
+    loss = ctypes.c_double(0.0)
+    _scheck(load().rkl_sur_train_step(sur, float(head_scale), _ptr(target), float(lr), ctypes.byref(loss)), sur)
+    return loss.value
+
+
+def rkl_sur_super_step(sur, plan, dt, T, b, head_scale, threshold):
+    """Returns (accepted, residual, s_used)."""
+    acc, res, s = ctypes.c_int(0), ctypes.c_double(0.0), ctypes.c_int(0)
+    _scheck(load().rkl_sur_super_step(sur, plan, float(dt), _ptr(T), _ptr(b), float(head_scale), float(threshold),
+                                      ctypes.byref(acc), ctypes.byref(res), ctypes.byref(s)), sur)
+    return bool(acc.value), res.value, s.value

@@ -350,6 +350,10 @@ rkl_status run_super_step(rkl_plan* p, double dt, int s, void* T, const void* b,
 namespace rkl {
 // Message for entry points without a plan (read back by rkl_last_error(NULL)).
 void set_unplanned_error(const std::string& msg) { g_create_error = msg; }
+// Read-only views of a plan for other parts of the library.
+const rkl_grid* plan_grid(const rkl_plan* p) { return &p->grid; }
+const rkl_phys* plan_phys(const rkl_plan* p) { return &p->phys; }
+cudaStream_t plan_stream(const rkl_plan* p) { return p->stream; }
 }  // namespace rkl
 
 extern "C" {

@@ -1,0 +1,35 @@
+// Host launchers of the surrogate's kernels (internal to the library).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rkl {
+namespace conv {
+
+// out = act(bias + conv3x3x3_periodic(in, wt)); patch D x H x W with D % 4,
+// H % 8, W % 16 == 0.  (cin, cout, mode) in {(16,32,0), (32,32,0),
+// (32,16,1), (32,32,2), (16,32,2)}; mode 0 ReLU bf16 out, 1 linear f32 out,
+// 2 no bias, result times (mask > 0), bf16 out.
+cudaError_t conv_forward(int cin, int cout, int mode, const void* in, const void* wt, const float* bias,
+                         const void* mask, void* out, int D, int H, int W, cudaStream_t st);
+// dW[27][cout][cin] += sum_v dz[v][cout] x[v + off][cin]; (cin, cout) in
+// {(16,32), (32,32), (32,16)}.  dW must be zeroed by the caller.
+cudaError_t conv_wgrad(int cin, int cout, const void* dz, const void* x, float* dW, int D, int H, int W, int nsplit,
+                       cudaStream_t st);
+// db[c] += sum_v dz[v][c]; c in {16, 32}.  db zeroed by the caller.
+cudaError_t conv_bgrad(int c, const void* dz, float* db, int64_t V, cudaStream_t st);
+
+cudaError_t features(const float* T, const float* b, int64_t V, float kappa0, int spitzer, float ratio, void* X,
+                     cudaStream_t st);
+cudaError_t head_div(const float* G, int D, int H, int W, float tau, const float inv_dx[3], float* dT,
+                     cudaStream_t st);
+cudaError_t loss_and_adjoint(const float* dT, const float* target, int D, int H, int W, float tau,
+                             const float inv_dx[3], float* r, double* partial, int npartial, void* dG,
+                             cudaStream_t st);
+cudaError_t pack_weights(const float* w, int cout, int cin, void* wf, void* wb, cudaStream_t st);
+cudaError_t adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps, int t,
+                 cudaStream_t st);
+
+}  // namespace conv
+}  // namespace rkl
