@@ -114,9 +114,22 @@ def dist_env():
     return world, rank, local
 
 
-def make_inputs():
+WORKLOADS = {
+    # name: (generator, dtype, algorithmic bytes per cell-stage of the stage kernel)
+    "tangled256": ("tangled", "f32", 32),
+    "blob512": ("blob", "f32", 32),
+    "ring100": ("ring", "f64", 56),
+}
+
+
+def make_inputs(name="tangled256"):
     import workloads
-    return workloads.tangled(N_GRID, seed=SEED)
+    gen = WORKLOADS[name][0]
+    if gen == "tangled":
+        return workloads.tangled(N_GRID, seed=SEED)
+    if gen == "blob":
+        return workloads.blob(512, seed=SEED)
+    return workloads.ring(100)
 
 
 def cpu_oracle_sample(W, target_seconds: float = 12.0):
@@ -182,14 +195,16 @@ def run_ours(args):
         torch.cuda.set_device(0)
     import paper_1702_05487_gb300 as rk
 
-    W = make_inputs()
+    W = make_inputs(args.workload)
+    _, dtype, bytes_per_cs = WORKLOADS[args.workload]
+    npdt = np.float32 if dtype == "f32" else np.float64
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    T0 = torch.from_numpy(W.T.astype(np.float32))
-    b0 = torch.from_numpy(W.b.astype(np.float32))
+    T0 = torch.from_numpy(W.T.astype(npdt))
+    b0 = torch.from_numpy(W.b.astype(npdt))
     T = T0.to(dev)
     b = b0.to(dev).contiguous()
-    plan = rk.Plan(W.T.shape, "f32", stream=stream, params=W.params)
+    plan = rk.Plan(W.T.shape, dtype, stream=stream, params=W.params)
     dt = W.ratio * plan.dt_expl(T)
     ncell = T.numel()
 
@@ -263,30 +278,32 @@ def run_ours(args):
 
     peak, peak_kind = measured_peaks()
     avg_launch_ms = stage_ms / max(1, stage_launches)
-    achieved = BYTES_PER_CELL_STAGE * ncell / (avg_launch_ms * 1e-3) / 1e9
+    achieved = bytes_per_cs * ncell / (avg_launch_ms * 1e-3) / 1e9
     traffic = None
-    if MEASURED_TRAFFIC["source_hash"] == kernel_source_hash():
+    if args.workload == "tangled256" and MEASURED_TRAFFIC["source_hash"] == kernel_source_hash():
         traffic = MEASURED_TRAFFIC["bytes_per_launch"]
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and args.workload == "tangled256":
         cpu, _ = cpu_oracle_sample(W)
-    s_last = s_used[-1] if s_used else rk.rkl_num_stages(RATIO)
+    s_last = s_used[-1] if s_used else rk.rkl_num_stages(W.ratio)
     line = {
         "metric": "Gcell-stage/s per RKL2 stage", "value": value, "unit": "Gcell-stage/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N_GRID, "cells": ncell, "s": s_last,
-                   "dt_over_dtexpl": RATIO, "step": "one RKL2 super-step (dt_expl pass + s stages)",
-                   "l2": "inputs larger than L2: 8 grid arrays of 67 MB per stage",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.workload == "tangled256" else W.name, "shape": list(W.T.shape),
+                   "cells": ncell, "s": s_last,
+                   "dt_over_dtexpl": W.ratio, "step": "one RKL2 super-step (dt_expl pass + s stages)",
+                   "l2": ("inputs larger than L2: 8 grid arrays per stage" if ncell * 32 > 129e6
+                          else "working set fits in L2"),
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "kernel": "rkl2 stage", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "algorithmic_bytes_per_launch": BYTES_PER_CELL_STAGE * ncell,
+                     "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_cs * ncell,
                      "avg_launch_ms": avg_launch_ms, "launches_timed": stage_launches},
         "e2e": {"value": e2e_value, "unit": "Gcell-stage/s",
-                "h2d_bytes_per_step": int(T0.numel() * 4 + b0.numel() * 4),
-                "d2h_bytes_per_step": int(T0.numel() * 4)},
+                "h2d_bytes_per_step": int(T0.numel() * T0.element_size() + b0.numel() * b0.element_size()),
+                "d2h_bytes_per_step": int(T0.numel() * T0.element_size())},
         "gpu_launches": int(stages + 2 * args.steps),
         "clocks": clocks.summary(),
         "cpu_baseline": cpu,
@@ -296,6 +313,84 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_ensemble(args):
+    """The batched workload: 64 uneven periodic problems, one step = one
+    super-step of every problem (autotuned schedule)."""
+    import torch
+    import paper_1702_05487_gb300 as rk
+    import workloads
+    torch.cuda.set_device(0)
+    specs = workloads.ensemble_specs(64, seed=4)
+    probs = []
+    for sp in specs:
+        shape = (sp["nz"], sp["ny"], sp["nx"])
+        probs.append((shape, dict(dx=(1.0 / sp["nx"], 1.0 / sp["ny"], 1.0 / sp["nz"]), kappa_model="spitzer",
+                                  kappa_par0=sp["kappa_par0"], kappa_perp_ratio=1e-4)))
+    ens = rk.Ensemble(probs)
+    T_all = torch.empty(ens.offsets[-1], device="cuda")
+    b_all = torch.empty(3 * ens.offsets[-1], device="cuda")
+    dts = []
+    for sp, (Tv, bv), (shape, prm) in zip(specs, ens.views(T_all, b_all), probs):
+        T, b = workloads.tangled_box(sp["nx"], sp["ny"], sp["nz"], sp["seed"])
+        Tv.copy_(torch.from_numpy(T.astype(np.float32)))
+        bv.copy_(torch.from_numpy(b.astype(np.float32)))
+        kmax = prm["kappa_par0"] * float(T.max()) ** 2.5 * (1 + 1e-4)
+        dts.append(sp["ratio"] * 0.5 / (kmax * (sp["nx"] ** 2 + sp["ny"] ** 2 + sp["nz"] ** 2)))
+    pers, nz, _ = ens.autotune(dts, T_all, b_all)
+    for _ in range(args.warmup):
+        ens.super_step(dts, T_all, b_all)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cs = 0.0
+    with ClockSampler(0) as clocks:
+        ev0.record()
+        for _ in range(args.steps):
+            s = ens.super_step(dts, T_all, b_all)
+            cs += sum(float(np.prod(sh)) * sp for (sh, _), sp in zip(probs, s))
+        ev1.record()
+        torch.cuda.synchronize()
+    assert ens.check() == 0
+    ms = ev0.elapsed_time(ev1)
+    value = cs / (ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    line = {"metric": "Gcell-stage/s per RKL2 stage", "value": value, "unit": "Gcell-stage/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "ensemble64", "problems": 64, "cells": int(ens.offsets[-1]),
+                       "schedule": "persistent" if pers else "per-launch", "nzchunk": nz,
+                       "step": "one super-step of every problem (statistics pass + stages)"},
+            "roofline": {"bound": "hbm", "kernel": "whole ensemble step", "achieved": 32 * value,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": 32 * value / peak,
+                         "traffic": None},
+            "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def run_surrogate(args):
+    """The learned surrogate on 128^3 patches: training on RKL2-generated
+    pairs, threshold calibration at 1e-3 relative L2 on held-out pairs, then
+    time-to-solution of surrogate + fallback against plain RKL2."""
+    import torch
+    from paper_1702_05487_gb300.surrogate import Surrogate, SurrogateConfig
+    torch.cuda.set_device(0)
+    sur = Surrogate(SurrogateConfig(n=128, pool=16))
+    t0 = time.perf_counter()
+    losses = sur.train(args.pairs)
+    train_s = time.perf_counter() - t0
+    thr, rows = sur.calibrate(64, accuracy=1e-3)
+    errs = [e for _, e in rows]
+    tts = sur.time_to_solution(10, accuracy=1e-3)
+    line = {"metric": "surrogate vs RKL2 time-to-solution @1e-3 L2", "value": tts["speedup"],
+            "unit": "x (RKL2 time / surrogate+fallback time)", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "bf16/f32", "data": "synthetic",
+            "config": {"workload": "surrogate128", "pairs": args.pairs, "train_s": train_s,
+                       "final_loss": float(np.mean(losses[-50:])), "threshold": thr,
+                       "heldout_rel_l2_median": float(np.median(errs)), "heldout_rel_l2_min": float(min(errs)),
+                       "heldout_within_1e-3": int(sum(e <= 1e-3 for e in errs)), "heldout": len(errs)},
+            "time_to_solution": tts}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -303,9 +398,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="tangled256",
+                    choices=list(WORKLOADS) + ["ensemble64", "surrogate128"])
+    ap.add_argument("--pairs", type=int, default=20000, help="training pairs of the surrogate workload")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ensemble64":
+        run_ensemble(args)
+    elif args.workload == "surrogate128":
+        run_surrogate(args)
     else:
         run_ours(args)
 

@@ -193,6 +193,17 @@ rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
 rkl_status rkl_plan_set_variant(rkl_plan *plan, int variant, int nzchunk);
 
 /*
+ * Autotuner: times one super-step of length dt (s from dt / dt_expl(T))
+ * with every kernel variant and z-chunk that applies to the grid (generic;
+ * tiled; paired-cell at 2 and 3 CTAs per SM with 8, 16, 32, 64 planes per
+ * CTA) on a scratch copy of T (T is not changed), keeps the fastest with
+ * rkl_plan_set_variant and returns it.  Allocates and frees one grid-sized
+ * scratch array.  Synchronises.
+ */
+rkl_status rkl_plan_autotune(rkl_plan *plan, double dt, const void *T, const void *b,
+                             int *variant_out, int *nzchunk_out, double *ms_out);
+
+/*
  * Waits for the plan's stream and returns the device status word collected
  * by the stage kernels since the last check (RKL_OK, RKL_ERR_NONFINITE or
  * RKL_ERR_NONPOSITIVE_T), then clears it.

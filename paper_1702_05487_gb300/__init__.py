@@ -111,6 +111,10 @@ class Plan:
     def set_variant(self, variant, nzchunk=0):
         rkl_plan_set_variant(self.handle, variant, nzchunk)
 
+    def autotune(self, dt, T, b):
+        from . import _lib
+        return _lib.rkl_plan_autotune(self.handle, dt, T, b)
+
     def set_timing(self, on):
         rkl_plan_set_timing(self.handle, on)
 

@@ -69,6 +69,7 @@ SIGNATURES = {
     "rkl_energy": (ctypes.c_int, [_vp, _vp, _dp]),
     "rkl_plan_check": (ctypes.c_int, [_vp]),
     "rkl_plan_set_variant": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "rkl_plan_autotune": (ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp, _ip, _ip, _dp]),
     "rkl_plan_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "rkl_plan_timing": (ctypes.c_int, [_vp, _dp, _i64p]),
     "rkl_run_host": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _vp, _vp, _ip]),
@@ -222,6 +223,14 @@ def rkl_plan_check(plan) -> int:
 
 def rkl_plan_set_variant(plan, variant: int, nzchunk: int = 0):
     _check(load().rkl_plan_set_variant(plan, int(variant), int(nzchunk)), plan)
+
+
+def rkl_plan_autotune(plan, dt, T, b):
+    """Returns (variant, nzchunk, ms of one super-step) of the fastest kernel."""
+    v, nz, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(load().rkl_plan_autotune(plan, float(dt), _ptr(T), _ptr(b), ctypes.byref(v), ctypes.byref(nz),
+                                    ctypes.byref(ms)), plan)
+    return v.value, nz.value, ms.value
 
 
 def rkl_plan_set_timing(plan, on: bool):

@@ -650,6 +650,66 @@ rkl_status rkl_energy(rkl_plan* p, const void* T, double* E_out)
     return RKL_OK;
 }
 
+rkl_status rkl_plan_autotune(rkl_plan* p, double dt, const void* T, const void* b, int* variant_out,
+                             int* nzchunk_out, double* ms_out)
+{
+    if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
+    if (!T || !b) return fail(p, RKL_ERR_INVALID_ARG, "null argument");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(p, RKL_ERR_INVALID_ARG, "dt must be finite and > 0");
+    if (!aligned16(T) || !aligned16(b)) return fail(p, RKL_ERR_INVALID_ARG, "T and b must be 16-byte aligned");
+    DeviceGuard dg(p->device);
+    double dte = 0.0;
+    rkl_status st = rkl_dt_expl(p, T, &dte);
+    if (st != RKL_OK) return st;
+    int s = 0;
+    if (rkl_num_stages(dt / dte, &s) != RKL_OK) return fail(p, RKL_ERR_INVALID_ARG, "dt/dt_expl too large");
+    struct Cand { int v, nz; };
+    std::vector<Cand> cands = {{1, 0}};
+    if (p->fast) cands.push_back({2, 0});
+    if (p->x2ok)
+        for (int nz : {8, 16, 32, 64}) {
+            cands.push_back({3, nz});
+            cands.push_back({4, nz});
+        }
+    void* scratch = nullptr;
+    RKL_CK(p, cudaMalloc(&scratch, (size_t)p->ncell * p->esize));
+    cudaEvent_t a = nullptr, e = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&e);
+    const int keep_v = p->variant, keep_nz = p->nzchunk;
+    double best = 1e300;
+    Cand bc = cands[0];
+    for (const Cand& c : cands) {
+        if (rkl_plan_set_variant(p, c.v, c.nz) != RKL_OK) continue;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && st == RKL_OK; ++rep) {          // the first repetition warms up
+            cudaMemcpyAsync(scratch, T, (size_t)p->ncell * p->esize, cudaMemcpyDeviceToDevice, p->stream);
+            cudaEventRecord(a, p->stream);
+            st = rkl_super_step_s(p, dt, s, scratch, b, nullptr, nullptr);
+            cudaEventRecord(e, p->stream);
+            cudaEventSynchronize(e);
+            cudaEventElapsedTime(&ms, a, e);
+        }
+        if (st != RKL_OK) break;
+        if (ms < best) {
+            best = ms;
+            bc = c;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(e);
+    cudaFree(scratch);
+    if (st != RKL_OK) {
+        rkl_plan_set_variant(p, keep_v, keep_nz);
+        return st;
+    }
+    rkl_plan_set_variant(p, bc.v, bc.nz);
+    if (variant_out) *variant_out = bc.v;
+    if (nzchunk_out) *nzchunk_out = p->nzchunk;
+    if (ms_out) *ms_out = best;
+    return rkl_plan_check(p);
+}
+
 rkl_status rkl_plan_set_variant(rkl_plan* p, int variant, int nzchunk)
 {
     if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;

@@ -47,6 +47,10 @@ __device__ __forceinline__ void ldsm_x4_t(unsigned addr, unsigned& r0, unsigned&
                  : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
                  : "r"(addr));
 }
+__device__ __forceinline__ void ldsm_x2_t(unsigned addr, unsigned& r0, unsigned& r1)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
 __device__ __forceinline__ void ldsm_x2(unsigned addr, unsigned& r0, unsigned& r1)
 {
     asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
@@ -180,38 +184,40 @@ conv_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restric
 
 // --------------------------------------------------------------------------
 // Weight gradient: dW[o][co][ci] += sum_v dz[v][co] * x[v + off(o)][ci].
-// CTA (o, split) walks its share of 512-voxel tiles; each warp owns 32
-// voxels of a tile as its k-slice and keeps the COUT x CIN partial in
-// registers; the 16 warps are folded in smem and added to dW atomically.
+// One persistent CTA per SM walks 512-voxel tiles; per tile it stages the
+// dz tile and the x tile with its one-cell halo once and serves all 27
+// offsets from them.  The work of a tile is split into units (offset o,
+// 8-channel ci block nt), each a COUT x 8 block of dW; warp w owns units
+// w, w + 16, ... and accumulates them over all its tiles in registers,
+// then adds them to dW atomically.
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(NTHR, 1)
 wgrad_kernel(const __nv_bfloat16* __restrict__ dz, const __nv_bfloat16* __restrict__ x, float* __restrict__ dW,
-             int D, int H, int W, int nsplit)
+             int D, int H, int W)
 {
     constexpr int SZ = COUT + 8, SXC = CIN + 8;
     constexpr int MT = COUT / 16;                       // m16 tiles over co
-    constexpr int NT = CIN / 8;
+    constexpr int NT = CIN / 8;                         // n8 blocks over ci
+    constexpr int NU = 27 * NT;                         // units per tile
+    constexpr int UPW = (NU + NWARP - 1) / NWARP;       // units per warp (at most)
     static_assert(COUT % 16 == 0 && CIN % 16 == 0, "channel counts are multiples of 16");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __nv_bfloat16* sZ = reinterpret_cast<__nv_bfloat16*>(smem_raw);        // [TV][SZ]
-    __nv_bfloat16* sX = sZ + TV * SZ;                                       // [TV][SXC]
-    float* sRed = reinterpret_cast<float*>(sX + TV * SXC);                   // [NWARP][COUT*CIN] reused
+    __nv_bfloat16* sX = sZ + TV * SZ;                                       // [HV][SXC]
 
-    const int o = blockIdx.x % 27, split = blockIdx.x / 27;
-    const int dzo = o / 9 - 1, dyo = (o / 3) % 3 - 1, dxo = o % 3 - 1;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tilesx = W / TX, tilesy = H / TY, tilesz = D / TZ;
     const int ntiles = tilesx * tilesy * tilesz;
 
-    float acc[MT][NT][4];
+    float acc[UPW][MT][4];
 #pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
+    for (int i = 0; i < UPW; ++i)
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
+        for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
+            for (int q = 0; q < 4; ++q) acc[i][mt][q] = 0.f;
 
-    for (int tile = split; tile < ntiles; tile += nsplit) {
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int bx = tile % tilesx, by = (tile / tilesx) % tilesy, bz = tile / (tilesx * tilesy);
         const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
         __syncthreads();
@@ -221,66 +227,62 @@ wgrad_kernel(const __nv_bfloat16* __restrict__ dz, const __nv_bfloat16* __restri
             const int64_t gv = ((int64_t)(z0 + tz) * H + (y0 + ty)) * W + (x0 + tx);
             cp16(smem_u32(sZ + m * SZ + ch * 8), dz + gv * COUT + ch * 8);
         }
-        for (int t = tid; t < TV * (CIN / 8); t += NTHR) {
-            const int m = t / (CIN / 8), ch = t % (CIN / 8);
-            const int tx = m % TX, ty = (m / TX) % TY, tz = m / (TX * TY);
-            const int gz = wrapi(z0 + tz + dzo, D), gy = wrapi(y0 + ty + dyo, H), gx = wrapi(x0 + tx + dxo, W);
+        for (int t = tid; t < HV * (CIN / 8); t += NTHR) {
+            const int hv = t / (CIN / 8), ch = t % (CIN / 8);
+            const int hx = hv % HX, hy = (hv / HX) % HY, hz = hv / (HX * HY);
+            const int gz = wrapi(z0 + hz - 1, D), gy = wrapi(y0 + hy - 1, H), gx = wrapi(x0 + hx - 1, W);
             const int64_t gv = ((int64_t)gz * H + gy) * W + gx;
-            cp16(smem_u32(sX + m * SXC + ch * 8), x + gv * CIN + ch * 8);
+            cp16(smem_u32(sX + hv * SXC + ch * 8), x + gv * CIN + ch * 8);
         }
         cp_commit();
         cp_wait_all();
         __syncthreads();
-        // k-slice of this warp: voxels [warp*32, warp*32 + 32), two k16 steps
-#pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-            const int v0 = warp * 32 + ks * 16;
+        for (int ks = 0; ks < TV / 16; ++ks) {
+            const int v0 = ks * 16;                      // one x-row of the tile
+            const int ty = (v0 / TX) % TY, tz = v0 / (TX * TY);
             // A = dz^T (m = co, k = v): transpose-load rows v of sZ
             unsigned a[MT][4];
 #pragma unroll
             for (int mt = 0; mt < MT; ++mt) {
-                // matrices: (co 0-7, v 0-7), (co 8-15, v 0-7), (co 0-7, v 8-15), (co 8-15, v 8-15)
                 const int q = lane >> 3, r = lane & 7;
                 const int vrow = v0 + r + 8 * (q >> 1);
                 const int cobase = mt * 16 + 8 * (q & 1);
                 ldsm_x4_t(smem_u32(sZ + vrow * SZ + cobase), a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
             }
-            // B = x_shifted (k = v, n = ci): transpose-load rows v of sX
+            // B = x shifted by the unit's offset (k = v, n = ci block)
+            const int rr = (lane & 7) + 8 * ((lane >> 3) & 1);
+            const int hvrow = ((tz + 1) * HY + (ty + 1)) * HX + rr + 1;
 #pragma unroll
-            for (int nt = 0; nt < NT; nt += 2) {
-                unsigned b0, b1, b2, b3;
-                const int q = lane >> 3, r = lane & 7;
-                const int vrow = v0 + r + 8 * (q & 1);
-                const int ci = nt * 8 + 8 * (q >> 1);
-                ldsm_x4_t(smem_u32(sX + vrow * SXC + ci), b0, b1, b2, b3);
+            for (int i = 0; i < UPW; ++i) {
+                const int u = warp + i * NWARP;
+                if (u < NU) {
+                    const int o = u / NT, nt = u % NT;
+                    const int dhv = ((o / 9 - 1) * HY + ((o / 3) % 3 - 1)) * HX + (o % 3 - 1);
+                    unsigned b0, b1;
+                    ldsm_x2_t(smem_u32(sX + (hvrow + dhv) * SXC + nt * 8), b0, b1);
 #pragma unroll
-                for (int mt = 0; mt < MT; ++mt) {
-                    mma16816(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
-                    if (nt + 1 < NT) mma16816(acc[mt][nt + 1], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b2, b3);
+                    for (int mt = 0; mt < MT; ++mt)
+                        mma16816(acc[i][mt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
                 }
             }
         }
     }
-    // fold the warps: each writes its COUT x CIN partial, then one pass sums
-    __syncthreads();
+    // rows co = mt*16 + lane/4 (+8), columns ci = nt*8 + 2(lane%4) + {0, 1}
 #pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
+    for (int i = 0; i < UPW; ++i) {
+        const int u = warp + i * NWARP;
+        if (u >= NU) continue;
+        const int o = u / NT, nt = u % NT;
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
+        for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int co = mt * 16 + (lane >> 2) + 8 * h;
                 const int ci = nt * 8 + 2 * (lane & 3);
-                if (co < COUT) {
-                    sRed[warp * COUT * CIN + co * CIN + ci] = acc[mt][nt][2 * h];
-                    sRed[warp * COUT * CIN + co * CIN + ci + 1] = acc[mt][nt][2 * h + 1];
-                }
+                float* dst = dW + ((int64_t)o * COUT + co) * CIN + ci;
+                atomicAdd(dst, acc[i][mt][2 * h]);
+                atomicAdd(dst + 1, acc[i][mt][2 * h + 1]);
             }
-    __syncthreads();
-    for (int t = tid; t < COUT * CIN; t += NTHR) {
-        float s = 0.f;
-        for (int w = 0; w < NWARP; ++w) s += sRed[w * COUT * CIN + t];
-        atomicAdd(&dW[(int64_t)o * COUT * CIN + t], s);
     }
 }
 
@@ -502,21 +504,23 @@ cudaError_t adam(float* p, const float* g, float* m, float* v, int n, float lr, 
 }
 
 template <int CIN, int COUT>
-static cudaError_t wgrad_t(const void* dz, const void* x, float* dW, int D, int H, int W, int nsplit, cudaStream_t st)
+static cudaError_t wgrad_t(const void* dz, const void* x, float* dW, int D, int H, int W, cudaStream_t st)
 {
     constexpr int SZ = COUT + 8, SXC = CIN + 8;
-    const int smem_tiles = (TV * SZ + TV * SXC) * 2;
-    const int smem_red = NWARP * COUT * CIN * 4;
-    const int smem = smem_tiles + smem_red;
+    const int smem = (TV * SZ + HV * SXC) * 2;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(wgrad_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    wgrad_kernel<CIN, COUT><<<27 * nsplit, NTHR, smem, st>>>(static_cast<const __nv_bfloat16*>(dz),
-                                                             static_cast<const __nv_bfloat16*>(x), dW, D, H, W,
-                                                             nsplit);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int ntiles = (D / TZ) * (H / TY) * (W / TX);
+    const int grid = ntiles < sms ? ntiles : sms;
+    wgrad_kernel<CIN, COUT><<<grid, NTHR, smem, st>>>(static_cast<const __nv_bfloat16*>(dz),
+                                                     static_cast<const __nv_bfloat16*>(x), dW, D, H, W);
     return cudaGetLastError();
 }
 
@@ -524,10 +528,10 @@ cudaError_t conv_wgrad(int cin, int cout, const void* dz, const void* x, float* 
                        cudaStream_t st)
 {
     if (D % TZ || H % TY || W % TX) return cudaErrorInvalidValue;
-    if (nsplit < 1) nsplit = 8;
-    if (cin == 16 && cout == 32) return wgrad_t<16, 32>(dz, x, dW, D, H, W, nsplit, st);
-    if (cin == 32 && cout == 32) return wgrad_t<32, 32>(dz, x, dW, D, H, W, nsplit, st);
-    if (cin == 32 && cout == 16) return wgrad_t<32, 16>(dz, x, dW, D, H, W, nsplit, st);
+    (void)nsplit;
+    if (cin == 16 && cout == 32) return wgrad_t<16, 32>(dz, x, dW, D, H, W, st);
+    if (cin == 32 && cout == 32) return wgrad_t<32, 32>(dz, x, dW, D, H, W, st);
+    if (cin == 32 && cout == 16) return wgrad_t<32, 16>(dz, x, dW, D, H, W, st);
     return cudaErrorInvalidValue;
 }
 

@@ -21,7 +21,6 @@ void set_unplanned_error(const std::string& msg);
 }
 
 namespace {
-constexpr int kMaxStagesE = 4096;
 constexpr int kChunk = 65536;            // cells per statistics chunk
 }  // namespace
 

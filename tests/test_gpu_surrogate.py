@@ -125,7 +125,13 @@ def test_gradients_match_oracle(rk):
         rlb, cosb = _stats(gb[:rco], grads[l][1])
         print(f"layer {l}: dW rel-L2 {rl2:.3e} cos {cos:.6f}; db rel-L2 {rlb:.3e} cos {cosb:.6f}")
         assert rl2 < 1e-1 and cos > 0.995, l
-        assert rlb < 1e-1 and cosb > 0.995, l
+        if l < 5:
+            assert rlb < 1e-1 and cosb > 0.995, l
+        else:
+            # a constant face flux has no divergence: the head's bias gradient
+            # is exactly zero (the adjoint telescopes); only rounding remains
+            assert np.max(np.abs(grads[l][1])) <= 1e-9 * np.max(np.abs(grads[l][0]))
+            assert np.max(np.abs(gb[:rco])) <= 1e-2 * np.max(np.abs(gw))
         # padded channels stay exactly zero
         assert np.all(gw[:, rco:, :] == 0) and np.all(gw[:, :, rci:] == 0)
     rk._lib.rkl_sur_destroy(sur)
