@@ -324,7 +324,7 @@ def run_ensemble(args):
     probs = []
     for sp in specs:
         shape = (sp["nz"], sp["ny"], sp["nx"])
-        probs.append((shape, dict(dx=(1.0 / sp["nx"], 1.0 / sp["ny"], 1.0 / sp["nz"]), kappa_model="spitzer",
+        probs.append((shape, dict(dx=(sp["h"],) * 3, kappa_model="spitzer",
                                   kappa_par0=sp["kappa_par0"], kappa_perp_ratio=1e-4)))
     ens = rk.Ensemble(probs)
     T_all = torch.empty(ens.offsets[-1], device="cuda")
@@ -335,7 +335,7 @@ def run_ensemble(args):
         Tv.copy_(torch.from_numpy(T.astype(np.float32)))
         bv.copy_(torch.from_numpy(b.astype(np.float32)))
         kmax = prm["kappa_par0"] * float(T.max()) ** 2.5 * (1 + 1e-4)
-        dts.append(sp["ratio"] * 0.5 / (kmax * (sp["nx"] ** 2 + sp["ny"] ** 2 + sp["nz"] ** 2)))
+        dts.append(sp["ratio"] * 0.5 / (kmax * 3.0 / sp["h"] ** 2))
     pers, nz, _ = ens.autotune(dts, T_all, b_all)
     for _ in range(args.warmup):
         ens.super_step(dts, T_all, b_all)

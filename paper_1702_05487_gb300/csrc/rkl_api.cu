@@ -155,7 +155,7 @@ rkl_status launch_stage(rkl_plan* p, const StageIO& io, double mu, double nu, do
                   aligned16(io.Yj) && aligned16(io.b);
         if (p->x2ok && al && (p->variant == 0 || p->variant == 3 || p->variant == 4))
             e = launch_stage_x2(p->cfg, p->gf, p->pf, io, cf, p->d_status, p->nzchunk,
-                                p->variant == 3 ? 2 : 3, st);
+                                p->variant == 4 ? 3 : 2, st);
         else if (p->fast && al && (p->variant == 0 || p->variant == 2))
             e = launch_stage_fast(p->cfg, p->gf, p->pf, io, cf, p->d_status, st);
         else
@@ -288,10 +288,10 @@ rkl_status collect_timing(rkl_plan* p)
 // FP64 {max, min, sum, status} of a device array into p->h_scal
 // (synchronises).  With take_status the device status word is read into
 // h_scal[3] and cleared; otherwise h_scal[3] = 0 and the word is kept.
-rkl_status stats(rkl_plan* p, const void* T, bool take_status = true)
+rkl_status stats(rkl_plan* p, const void* T, bool take_status = true, bool need_sum = true)
 {
     cudaError_t e = launch_stats(p->cfg.dtype, T, p->ncell, p->d_partials, p->d_scal,
-                                 take_status ? p->d_status : nullptr, p->stream);
+                                 take_status ? p->d_status : nullptr, p->stream, need_sum);
     if (e != cudaSuccess) return cuda_fail(p, e, "stats launch");
     RKL_CK(p, cudaMemcpyAsync(p->h_scal, p->d_scal, 4 * sizeof(double), cudaMemcpyDeviceToHost,
                               p->stream));
@@ -517,7 +517,7 @@ rkl_status rkl_dt_expl(rkl_plan* p, const void* T, double* dt_out)
     DeviceGuard dg(p->device);
     double Tmax = 1.0;
     if (p->phys.kappa_model == RKL_KAPPA_SPITZER) {
-        rkl_status st = stats(p, T);
+        rkl_status st = stats(p, T, true, false);
         if (st != RKL_OK) return st;
         Tmax = p->h_scal[0];
         if (!(p->h_scal[1] > 0.0) || !std::isfinite(Tmax))
@@ -600,7 +600,7 @@ rkl_status rkl_super_step(rkl_plan* p, double dt, void* T, const void* b, int* s
     double Tmax = 1.0;
     bool need_stats = p->phys.kappa_model == RKL_KAPPA_SPITZER || eb != nullptr;
     if (need_stats) {
-        st = stats(p, T);
+        st = stats(p, T, true, eb != nullptr);
         if (st != RKL_OK) return st;
         st = status_from_word(p, (unsigned)p->h_scal[3]);
         if (st != RKL_OK) return st;

@@ -232,33 +232,51 @@ __device__ __forceinline__ void acc(double v, double& mx, double& mn, double& sm
     sm += v;
 }
 
-template <typename R>
+// Max and min are exact in the data's own type; the sum (energy) is
+// accumulated in FP64 and only when asked for (FP64 arithmetic is scarce on
+// this GPU, and dt_expl needs only the extrema).
+template <typename R, bool SUM>
 __global__ void __launch_bounds__(256) stats_kernel(const R* __restrict__ T, int64_t n, double* partials)
 {
-    double mx = -INFINITY, mn = INFINITY, sm = 0.0;
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride)
-        acc<R>((double)T[c], mx, mn, sm);
+    R mx = -INFINITY, mn = INFINITY;
+    double sm = 0.0;
+    auto fold = [&](R v) {
+        mx = (v > mx || v != v) ? v : mx;
+        mn = (v < mn || v != v) ? v : mn;
+        if (SUM) sm += (double)v;
+    };
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (sizeof(R) == 4 && (n & 3) == 0 && (reinterpret_cast<uintptr_t>(T) & 15) == 0) {
+        const float4* T4 = reinterpret_cast<const float4*>(T);
+        for (int64_t c = t0; c < n / 4; c += stride) {
+            const float4 v = T4[c];
+            fold((R)v.x); fold((R)v.y); fold((R)v.z); fold((R)v.w);
+        }
+    } else {
+        for (int64_t c = t0; c < n; c += stride) fold(T[c]);
+    }
+    double dmx = (double)mx, dmn = (double)mn;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        double omx = __shfl_xor_sync(0xffffffffu, mx, o);
-        double omn = __shfl_xor_sync(0xffffffffu, mn, o);
-        mx = (omx > mx || omx != omx) ? omx : mx;
-        mn = (omn < mn || omn != omn) ? omn : mn;
-        sm += __shfl_xor_sync(0xffffffffu, sm, o);
+        double omx = __shfl_xor_sync(0xffffffffu, dmx, o);
+        double omn = __shfl_xor_sync(0xffffffffu, dmn, o);
+        dmx = (omx > dmx || omx != omx) ? omx : dmx;
+        dmn = (omn < dmn || omn != omn) ? omn : dmn;
+        if (SUM) sm += __shfl_xor_sync(0xffffffffu, sm, o);
     }
     __shared__ double s[3][8];
     int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) { s[0][w] = mx; s[1][w] = mn; s[2][w] = sm; }
+    if (l == 0) { s[0][w] = dmx; s[1][w] = dmn; s[2][w] = sm; }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int q = 1; q < 8; ++q) {
-            mx = (s[0][q] > mx || s[0][q] != s[0][q]) ? s[0][q] : mx;
-            mn = (s[1][q] < mn || s[1][q] != s[1][q]) ? s[1][q] : mn;
+            dmx = (s[0][q] > dmx || s[0][q] != s[0][q]) ? s[0][q] : dmx;
+            dmn = (s[1][q] < dmn || s[1][q] != s[1][q]) ? s[1][q] : dmn;
             sm += s[2][q];
         }
-        partials[3 * blockIdx.x + 0] = mx;
-        partials[3 * blockIdx.x + 1] = mn;
+        partials[3 * blockIdx.x + 0] = dmx;
+        partials[3 * blockIdx.x + 1] = dmn;
         partials[3 * blockIdx.x + 2] = sm;
     }
 }
@@ -308,12 +326,15 @@ cudaError_t launch_flux_generic(const LaunchCfg& c, const void* grid, const void
 }
 
 cudaError_t launch_stats(int dtype, const void* T, int64_t n, double* partials, double* out,
-                         unsigned* status, cudaStream_t st)
+                         unsigned* status, cudaStream_t st, bool need_sum)
 {
-    if (dtype == 1)
-        stats_kernel<double><<<kStatsBlocks, 256, 0, st>>>(static_cast<const double*>(T), n, partials);
-    else
-        stats_kernel<float><<<kStatsBlocks, 256, 0, st>>>(static_cast<const float*>(T), n, partials);
+    if (dtype == 1) {
+        if (need_sum) stats_kernel<double, true><<<kStatsBlocks, 256, 0, st>>>(static_cast<const double*>(T), n, partials);
+        else stats_kernel<double, false><<<kStatsBlocks, 256, 0, st>>>(static_cast<const double*>(T), n, partials);
+    } else {
+        if (need_sum) stats_kernel<float, true><<<kStatsBlocks, 256, 0, st>>>(static_cast<const float*>(T), n, partials);
+        else stats_kernel<float, false><<<kStatsBlocks, 256, 0, st>>>(static_cast<const float*>(T), n, partials);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     stats_final_kernel<<<1, 32, 0, st>>>(partials, kStatsBlocks, out, status);

@@ -56,7 +56,7 @@ cudaError_t launch_stage_x2(const LaunchCfg& c, const KGrid<float>& g, const KPh
 // followed by the status word (as a double), which is then cleared.
 constexpr int kStatsBlocks = 1216;   // 8 x 152 SMs
 cudaError_t launch_stats(int dtype, const void* T, int64_t n, double* partials, double* out,
-                         unsigned* status, cudaStream_t st);
+                         unsigned* status, cudaStream_t st, bool need_sum = true);
 
 // FP64 {max, min, sum} per problem of an ensemble (FP32 data), from a chunk
 // table: chunk c covers cells [cstart[c], cstart[c] + clen[c]); problem p

@@ -351,12 +351,47 @@ __device__ __forceinline__ void tile_x2(x2::Smem& sm, const KGrid<float>& g, con
     const bool in0 = (j0 + r < ny) && (i0 + c < nx);   // nx % 4 == 0: both cells or none
     int64_t cbase = ((int64_t)z0 * ny + (j0 + r)) * nx + (i0 + c);
 
+    // Plane q's divergence needs the y-face below each row (written by the
+    // warp below) and, for lane 0, the tile's left boundary face; both are
+    // read after the next plane's barrier, so each plane costs one barrier.
+    // Pending between the two: the known part of the divergence, T and the
+    // Y0 / Y_{j-2} / M(Y0) values of the pair, and its output offset.
+    float2 pend = bc2(0.f), pTo = bc2(0.f), py0 = bc2(0.f), pyjm2 = bc2(0.f), pmy0 = bc2(0.f);
+    int64_t pcb = 0;
+    auto finish = [&](int qp) {
+        const int par = qp & 1;
+        float2 div = sub2(pend, mul2(lds2(&sm.Fy[par][r][c]), idy2));
+        if (lane == 0) div.x -= sm.FxLo[par][r] * g.inv_dx[0];
+        const float2 M = mul2(bc2(-1.f), div);
+        if (in0) {
+            float2* out = reinterpret_cast<float2*>(a.out + pcb);
+            if (MODE == 0) {
+                *out = M;
+            } else if (MODE == 1) {
+                if (a.MY0out) *reinterpret_cast<float2*>(a.MY0out + pcb) = M;
+                const float2 y = fma2(bc2(cf.mt), M, pTo);
+                check_value<float, SP>(y.x, status);
+                check_value<float, SP>(y.y, status);
+                *out = y;
+            } else {
+                const float2 inc = fma2(bc2(cf.mu), sub2(pTo, py0),
+                                        fma2(bc2(cf.nu), sub2(pyjm2, py0), fma2(bc2(cf.mt), M, mul2(bc2(cf.gt), pmy0))));
+                const float2 y = add2(py0, inc);
+                check_value<float, SP>(y.x, status);
+                check_value<float, SP>(y.y, status);
+                *out = y;
+            }
+        }
+    };
+
     // one plane: cur holds plane q, nxt receives plane q + 1
     auto step = [&](int q, QZ& cur, QZ& nxt) {
+        cp_wait<0>();                      // bundle q + 1 has landed
+        __syncthreads();
+        // the slots of bundle q + 2 held planes no thread reads any more
         if (q + 2 <= nzc) load(q + 2, q + 2 < nzc);
         cp_commit();
-        cp_wait<1>();
-        __syncthreads();
+        if (q > 0) finish(q - 1);
 
         const float2 TmRp = make_float2(TmO.y, TmR);
         const QXY cx = read_qxy(sm, tslot(q), bslot(q), c, r, cur);
@@ -391,40 +426,19 @@ __device__ __forceinline__ void tile_x2(x2::Smem& sm, const KGrid<float>& g, con
         } else if (r == 1 && lane < TY) {
             sm.FxLo[par][lane] = low_xface<SP, SAT>(sm, g, p, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), lane);
         }
-        float2 y0v = bc2(0.f), yjm2v = bc2(0.f), my0v = bc2(0.f);
         if (MODE == 2) {
             const int ys = yslot(q);
-            y0v = lds2(&sm.Y[ys][0][r * TX + c]);
-            yjm2v = lds2(&sm.Y[ys][1][r * TX + c]);
-            my0v = lds2(&sm.Y[ys][2][r * TX + c]);
+            py0 = lds2(&sm.Y[ys][0][r * TX + c]);
+            pyjm2 = lds2(&sm.Y[ys][1][r * TX + c]);
+            pmy0 = lds2(&sm.Y[ys][2][r * TX + c]);
         }
         *reinterpret_cast<float2*>(&sm.Fy[par][r + 1][c]) = Fy;
         const float fxl = __shfl_up_sync(0xffffffffu, Fx.y, 1);
-        __syncthreads();
-
-        const float2 Fx_lo = make_float2(lane == 0 ? sm.FxLo[par][r] : fxl, Fx.x);
-        const float2 Fy_lo = lds2(&sm.Fy[par][r][c]);
-        const float2 div = fma2(sub2(Fx, Fx_lo), idx2, fma2(sub2(Fy, Fy_lo), idy2, mul2(sub2(Fz, Fz_lo), idz2)));
-        const float2 M = mul2(bc2(-1.f), div);
-        if (in0) {
-            float2* out = reinterpret_cast<float2*>(a.out + cbase);
-            if (MODE == 0) {
-                *out = M;
-            } else if (MODE == 1) {
-                if (a.MY0out) *reinterpret_cast<float2*>(a.MY0out + cbase) = M;
-                const float2 y = fma2(bc2(cf.mt), M, cur.To);
-                check_value<float, SP>(y.x, status);
-                check_value<float, SP>(y.y, status);
-                *out = y;
-            } else {
-                const float2 inc = fma2(bc2(cf.mu), sub2(cur.To, y0v),
-                                        fma2(bc2(cf.nu), sub2(yjm2v, y0v), fma2(bc2(cf.mt), M, mul2(bc2(cf.gt), my0v))));
-                const float2 y = add2(y0v, inc);
-                check_value<float, SP>(y.x, status);
-                check_value<float, SP>(y.y, status);
-                *out = y;
-            }
-        }
+        // divergence without the y-face below (and, on lane 0, the left face)
+        const float2 Fx_lo = make_float2(lane == 0 ? 0.f : fxl, Fx.x);
+        pend = fma2(sub2(Fx, Fx_lo), idx2, fma2(Fy, idy2, mul2(sub2(Fz, Fz_lo), idz2)));
+        pTo = cur.To;
+        pcb = cbase;
         cbase += g.plane;
         Fz_lo = Fz;
         TmO = cur.To;
@@ -439,6 +453,8 @@ __device__ __forceinline__ void tile_x2(x2::Smem& sm, const KGrid<float>& g, con
     }
     if (q < nzc) step(q, B, A);
     cp_wait<0>();
+    __syncthreads();
+    finish(nzc - 1);
     __syncthreads();
 }
 

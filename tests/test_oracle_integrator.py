@@ -238,3 +238,30 @@ def test_ring_undershoots_without_limiters(orc):
     assert T.min() < 10.0
     assert T.min() > 9.5
     assert T.max() < 12.0
+
+
+def test_anisotropic_cells_leave_the_stability_interval(orc):
+    """Eq. dt_exp bounds the spectrum by chi sum_d 1/dx_d^2, and RKL2 is
+    stable for eigenvalues on [-2/w_1, 0].  With arithmetic-mean transverse
+    gradients and a varying field the discrete operator is not symmetric;
+    on cubic cells its spectrum stays inside the RKL2 stability region at
+    dt = 320 dt_expl (s = 36), but on cells of aspect ratio 6 it does not
+    (max |R_s(tau lambda)| > 1): the batched workload therefore uses cubic
+    cells (its boxes are bricks of equal cells)."""
+    from numpy.polynomial import legendre as npleg
+    nx, ny, nz = 36, 6, 12
+    T, b = workloads.tangled_box(nx, ny, nz, 7)
+    out = {}
+    for cubic in (False, True):
+        dx = (1.0 / max(nx, ny, nz),) * 3 if cubic else (1.0 / nx, 1.0 / ny, 1.0 / nz)
+        P = Problem((nz, ny, nx), dx=dx, kappa_par0=1.0, kappa_perp_ratio=1e-4)
+        lam = np.linalg.eigvals(_matrix(orc, P, b))
+        ratio = 320.0
+        s = orc.num_stages(ratio)
+        tau = ratio * orc.dt_expl(P, np.ones(P.shape))
+        w1 = 4.0 / (s * s + s - 2)
+        bs = (s * s + s - 2) / (2.0 * s * (s + 1))
+        R = (1 - bs) + bs * npleg.legval(1 + w1 * tau * lam, [0] * s + [1])
+        out[cubic] = float(np.abs(R).max())
+    assert out[True] <= 1 + 1e-9
+    assert out[False] > 1.2

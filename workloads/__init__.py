@@ -165,12 +165,14 @@ ENSEMBLE_SIZES = (32, 48, 64, 96, 128, 192)
 def ensemble_specs(count: int = 64, seed: int = 4):
     """Seeded uneven periodic problems: per-axis sizes drawn from
     ENSEMBLE_SIZES, kappa_par0 uniform in [1e-3, 1e-1], dt/dt_expl uniform in
-    [20, 400].  Returns a list of dicts (nx, ny, nz, kappa_par0, ratio, seed)."""
+    [20, 400].  Cells are cubes of side h = 1 / max(nx, ny, nz) (the box is
+    an nx*ny*nz brick of them).  Returns a list of dicts (nx, ny, nz, h,
+    kappa_par0, ratio, seed)."""
     rng = np.random.default_rng(seed)
     out = []
     for p in range(count):
         nx, ny, nz = (int(v) for v in rng.choice(ENSEMBLE_SIZES, 3))
-        out.append(dict(nx=nx, ny=ny, nz=nz,
+        out.append(dict(nx=nx, ny=ny, nz=nz, h=1.0 / max(nx, ny, nz),
                         kappa_par0=float(rng.uniform(1e-3, 1e-1)),
                         ratio=float(rng.uniform(20.0, 400.0)),
                         seed=int(1000 + p)))
