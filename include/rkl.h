@@ -105,6 +105,43 @@ rkl_status rkl_num_stages(double ratio, int *s_out);
 rkl_status rkl_coeffs(int s, double *mu, double *nu, double *mut, double *gt);
 
 /*
+ * Super-time-stepping methods of Section 3.3.  RKL2 (Appendix A) is the
+ * default and the only second-order one; RKL1 and AAG-STS are the
+ * first-order methods the paper compares it with.  All three run through
+ * the same stage kernels with different coefficient tables:
+ *   RKL1  : stability polynomial P_s(1 + w_1 z), w_1 = 2/(s^2+s); Eq. RKL-s
+ *           gives dt/dt_expl = (s^2+s)/2, s = 1 + floor of its root;
+ *           stages Y_1 = Y_0 + w_1 tau M(Y_0), Y_j = mu_j Y_{j-1}
+ *           + nu_j Y_{j-2} + mu_j w_1 tau M(Y_{j-1}), mu_j = (2j-1)/j,
+ *           nu_j = -(j-1)/j (the Legendre recursion, Eq. recLegP).
+ *   AAG-STS (damping sts_nu in (0, 1)): N forward-Euler sub-steps tau_j =
+ *           dt_p / ((nu-1) cos((2j-1) pi/(2N)) + 1 + nu); N is the smallest
+ *           count whose super-step of Eq. AAG-STS reaches dt/dt_expl, and
+ *           dt_p = dt / gain(N) so that the sub-steps sum to dt.
+ * In the coefficient arrays of rkl_coeffs_method the stage update is
+ *   Y_j = mu_j Y_{j-1} + nu_j Y_{j-2} + (1 - mu_j - nu_j) Y_0
+ *         + mut_j tau M(Y_{j-1}) + gt_j tau M(Y_0)
+ * (Y_{-1} := Y_0 at j = 1), so RKL1 has gt = 0 and AAG-STS mu = 1, nu = 0,
+ * gt = 0, mut_j = tau_j / dt.
+ */
+enum { RKL_METHOD_RKL2 = 0, RKL_METHOD_RKL1 = 1, RKL_METHOD_STS = 2 };
+
+/*
+ * Stage count of a method for ratio = dt/dt_expl > 0 (sts_nu is read only by
+ * RKL_METHOD_STS and must lie in (0, 1)).  Host only, FP64.  Writes *s_out
+ * (>= 2 for RKL2, >= 1 otherwise).  RKL_ERR_INVALID_ARG past 4096 stages.
+ */
+rkl_status rkl_num_stages_method(int method, double ratio, double sts_nu, int *s_out);
+
+/*
+ * Coefficients of a method for s stages in the form stated above, FP64, as
+ * caller-owned host arrays of s + 1 doubles indexed by j (j = 0 unused).
+ * s in [2, 4096] for RKL2, [1, 4096] otherwise.  Host only.
+ */
+rkl_status rkl_coeffs_method(int method, int s, double sts_nu, double *mu, double *nu,
+                             double *mut, double *gt);
+
+/*
  * Create a plan for one grid and physics on a CUDA stream (cudaStream_t
  * passed as void*; NULL is the legacy default stream).  The plan allocates
  * its own device workspace: three stage buffers, M(Y_0), reduction scratch
@@ -146,7 +183,8 @@ rkl_status rkl_apply_M(rkl_plan *plan, const void *T, const void *b, void *MT);
  *   j >= 2: Yj = mu_j Yjm1 + nu_j Yjm2 + (1 - mu_j - nu_j) Y0
  *                + mut_j tau M(Yjm1) + gt_j tau MY0
  * j = 1 ignores Yjm1 and Yjm2.  s = 1 is accepted as forward Euler
- * (Yj = Y0 + tau M(Y0)).  For j >= 2 Yj may alias Y0 (Y0 is read only at
+ * (Yj = Y0 + tau M(Y0)).  The coefficients are those of the plan's method
+ * (rkl_plan_set_method; RKL2 by default).  For j >= 2 Yj may alias Y0 (Y0 is read only at
  * the cell being written) but no other input; for j = 1 Yj aliases nothing
  * (M reads Y0 at neighbouring cells).  Asynchronous.
  */
@@ -156,7 +194,8 @@ rkl_status rkl_stage(rkl_plan *plan, int j, int s, double dt, const void *b,
 
 /*
  * One RKL2 super-step of length dt applied in place to the device array T:
- * dt_expl from T (Eq. dt_exp), s = rkl_num_stages(dt/dt_expl), FP64
+ * dt_expl from T (Eq. dt_exp), s = rkl_num_stages(dt/dt_expl) (or
+ * rkl_num_stages_method for the plan's method), FP64
  * coefficients (rounded once to the grid dtype), then the s stages launched
  * as one cached CUDA graph.  Optionally the FP64 energy sum_c T_c dV before
  * and after (pass NULL to skip).  *s_used receives s (may be NULL).
@@ -169,7 +208,8 @@ rkl_status rkl_super_step(rkl_plan *plan, double dt, void *T, const void *b,
                           int *s_used, double *energy_before, double *energy_after);
 
 /*
- * As rkl_super_step, but s is given (s >= 2) instead of chosen from dt_expl;
+ * As rkl_super_step, but s is given (s >= 2; s >= 1 for RKL1 and AAG-STS)
+ * instead of chosen from dt_expl;
  * no synchronisation unless energies are requested.
  */
 rkl_status rkl_super_step_s(rkl_plan *plan, double dt, int s, void *T, const void *b,
@@ -191,6 +231,14 @@ rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
  * within FP32 rounding.
  */
 rkl_status rkl_plan_set_variant(rkl_plan *plan, int variant, int nzchunk);
+
+/*
+ * Selects the super-time-stepping method used by rkl_super_step,
+ * rkl_super_step_s and rkl_stage (RKL_METHOD_RKL2 by default; sts_nu is the
+ * AAG-STS damping, read only for RKL_METHOD_STS).  A plan created for RKL2
+ * keeps its workspace; the coefficient table is rebuilt at the next call.
+ */
+rkl_status rkl_plan_set_method(rkl_plan *plan, int method, double sts_nu);
 
 /*
  * Autotuner: times one super-step of length dt (s from dt / dt_expl(T))

@@ -100,6 +100,19 @@ def _load():
         lib.orc_rkl2_scalar.restype = ctypes.c_double
         lib.orc_set_threads.argtypes = [ctypes.c_int]
         lib.orc_set_threads.restype = ctypes.c_int
+        lib.orc_num_stages_rkl1.argtypes = [ctypes.c_double]
+        lib.orc_num_stages_rkl1.restype = ctypes.c_int
+        lib.orc_rkl1_super_step.argtypes = [P, ctypes.c_double, ctypes.c_int, dp, dp]
+        lib.orc_rkl1_super_step.restype = ctypes.c_int
+        lib.orc_rkl1_scalar.argtypes = [ctypes.c_int, ctypes.c_double]
+        lib.orc_rkl1_scalar.restype = ctypes.c_double
+        lib.orc_sts_gain.argtypes = [ctypes.c_int, ctypes.c_double]
+        lib.orc_sts_gain.restype = ctypes.c_double
+        lib.orc_num_stages_sts.argtypes = [ctypes.c_double, ctypes.c_double]
+        lib.orc_num_stages_sts.restype = ctypes.c_int
+        lib.orc_sts_substeps.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
+        lib.orc_sts_super_step.argtypes = [P, ctypes.c_double, ctypes.c_int, ctypes.c_double, dp, dp]
+        lib.orc_sts_super_step.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -265,3 +278,54 @@ def energy(P: Problem, T) -> float:
 def rkl2_scalar(s: int, z: float) -> float:
     """R_s(z): Eq. rkl2scheme applied to the scalar ODE dY/dt = lambda Y, z = tau lambda."""
     return _load().orc_rkl2_scalar(int(s), float(z))
+
+
+# --- first-order super-time-steppers (Section 3.3) -------------------------
+
+def num_stages_rkl1(ratio: float) -> int:
+    """Eq. RKL-s for RKL1 (dt/dt_expl = (s^2 + s)/2), s -> 1 + floor(s)."""
+    return _load().orc_num_stages_rkl1(float(ratio))
+
+
+def rkl1_super_step(P: Problem, T, b, dt: float, s: int = 0):
+    """One RKL1 super-step (Legendre recursion at 1 + w1 tau M, w1 = 2/(s^2+s))."""
+    T = _f64(T).copy().reshape(P.shape)
+    bb = _bfield(P, b)
+    if s <= 0:
+        s = num_stages_rkl1(dt / dt_expl(P, T))
+    c = P.cstruct()
+    _load().orc_rkl1_super_step(ctypes.byref(c), float(dt), int(s), _ptr(T), _ptr(bb))
+    return T, s
+
+
+def rkl1_scalar(s: int, z: float) -> float:
+    """RKL1 amplification factor R_s(z) for dY/dt = lambda Y, z = tau lambda."""
+    return _load().orc_rkl1_scalar(int(s), float(z))
+
+
+def sts_gain(N: int, nu: float) -> float:
+    """Eq. AAG-STS: super-step over explicit step for N sub-steps, damping nu."""
+    return _load().orc_sts_gain(int(N), float(nu))
+
+
+def num_stages_sts(ratio: float, nu: float) -> int:
+    """Smallest N with sts_gain(N, nu) >= ratio."""
+    return _load().orc_num_stages_sts(float(ratio), float(nu))
+
+
+def sts_substeps(N: int, nu: float, dt: float) -> np.ndarray:
+    """The N AAG-STS sub-steps of a super-step of length dt (they sum to dt)."""
+    tau = np.zeros(N)
+    _load().orc_sts_substeps(int(N), float(nu), float(dt), _ptr(tau))
+    return tau
+
+
+def sts_super_step(P: Problem, T, b, dt: float, nu: float = 1e-3, N: int = 0):
+    """One AAG-STS super-step: N forward-Euler sub-steps summing to dt."""
+    T = _f64(T).copy().reshape(P.shape)
+    bb = _bfield(P, b)
+    if N <= 0:
+        N = num_stages_sts(dt / dt_expl(P, T), nu)
+    c = P.cstruct()
+    _load().orc_sts_super_step(ctypes.byref(c), float(dt), int(N), float(nu), _ptr(T), _ptr(bb))
+    return T, N

@@ -351,6 +351,102 @@ double orc_rkl2_scalar(int s, double z)
     return Yjm1;
 }
 
+/* ------------------------------------------------------------------------
+ * First-order super-time-steppers of Section 3.3 (comparison methods).
+ *
+ * RKL1: the stability polynomial is P_s(1 + w1 z) with w1 = 2/(s^2 + s)
+ * (Eq. stabpara with a_s = 0, b_s = 1), and Eq. RKL-s gives
+ * dt / dt_expl = (s^2 + s)/2.  Writing the Legendre three-term recursion
+ * (Eq. recLegP) at x = 1 + w1 tau M gives the stages
+ *   Y_1 = Y_0 + w1 tau M(Y_0),
+ *   Y_j = mu_j Y_{j-1} + nu_j Y_{j-2} + mu_j w1 tau M(Y_{j-1}),
+ * with mu_j = (2j-1)/j and nu_j = -(j-1)/j.
+ * ---------------------------------------------------------------------- */
+
+/* Eq. RKL-s for RKL1 solved for s, then s -> 1 + floor(s) as for RKL2. */
+int orc_num_stages_rkl1(double ratio)
+{
+    double s = 0.5 * (-1.0 + sqrt(1.0 + 8.0 * ratio));
+    return 1 + (int)floor(s);
+}
+
+int orc_rkl1_super_step(const orc_problem *P, double dt, int s, double *T, const double *b)
+{
+    long N = ncell(P);
+    size_t bytes = sizeof(double) * N;
+    double w1 = 2.0 / ((double)s * s + s);
+    double *Yjm2 = malloc(bytes), *Yjm1 = malloc(bytes), *Yj = malloc(bytes), *MY = malloc(bytes);
+    memcpy(Yjm2, T, bytes);
+    orc_apply_M(P, Yjm2, b, MY);
+    for (long c = 0; c < N; ++c) Yjm1[c] = Yjm2[c] + w1 * dt * MY[c];
+    for (int j = 2; j <= s; ++j) {
+        double mu = (2.0 * j - 1.0) / j, nu = -((double)j - 1.0) / j;
+        orc_apply_M(P, Yjm1, b, MY);
+        for (long c = 0; c < N; ++c) Yj[c] = mu * Yjm1[c] + nu * Yjm2[c] + mu * w1 * dt * MY[c];
+        double *t = Yjm2; Yjm2 = Yjm1; Yjm1 = Yj; Yj = t;
+    }
+    memcpy(T, Yjm1, bytes);
+    free(Yjm2); free(Yjm1); free(Yj); free(MY);
+    return s;
+}
+
+/* Scalar RKL1 on dY/dt = lambda Y: returns R_s(z), z = tau lambda. */
+double orc_rkl1_scalar(int s, double z)
+{
+    double w1 = 2.0 / ((double)s * s + s);
+    double Yjm2 = 1.0, Yjm1 = 1.0 + w1 * z;
+    for (int j = 2; j <= s; ++j) {
+        double mu = (2.0 * j - 1.0) / j, nu = -((double)j - 1.0) / j;
+        double Yj = mu * Yjm1 + nu * Yjm2 + mu * w1 * z * Yjm1;
+        Yjm2 = Yjm1;
+        Yjm1 = Yj;
+    }
+    return Yjm1;
+}
+
+/* ------------------------------------------------------------------------
+ * AAG-STS (Alexiades, Amiez & Gremaud 1996): N forward-Euler sub-steps with
+ * damping nu,  tau_j = dt_p / ((nu - 1) cos((2j - 1) pi / (2N)) + 1 + nu),
+ * whose sum is the super-step of Eq. AAG-STS,
+ *   dt_h = dt_p N/(2 sqrt(nu)) [(1+sqrt nu)^(2N) - (1-sqrt nu)^(2N)]
+ *                             / [(1+sqrt nu)^(2N) + (1-sqrt nu)^(2N)].
+ * ---------------------------------------------------------------------- */
+
+/* Eq. AAG-STS: dt_h / dt_p for N sub-steps. */
+double orc_sts_gain(int N, double nu)
+{
+    double r = sqrt(nu);
+    double a = pow(1.0 + r, 2.0 * N), c = pow(1.0 - r, 2.0 * N);
+    return N / (2.0 * r) * (a - c) / (a + c);
+}
+
+/* Smallest N whose super-step reaches ratio * dt_p (Eq. AAG-STS). */
+int orc_num_stages_sts(double ratio, double nu)
+{
+    int N = 1;
+    while (orc_sts_gain(N, nu) < ratio && N < 100000) ++N;
+    return N;
+}
+
+/* The N sub-steps of a super-step of length dt: dt_p is set to
+ * dt / gain(N) (at most the explicit step) so that they sum to dt. */
+void orc_sts_substeps(int N, double nu, double dt, double *tau)
+{
+    double dtp = dt / orc_sts_gain(N, nu);
+    const double pi = 3.14159265358979323846;
+    for (int j = 1; j <= N; ++j)
+        tau[j - 1] = dtp / ((nu - 1.0) * cos((2.0 * j - 1.0) * pi / (2.0 * N)) + 1.0 + nu);
+}
+
+int orc_sts_super_step(const orc_problem *P, double dt, int N, double nu, double *T, const double *b)
+{
+    double *tau = malloc(sizeof(double) * N);
+    orc_sts_substeps(N, nu, dt, tau);
+    for (int j = 0; j < N; ++j) orc_euler_step(P, tau[j], T, b);
+    free(tau);
+    return N;
+}
+
 int orc_set_threads(int nthreads)
 {
 #ifdef _OPENMP

@@ -13,11 +13,11 @@ from __future__ import annotations
 from dataclasses import dataclass
 
 from ._lib import (  # noqa: F401  (the C ABI, same names)
-    RKL_DIRICHLET, RKL_F32, RKL_F64, RKL_KAPPA_CONST, RKL_KAPPA_SPITZER, RKL_OK, RKL_PERIODIC,
-    RklError, load, library_path, rkl_apply_M, rkl_coeffs, rkl_dt_expl, rkl_energy, rkl_flux,
-    rkl_grid, rkl_num_stages, rkl_phys, rkl_plan_check, rkl_plan_create, rkl_plan_destroy,
-    rkl_plan_set_timing, rkl_plan_set_variant, rkl_plan_timing, rkl_run_host, rkl_stage, rkl_super_step,
-    rkl_super_step_s,
+    RKL_DIRICHLET, RKL_F32, RKL_F64, RKL_KAPPA_CONST, RKL_KAPPA_SPITZER, RKL_METHOD_RKL1, RKL_METHOD_RKL2,
+    RKL_METHOD_STS, RKL_OK, RKL_PERIODIC, RklError, load, library_path, rkl_apply_M, rkl_coeffs,
+    rkl_coeffs_method, rkl_dt_expl, rkl_energy, rkl_flux, rkl_grid, rkl_num_stages, rkl_num_stages_method,
+    rkl_phys, rkl_plan_check, rkl_plan_create, rkl_plan_destroy, rkl_plan_set_method, rkl_plan_set_timing,
+    rkl_plan_set_variant, rkl_plan_timing, rkl_run_host, rkl_stage, rkl_super_step, rkl_super_step_s,
 )
 
 __all__ = ["Plan", "make_grid", "make_phys", "RklError"]
@@ -110,6 +110,11 @@ class Plan:
 
     def set_variant(self, variant, nzchunk=0):
         rkl_plan_set_variant(self.handle, variant, nzchunk)
+
+    def set_method(self, method, sts_nu=1e-3):
+        """"rkl2" (default), "rkl1" or "sts" (AAG-STS with damping sts_nu)."""
+        m = {"rkl2": RKL_METHOD_RKL2, "rkl1": RKL_METHOD_RKL1, "sts": RKL_METHOD_STS}.get(method, method)
+        rkl_plan_set_method(self.handle, m, sts_nu)
 
     def autotune(self, dt, T, b):
         from . import _lib

@@ -25,6 +25,7 @@ RKL_ERR_NOMEM = 7
 
 RKL_PERIODIC, RKL_DIRICHLET = 0, 1
 RKL_F32, RKL_F64 = 0, 1
+RKL_METHOD_RKL2, RKL_METHOD_RKL1, RKL_METHOD_STS = 0, 1, 2
 RKL_KAPPA_CONST, RKL_KAPPA_SPITZER = 0, 1
 
 
@@ -56,6 +57,9 @@ SIGNATURES = {
     "rkl_last_error": (ctypes.c_char_p, [_vp]),
     "rkl_num_stages": (ctypes.c_int, [ctypes.c_double, _ip]),
     "rkl_coeffs": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp, _dp]),
+    "rkl_num_stages_method": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, _ip]),
+    "rkl_coeffs_method": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp]),
+    "rkl_plan_set_method": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double]),
     "rkl_plan_create": (ctypes.c_int, [ctypes.POINTER(rkl_grid), ctypes.POINTER(rkl_phys), _vp,
                                        ctypes.POINTER(_vp)]),
     "rkl_plan_destroy": (ctypes.c_int, [_vp]),
@@ -158,6 +162,23 @@ def rkl_coeffs(s: int):
     arrs = [np.zeros(s + 1) for _ in range(4)]
     _check(load().rkl_coeffs(int(s), *[a.ctypes.data_as(_dp) for a in arrs]))
     return tuple(arrs)
+
+
+def rkl_num_stages_method(method: int, ratio: float, sts_nu: float = 1e-3) -> int:
+    s = ctypes.c_int(0)
+    _check(load().rkl_num_stages_method(int(method), float(ratio), float(sts_nu), ctypes.byref(s)))
+    return s.value
+
+
+def rkl_coeffs_method(method: int, s: int, sts_nu: float = 1e-3):
+    import numpy as np
+    arrs = [np.zeros(s + 1) for _ in range(4)]
+    _check(load().rkl_coeffs_method(int(method), int(s), float(sts_nu), *[a.ctypes.data_as(_dp) for a in arrs]))
+    return tuple(arrs)
+
+
+def rkl_plan_set_method(plan, method: int, sts_nu: float = 1e-3):
+    _check(load().rkl_plan_set_method(plan, int(method), float(sts_nu)), plan)
 
 
 def rkl_plan_create(grid: rkl_grid, phys: rkl_phys, stream=None):

@@ -56,6 +56,8 @@ struct rkl_plan {
     double* h_scal = nullptr;          // pinned mirror
     unsigned* d_status = nullptr;
 
+    int method = RKL_METHOD_RKL2;      // super-time-stepping method (Section 3.3)
+    double sts_nu = 1e-3;              // AAG-STS damping
     void* d_coef = nullptr;            // [(kMaxStages + 1) * 4] of the grid dtype
     void* h_coef = nullptr;            // pinned [kCoefRing][(kMaxStages + 1) * 4]
     cudaEvent_t coef_ev[kCoefRing] = {};
@@ -137,6 +139,65 @@ void host_coeffs(int s, double* mu, double* nu, double* mut, double* gt)
     }
 }
 
+// Eq. AAG-STS: super-step over explicit step for N sub-steps, damping nu.
+double sts_gain(int N, double nu)
+{
+    const double r = std::sqrt(nu);
+    const double a = std::pow(1.0 + r, 2.0 * N), c = std::pow(1.0 - r, 2.0 * N);
+    return N / (2.0 * r) * (a - c) / (a + c);
+}
+
+bool method_ok(int method, double nu)
+{
+    if (method == RKL_METHOD_RKL2 || method == RKL_METHOD_RKL1) return true;
+    return method == RKL_METHOD_STS && nu > 0.0 && nu < 1.0;
+}
+
+// Stage count for dt/dt_expl = ratio (Eq. RKL-s for RKL2 and RKL1, Eq.
+// AAG-STS for AAG-STS); 0 when more than kMaxStages would be needed.
+int method_stages(int method, double ratio, double nu)
+{
+    if (method == RKL_METHOD_STS) {
+        int N = 1;
+        while (sts_gain(N, nu) < ratio) {
+            if (++N > kMaxStages) return 0;
+        }
+        return N;
+    }
+    const double x = method == RKL_METHOD_RKL1 ? 0.5 * (-1.0 + std::sqrt(1.0 + 8.0 * ratio))
+                                               : 0.5 * (-1.0 + std::sqrt(9.0 + 16.0 * ratio));
+    if (x + 1.0 > (double)kMaxStages) return 0;
+    return 1 + (int)std::floor(x);
+}
+
+// Coefficients of a method in the common stage form
+//   Y_j = mu_j Y_{j-1} + nu_j Y_{j-2} + (1 - mu_j - nu_j) Y_0 + mut_j tau M(Y_{j-1}) + gt_j tau M(Y_0).
+void method_coeffs(int method, int s, double sts_nu, double* mu, double* nu, double* mut, double* gt)
+{
+    if (method == RKL_METHOD_RKL2) {
+        host_coeffs(s, mu, nu, mut, gt);
+        return;
+    }
+    for (int j = 0; j <= s; ++j) mu[j] = nu[j] = mut[j] = gt[j] = 0.0;
+    if (method == RKL_METHOD_RKL1) {
+        const double w1 = 2.0 / ((double)s * s + s);
+        mut[1] = w1;
+        for (int j = 2; j <= s; ++j) {
+            mu[j] = (2.0 * j - 1.0) / j;
+            nu[j] = -((double)j - 1.0) / j;
+            mut[j] = mu[j] * w1;
+        }
+        return;
+    }
+    // AAG-STS: sub-steps of a unit super-step (dt_p = 1 / gain(s))
+    const double dtp = 1.0 / sts_gain(s, sts_nu);
+    const double pi = 3.14159265358979323846;
+    for (int j = 1; j <= s; ++j) {
+        mu[j] = j >= 2 ? 1.0 : 0.0;
+        mut[j] = dtp / ((sts_nu - 1.0) * std::cos((2.0 * j - 1.0) * pi / (2.0 * s)) + 1.0 + sts_nu);
+    }
+}
+
 rkl_status check_plan(rkl_plan* p)
 {
     if (!p) return RKL_ERR_INVALID_ARG;
@@ -183,6 +244,10 @@ rkl_status enqueue_stages(rkl_plan* p, int s, void* T, const void* b, bool with_
     io.Yj = p->ybuf[0];
     rkl_status st = launch_stage(p, io, 0, 0, 0, 0, cs);
     if (st != RKL_OK) return st;
+    if (s == 1) {                      // single forward-Euler stage (RKL1, AAG-STS)
+        RKL_CK(p, cudaMemcpyAsync(T, p->ybuf[0], (size_t)p->ncell * p->esize, cudaMemcpyDeviceToDevice, cs));
+        return RKL_OK;
+    }
     if (with_events) RKL_CK(p, cudaEventRecordWithFlags(p->ev_a, cs, cudaEventRecordExternal));
     for (int j = 2; j <= s; ++j) {
         StageIO q{};
@@ -205,7 +270,7 @@ rkl_status enqueue_stages(rkl_plan* p, int s, void* T, const void* b, bool with_
 rkl_status upload_coeffs(rkl_plan* p, int s, double dt)
 {
     std::vector<double> mu(s + 1), nu(s + 1), mut(s + 1), gt(s + 1);
-    host_coeffs(s, mu.data(), nu.data(), mut.data(), gt.data());
+    method_coeffs(p->method, s, p->sts_nu, mu.data(), nu.data(), mut.data(), gt.data());
     int slot = p->coef_slot;
     p->coef_slot = (p->coef_slot + 1) % kCoefRing;
     RKL_CK(p, cudaEventSynchronize(p->coef_ev[slot]));
@@ -330,7 +395,7 @@ rkl_status run_super_step(rkl_plan* p, double dt, int s, void* T, const void* b,
     st = get_graph(p, s, T, b, &exec);
     if (st != RKL_OK) return st;
     RKL_CK(p, cudaGraphLaunch(exec, p->stream));
-    if (p->timing) {
+    if (p->timing && s >= 2) {         // events bracket stages 2..s
         p->timing_pending = true;
         p->pending_launches = s - 1;
     }
@@ -392,6 +457,32 @@ rkl_status rkl_coeffs(int s, double* mu, double* nu, double* mut, double* gt)
 {
     if (s < 2 || s > kMaxStages || !mu || !nu || !mut || !gt) return RKL_ERR_INVALID_ARG;
     host_coeffs(s, mu, nu, mut, gt);
+    return RKL_OK;
+}
+
+rkl_status rkl_num_stages_method(int method, double ratio, double sts_nu, int* s_out)
+{
+    if (!s_out || !std::isfinite(ratio) || ratio <= 0.0 || !method_ok(method, sts_nu)) return RKL_ERR_INVALID_ARG;
+    const int s = method_stages(method, ratio, sts_nu);
+    if (s == 0) return RKL_ERR_INVALID_ARG;
+    *s_out = s;
+    return RKL_OK;
+}
+
+rkl_status rkl_coeffs_method(int method, int s, double sts_nu, double* mu, double* nu, double* mut, double* gt)
+{
+    if (!method_ok(method, sts_nu) || !mu || !nu || !mut || !gt) return RKL_ERR_INVALID_ARG;
+    if (s < (method == RKL_METHOD_RKL2 ? 2 : 1) || s > kMaxStages) return RKL_ERR_INVALID_ARG;
+    method_coeffs(method, s, sts_nu, mu, nu, mut, gt);
+    return RKL_OK;
+}
+
+rkl_status rkl_plan_set_method(rkl_plan* p, int method, double sts_nu)
+{
+    if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
+    if (!method_ok(method, sts_nu)) return fail(p, RKL_ERR_INVALID_ARG, "unknown method or sts_nu outside (0, 1)");
+    p->method = method;
+    if (method == RKL_METHOD_STS) p->sts_nu = sts_nu;
     return RKL_OK;
 }
 
@@ -465,8 +556,11 @@ rkl_status rkl_plan_create(const rkl_grid* grid, const rkl_phys* phys, void* cud
     for (int k = 0; k < 3; ++k)
         if ((e = cudaMalloc(&p->ybuf[k], bytes)) != cudaSuccess) return bail(e, "cudaMalloc(stage buffer)");
     if ((e = cudaMalloc(&p->my0, bytes)) != cudaSuccess) return bail(e, "cudaMalloc(MY0)");
-    if ((e = cudaMalloc(&p->d_partials, sizeof(double) * 3 * kStatsBlocks)) != cudaSuccess)
+    // partials of the statistics pass, then its block ticket counter (zeroed)
+    if ((e = cudaMalloc(&p->d_partials, sizeof(double) * (3 * kStatsBlocks + 1))) != cudaSuccess)
         return bail(e, "cudaMalloc(partials)");
+    if ((e = cudaMemsetAsync(p->d_partials, 0, sizeof(double) * (3 * kStatsBlocks + 1), p->stream)) != cudaSuccess)
+        return bail(e, "cudaMemset(partials)");
     if ((e = cudaMalloc(&p->d_scal, sizeof(double) * 4)) != cudaSuccess) return bail(e, "cudaMalloc(scalars)");
     if ((e = cudaMallocHost(&p->h_scal, sizeof(double) * 4)) != cudaSuccess) return bail(e, "cudaMallocHost");
     if ((e = cudaMalloc(&p->d_status, sizeof(unsigned))) != cudaSuccess) return bail(e, "cudaMalloc(status)");
@@ -583,7 +677,7 @@ rkl_status rkl_stage(rkl_plan* p, int j, int s, double dt, const void* b, const 
         return launch_stage(p, io, 0, 0, dt, 0, p->stream);
     }
     std::vector<double> mu(s + 1), nu(s + 1), mut(s + 1), gt(s + 1);
-    host_coeffs(s, mu.data(), nu.data(), mut.data(), gt.data());
+    method_coeffs(p->method, s, p->sts_nu, mu.data(), nu.data(), mut.data(), gt.data());
     io.mode = j == 1 ? 1 : 2;
     return launch_stage(p, io, mu[j], nu[j], mut[j] * dt, gt[j] * dt, p->stream);
 }
@@ -612,8 +706,8 @@ rkl_status rkl_super_step(rkl_plan* p, double dt, void* T, const void* b, int* s
         if (eb) *eb = p->h_scal[2] * cell_volume(p->grid);
     }
     double dte = dt_expl_from_max(p, Tmax);
-    int s = 0;
-    if (rkl_num_stages(dt / dte, &s) != RKL_OK) return fail(p, RKL_ERR_INVALID_ARG, "dt/dt_expl needs more than 4096 stages");
+    const int s = method_stages(p->method, dt / dte, p->sts_nu);
+    if (s == 0) return fail(p, RKL_ERR_INVALID_ARG, "dt/dt_expl needs more than 4096 stages");
     if (s_used) *s_used = s;
     return run_super_step(p, dt, s, T, b, nullptr, ea);
 }
@@ -622,7 +716,8 @@ rkl_status rkl_super_step_s(rkl_plan* p, double dt, int s, void* T, const void* 
 {
     if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(p, RKL_ERR_INVALID_ARG, "dt must be finite and > 0");
-    if (s < 2 || s > kMaxStages) return fail(p, RKL_ERR_INVALID_ARG, "need 2 <= s <= 4096");
+    const int smin = p->method == RKL_METHOD_RKL2 ? 2 : 1;
+    if (s < smin || s > kMaxStages) return fail(p, RKL_ERR_INVALID_ARG, "need 2 <= s <= 4096 (1 <= s for RKL1, AAG-STS)");
     if (!T || !b) return fail(p, RKL_ERR_INVALID_ARG, "null argument");
     if (!aligned16(T) || !aligned16(b)) return fail(p, RKL_ERR_INVALID_ARG, "T and b must be 16-byte aligned");
     DeviceGuard dg(p->device);
@@ -661,8 +756,8 @@ rkl_status rkl_plan_autotune(rkl_plan* p, double dt, const void* T, const void* 
     double dte = 0.0;
     rkl_status st = rkl_dt_expl(p, T, &dte);
     if (st != RKL_OK) return st;
-    int s = 0;
-    if (rkl_num_stages(dt / dte, &s) != RKL_OK) return fail(p, RKL_ERR_INVALID_ARG, "dt/dt_expl too large");
+    const int s = method_stages(p->method, dt / dte, p->sts_nu);
+    if (s == 0) return fail(p, RKL_ERR_INVALID_ARG, "dt/dt_expl too large");
     struct Cand { int v, nz; };
     std::vector<Cand> cands = {{1, 0}};
     if (p->fast) cands.push_back({2, 0});

@@ -234,9 +234,40 @@ __device__ __forceinline__ void acc(double v, double& mx, double& mn, double& sm
 
 // Max and min are exact in the data's own type; the sum (energy) is
 // accumulated in FP64 and only when asked for (FP64 arithmetic is scarce on
-// this GPU, and dt_expl needs only the extrema).
+// this GPU, and dt_expl needs only the extrema).  Each block leaves its
+// partial {max, min, sum}; the block that finishes last (ticket counter at
+// partials[3 * gridDim.x], reset by that block) folds all partials in a
+// fixed order, so the result does not depend on which block is last.
+__device__ __forceinline__ void fold_mm(double vmx, double vmn, double& mx, double& mn)
+{
+    mx = (vmx > mx || vmx != vmx) ? vmx : mx;
+    mn = (vmn < mn || vmn != vmn) ? vmn : mn;
+}
+
+template <bool SUM>
+__device__ __forceinline__ void block_fold(double& mx, double& mn, double& sm)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fold_mm(__shfl_xor_sync(0xffffffffu, mx, o), __shfl_xor_sync(0xffffffffu, mn, o), mx, mn);
+        if (SUM) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+    }
+    __shared__ double s[3][8];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) { s[0][w] = mx; s[1][w] = mn; s[2][w] = sm; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < 8; ++q) {
+            fold_mm(s[0][q], s[1][q], mx, mn);
+            sm += s[2][q];
+        }
+    }
+}
+
 template <typename R, bool SUM>
-__global__ void __launch_bounds__(256) stats_kernel(const R* __restrict__ T, int64_t n, double* partials)
+__global__ void __launch_bounds__(256) stats_kernel(const R* __restrict__ T, int64_t n, double* partials,
+                                                    double* out, unsigned* status)
 {
     R mx = -INFINITY, mn = INFINITY;
     double sm = 0.0;
@@ -257,55 +288,33 @@ __global__ void __launch_bounds__(256) stats_kernel(const R* __restrict__ T, int
         for (int64_t c = t0; c < n; c += stride) fold(T[c]);
     }
     double dmx = (double)mx, dmn = (double)mn;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        double omx = __shfl_xor_sync(0xffffffffu, dmx, o);
-        double omn = __shfl_xor_sync(0xffffffffu, dmn, o);
-        dmx = (omx > dmx || omx != omx) ? omx : dmx;
-        dmn = (omn < dmn || omn != omn) ? omn : dmn;
-        if (SUM) sm += __shfl_xor_sync(0xffffffffu, sm, o);
-    }
-    __shared__ double s[3][8];
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) { s[0][w] = dmx; s[1][w] = dmn; s[2][w] = sm; }
-    __syncthreads();
+    block_fold<SUM>(dmx, dmn, sm);
+    __shared__ bool last;
+    unsigned* ticket = reinterpret_cast<unsigned*>(partials + 3 * gridDim.x);
     if (threadIdx.x == 0) {
-        for (int q = 1; q < 8; ++q) {
-            dmx = (s[0][q] > dmx || s[0][q] != s[0][q]) ? s[0][q] : dmx;
-            dmn = (s[1][q] < dmn || s[1][q] != s[1][q]) ? s[1][q] : dmn;
-            sm += s[2][q];
-        }
         partials[3 * blockIdx.x + 0] = dmx;
         partials[3 * blockIdx.x + 1] = dmn;
         partials[3 * blockIdx.x + 2] = sm;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
-}
-
-__global__ void __launch_bounds__(32) stats_final_kernel(const double* partials, int nblk, double* out,
-                                                         unsigned* status)
-{
-    double mx = -INFINITY, mn = INFINITY, sm = 0.0;
-    for (int q = threadIdx.x; q < nblk; q += 32) {
-        double a = partials[3 * q], b = partials[3 * q + 1];
-        mx = (a > mx || a != a) ? a : mx;
-        mn = (b < mn || b != b) ? b : mn;
-        sm += partials[3 * q + 2];
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    dmx = -INFINITY; dmn = INFINITY; sm = 0.0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) {
+        fold_mm(__ldcg(&partials[3 * q]), __ldcg(&partials[3 * q + 1]), dmx, dmn);
+        sm += __ldcg(&partials[3 * q + 2]);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        double omx = __shfl_xor_sync(0xffffffffu, mx, o);
-        double omn = __shfl_xor_sync(0xffffffffu, mn, o);
-        mx = (omx > mx || omx != omx) ? omx : mx;
-        mn = (omn < mn || omn != omn) ? omn : mn;
-        sm += __shfl_xor_sync(0xffffffffu, sm, o);
-    }
+    block_fold<SUM>(dmx, dmn, sm);
     if (threadIdx.x == 0) {
-        out[0] = mx;
-        out[1] = mn;
+        out[0] = dmx;
+        out[1] = dmn;
         out[2] = sm;
         unsigned st = status ? *status : 0u;
         out[3] = (double)st;
         if (status) *status = 0u;
+        *ticket = 0u;
     }
 }
 
@@ -328,16 +337,16 @@ cudaError_t launch_flux_generic(const LaunchCfg& c, const void* grid, const void
 cudaError_t launch_stats(int dtype, const void* T, int64_t n, double* partials, double* out,
                          unsigned* status, cudaStream_t st, bool need_sum)
 {
+    const int nb = kStatsBlocks;
     if (dtype == 1) {
-        if (need_sum) stats_kernel<double, true><<<kStatsBlocks, 256, 0, st>>>(static_cast<const double*>(T), n, partials);
-        else stats_kernel<double, false><<<kStatsBlocks, 256, 0, st>>>(static_cast<const double*>(T), n, partials);
+        const double* Td = static_cast<const double*>(T);
+        if (need_sum) stats_kernel<double, true><<<nb, 256, 0, st>>>(Td, n, partials, out, status);
+        else stats_kernel<double, false><<<nb, 256, 0, st>>>(Td, n, partials, out, status);
     } else {
-        if (need_sum) stats_kernel<float, true><<<kStatsBlocks, 256, 0, st>>>(static_cast<const float*>(T), n, partials);
-        else stats_kernel<float, false><<<kStatsBlocks, 256, 0, st>>>(static_cast<const float*>(T), n, partials);
+        const float* Tf = static_cast<const float*>(T);
+        if (need_sum) stats_kernel<float, true><<<nb, 256, 0, st>>>(Tf, n, partials, out, status);
+        else stats_kernel<float, false><<<nb, 256, 0, st>>>(Tf, n, partials, out, status);
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    stats_final_kernel<<<1, 32, 0, st>>>(partials, kStatsBlocks, out, status);
     return cudaGetLastError();
 }
 

@@ -52,7 +52,8 @@ cudaError_t launch_stage_x2(const LaunchCfg& c, const KGrid<float>& g, const KPh
                             cudaStream_t st);
 
 // FP64 statistics of a grid array: max, min and sum (fixed-order, deterministic).
-// partials must hold 3 * kStatsBlocks doubles; out receives {max, min, sum}
+// partials must hold 3 * kStatsBlocks + 1 doubles, the last one zero before
+// the first call (a ticket counter the pass leaves at zero); out receives {max, min, sum}
 // followed by the status word (as a double), which is then cleared.
 constexpr int kStatsBlocks = 1216;   // 8 x 152 SMs
 cudaError_t launch_stats(int dtype, const void* T, int64_t n, double* partials, double* out,

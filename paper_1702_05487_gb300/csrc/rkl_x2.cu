@@ -107,8 +107,8 @@ constexpr int kY = 3 * TY * (TX / 4);        // 384
 constexpr int kTasks = kTB + kY;             // 1104
 constexpr int kSlots = (kTasks + NTHREADS - 1) / NTHREADS;   // 5
 
-template <int MODE>
-__device__ __forceinline__ Task make_task(const Smem& sm, const KGrid<float>& g, const FastArgs& a, int t, int i0,
+template <int MODE, class SM>
+__device__ __forceinline__ Task make_task(const SM& sm, const KGrid<float>& g, const FastArgs& a, int t, int i0,
                                           int j0)
 {
     Task k{nullptr, 0u, 0u};
@@ -211,7 +211,8 @@ struct QXY {
     float2 bU[3];     // b one row up
 };
 
-__device__ __forceinline__ QZ read_qz(const Smem& sm, int ts, int bs, int c, int r)
+template <class SM>
+__device__ __forceinline__ QZ read_qz(const SM& sm, int ts, int bs, int c, int r)
 {
     const float* T = sm.T[ts];
     QZ q;
@@ -230,7 +231,8 @@ __device__ __forceinline__ QZ read_qz(const Smem& sm, int ts, int bs, int c, int
     return q;
 }
 
-__device__ __forceinline__ QXY read_qxy(const Smem& sm, int ts, int bs, int c, int r, const QZ& z)
+template <class SM>
+__device__ __forceinline__ QXY read_qxy(const SM& sm, int ts, int bs, int c, int r, const QZ& z)
 {
     const float* T = sm.T[ts];
     QXY q;
@@ -252,8 +254,8 @@ __device__ __forceinline__ QXY read_qxy(const Smem& sm, int ts, int bs, int c, i
 // Boundary faces of the tile, straight from smem: the y-face pair between
 // row -1 and row 0 at columns (c, c+1), and the x-face between columns -1
 // and 0 at row r.
-template <bool SP, bool SAT>
-__device__ __forceinline__ float2 low_yface2(const Smem& sm, const KGrid<float>& g, const KPhys<float>& p, int tm,
+template <bool SP, bool SAT, class SM>
+__device__ __forceinline__ float2 low_yface2(const SM& sm, const KGrid<float>& g, const KPhys<float>& p, int tm,
                                              int tc, int tp, int bs, int c)
 {
     const float* T = sm.T[tc];
@@ -272,8 +274,8 @@ __device__ __forceinline__ float2 low_yface2(const Smem& sm, const KGrid<float>&
                           mul2(add2(gzL, gzR), bc2(g.inv_4dx[2])), b[1], b[0], b[2], p);
 }
 
-template <bool SP, bool SAT>
-__device__ __forceinline__ float low_xface(const Smem& sm, const KGrid<float>& g, const KPhys<float>& p, int tm,
+template <bool SP, bool SAT, class SM>
+__device__ __forceinline__ float low_xface(const SM& sm, const KGrid<float>& g, const KPhys<float>& p, int tm,
                                            int tc, int tp, int bs, int r)
 {
     const float* T = sm.T[tc];
@@ -294,8 +296,8 @@ __device__ __forceinline__ float low_xface(const Smem& sm, const KGrid<float>& g
 // --------------------------------------------------------------------------
 // one tile: columns [i0, i0 + 64), rows [j0, j0 + 8), planes [z0, z0 + nzc)
 
-template <bool SP, bool SAT, int MODE>
-__device__ __forceinline__ void tile_x2(x2::Smem& sm, const KGrid<float>& g, const KPhys<float>& p,
+template <bool SP, bool SAT, int MODE, int PD>
+__device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g, const KPhys<float>& p,
                                         const x2::FastArgs& a, KCoef<float> cf, unsigned* status, int i0, int j0,
                                         int z0, int nzc)
 {
@@ -315,25 +317,42 @@ __device__ __forceinline__ void tile_x2(x2::Smem& sm, const KGrid<float>& g, con
 #pragma unroll
     for (int s = 0; s < kSlots; ++s) tk[s] = make_task<MODE>(sm, g, a, tid + s * NTHREADS, i0, j0);
 
-    auto tslot = [](int q) { return (q + 1) & 3; };
-    auto bslot = [](int q) { return (q + 1) % 3; };
-    auto yslot = [](int q) { return (q + 3) % 3; };
+    using SM = SmemT<PD>;
+    auto tslot = [](int q) { return (q + 1) % SM::NT; };
+    auto bslot = [](int q) { return (q + 1) % SM::NB; };
+    auto yslot = [](int q) { return (q + SM::NY) % SM::NY; };
+    // Periodic grids have no ghost or broadcast tasks: every task is one
+    // 16-byte copy, issued without branches (the slot offset selected by
+    // the task's array, invalid and skipped-Y tasks predicated off).
+    const bool plain = g.bc == 0;
     auto load = [&](int q, bool withY) {
         const PlaneOff po = plane_offsets(g, z0 + q);
         const unsigned ts = (unsigned)(tslot(q) * PLANE * 4);
         const unsigned bs = (unsigned)(bslot(q) * 3 * PLANE * 4);
         const unsigned ys = (unsigned)(yslot(q) * 3 * TY * TX * 4);
+        if (plain) {
 #pragma unroll
-        for (int s = 0; s < kSlots; ++s) issue(tk[s], po, ts, bs, ys, withY, g.bcv);
+            for (int s = 0; s < kSlots; ++s) {
+                const unsigned f = tk[s].flags;
+                const unsigned off = (f & TK_T) ? ts : ((f & TK_Y) ? ys : bs);
+                const bool on = (f & TK_VALID) && (withY || !(f & TK_Y));
+                if (on) cp16(tk[s].dst + off, tk[s].src + po.t);
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < kSlots; ++s) issue(tk[s], po, ts, bs, ys, withY, g.bcv);
+        }
     };
 
+    // planes -1 .. PD in flight; -1 and 0 must land before the first reads
     load(-1, false);
     cp_commit();
-    load(0, true);
-    cp_commit();
-    load(1, nzc > 1);
-    cp_commit();
-    cp_wait<0>();
+#pragma unroll
+    for (int k = 0; k <= PD; ++k) {
+        if (k <= nzc) load(k, k < nzc);
+        cp_commit();
+    }
+    cp_wait<PD>();
     __syncthreads();
 
     const float2 idx2 = bc2(g.inv_dx[0]), idy2 = bc2(g.inv_dx[1]), idz2 = bc2(g.inv_dx[2]);
@@ -358,6 +377,11 @@ __device__ __forceinline__ void tile_x2(x2::Smem& sm, const KGrid<float>& g, con
     // Y0 / Y_{j-2} / M(Y0) values of the pair, and its output offset.
     float2 pend = bc2(0.f), pTo = bc2(0.f), py0 = bc2(0.f), pyjm2 = bc2(0.f), pmy0 = bc2(0.f);
     int64_t pcb = 0;
+    // Status of the values written, reported once at the end of the tile:
+    // the sum of (y - y) stays 0 unless some y was NaN or +-Inf, the running
+    // minimum flags y <= 0 (Spitzer conductivity needs T > 0).
+    float2 nfacc = bc2(0.f);
+    float mnacc = INFINITY;
     auto finish = [&](int qp) {
         const int par = qp & 1;
         float2 div = sub2(pend, mul2(lds2(&sm.Fy[par][r][c]), idy2));
@@ -370,15 +394,15 @@ __device__ __forceinline__ void tile_x2(x2::Smem& sm, const KGrid<float>& g, con
             } else if (MODE == 1) {
                 if (a.MY0out) *reinterpret_cast<float2*>(a.MY0out + pcb) = M;
                 const float2 y = fma2(bc2(cf.mt), M, pTo);
-                check_value<float, SP>(y.x, status);
-                check_value<float, SP>(y.y, status);
+                nfacc = add2(nfacc, sub2(y, y));
+                if (SP) mnacc = fminf(mnacc, fminf(y.x, y.y));
                 *out = y;
             } else {
                 const float2 inc = fma2(bc2(cf.mu), sub2(pTo, py0),
                                         fma2(bc2(cf.nu), sub2(pyjm2, py0), fma2(bc2(cf.mt), M, mul2(bc2(cf.gt), pmy0))));
                 const float2 y = add2(py0, inc);
-                check_value<float, SP>(y.x, status);
-                check_value<float, SP>(y.y, status);
+                nfacc = add2(nfacc, sub2(y, y));
+                if (SP) mnacc = fminf(mnacc, fminf(y.x, y.y));
                 *out = y;
             }
         }
@@ -386,10 +410,10 @@ __device__ __forceinline__ void tile_x2(x2::Smem& sm, const KGrid<float>& g, con
 
     // one plane: cur holds plane q, nxt receives plane q + 1
     auto step = [&](int q, QZ& cur, QZ& nxt) {
-        cp_wait<0>();                      // bundle q + 1 has landed
+        cp_wait<PD - 1>();                 // bundle q + 1 has landed
         __syncthreads();
-        // the slots of bundle q + 2 held planes no thread reads any more
-        if (q + 2 <= nzc) load(q + 2, q + 2 < nzc);
+        // the slots of bundle q + PD + 1 held planes no thread reads any more
+        if (q + PD + 1 <= nzc) load(q + PD + 1, q + PD + 1 < nzc);
         cp_commit();
         if (q > 0) finish(q - 1);
 
@@ -419,11 +443,14 @@ __device__ __forceinline__ void tile_x2(x2::Smem& sm, const KGrid<float>& g, con
                                          mul2(half, add2(cur.bo[2], nxt.bo[2])), mul2(half, add2(cur.bo[0], nxt.bo[0])),
                                          mul2(half, add2(cur.bo[1], nxt.bo[1])), p);
 
+        // the tile's bottom y-faces and left x-faces: one extra face each,
+        // taken by warps on different schedulers from plane to plane
         const int par = q & 1;
-        if (r == 0) {
+        const int wy = q & 3, wx = 4 + ((q + 2) & 3);
+        if (r == wy) {
             *reinterpret_cast<float2*>(&sm.Fy[par][0][c]) =
                 low_yface2<SP, SAT>(sm, g, p, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), c);
-        } else if (r == 1 && lane < TY) {
+        } else if (r == wx && lane < TY) {
             sm.FxLo[par][lane] = low_xface<SP, SAT>(sm, g, p, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), lane);
         }
         if (MODE == 2) {
@@ -455,6 +482,11 @@ __device__ __forceinline__ void tile_x2(x2::Smem& sm, const KGrid<float>& g, con
     cp_wait<0>();
     __syncthreads();
     finish(nzc - 1);
+    if (MODE != 0) {
+        const bool bad_nf = nfacc.x != 0.f || nfacc.y != 0.f;
+        const bool bad_np = SP && !(mnacc > 0.f);
+        if (bad_nf || bad_np) atomicOr(status, (bad_nf ? ST_NONFINITE : 0u) | (bad_np ? ST_NONPOSITIVE : 0u));
+    }
     __syncthreads();
 }
 
@@ -467,19 +499,20 @@ __global__ void __launch_bounds__(x2::NTHREADS, OCC)
 stage_x2_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf, unsigned* status, int nzchunk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    x2::Smem& sm = *reinterpret_cast<x2::Smem*>(smem_raw);
+    constexpr int PD = OCC == 2 ? x2::kPD : 1;     // 3 CTAs per SM leave room for one plane in flight
+    x2::SmemT<PD>& sm = *reinterpret_cast<x2::SmemT<PD>*>(smem_raw);
     const int i0 = blockIdx.x * x2::TX;
     const int j0 = blockIdx.y * x2::TY;
     const int z0 = blockIdx.z * nzchunk;
     const int nzc = min(nzchunk, g.n[2] - z0);
-    tile_x2<SP, SAT, MODE>(sm, g, p, a, cf, status, i0, j0, z0, nzc);
+    tile_x2<SP, SAT, MODE, PD>(sm, g, p, a, cf, status, i0, j0, z0, nzc);
 }
 
 template <bool SP, bool SAT, int MODE, int OCC>
 cudaError_t launch3(const KGrid<float>& g, const KPhys<float>& p, const x2::FastArgs& a, const KCoef<float>& cf,
                     unsigned* status, int nzchunk, cudaStream_t st)
 {
-    const int smem = (int)sizeof(x2::Smem);
+    const int smem = (int)sizeof(x2::SmemT<OCC == 2 ? x2::kPD : 1>);
     static bool attr_set = false;       // the attribute is per function, set once
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(stage_x2_kernel<SP, SAT, MODE, OCC>,
@@ -620,14 +653,14 @@ ensemble_x2_kernel(const x2::EnsProb* __restrict__ probs, const x2::EnsSeg* __re
             a.MY0in = nullptr;
             a.MY0out = d.my0;
             a.out = d.buf[0];
-            tile_x2<SP, SAT, 1>(sm, d.g, d.p, a, cf, status, bx * x2::TX, by * x2::TY, z0, nzc);
+            tile_x2<SP, SAT, 1, x2::kPD>(sm, d.g, d.p, a, cf, status, bx * x2::TX, by * x2::TY, z0, nzc);
         } else {
             a.Tin = d.buf[(j - 2) % 3];
             a.Yjm2 = j == 2 ? d.T : d.buf[(j - 3) % 3];
             a.MY0in = d.my0;
             a.MY0out = nullptr;
             a.out = j == d.s ? d.T : d.buf[(j - 1) % 3];
-            tile_x2<SP, SAT, 2>(sm, d.g, d.p, a, cf, status, bx * x2::TX, by * x2::TY, z0, nzc);
+            tile_x2<SP, SAT, 2, x2::kPD>(sm, d.g, d.p, a, cf, status, bx * x2::TX, by * x2::TY, z0, nzc);
         }
         if (threadIdx.x == 0) {
             __threadfence();

@@ -27,13 +27,20 @@ struct FastArgs {
     int j;
 };
 
-struct Smem {
-    float T[4][PLANE];              // Y_{j-1} planes q-1, q, q+1 and the one in flight
-    float B[3][3][PLANE];           // b planes q, q+1 and the one in flight
-    float Y[3][3][TY * TX];         // Y0, Y_{j-2}, M(Y0) of planes q, q+1, in flight
+// Plane rings for a prefetch distance of PD planes: while plane q is
+// computed, planes q+1 .. q+PD are in flight and plane q+PD+1 is being
+// issued into the slots that plane q-2 (T) or q-1 (b, Y) released.
+template <int PD>
+struct SmemT {
+    static constexpr int NT = 3 + PD, NB = 2 + PD, NY = 2 + PD;
+    float T[NT][PLANE];             // Y_{j-1} planes q-1, q, q+1 and those in flight
+    float B[NB][3][PLANE];          // b planes q, q+1 and those in flight
+    float Y[NY][3][TY * TX];        // Y0, Y_{j-2}, M(Y0) of plane q and those in flight
     float Fy[2][TY + 1][TX];        // y-face fluxes (row 0: the tile's lower boundary)
     float FxLo[2][TY];              // x-faces on the tile's left boundary
 };
+constexpr int kPD = 2;              // prefetch distance at 2 CTAs per SM (82 KB each)
+using Smem = SmemT<kPD>;
 
 // One problem of an ensemble as the persistent kernel sees it.
 struct EnsProb {

@@ -56,6 +56,49 @@ def test_coeffs_match_oracle(lib, orc, s):
         assert np.array_equal(g, w)
 
 
+@pytest.mark.parametrize("ratio", [0.3, 1.0, 2.9, 20, 50, 100, 400, 1234.5])
+def test_first_order_stage_counts_match_oracle(lib, orc, ratio):
+    assert lib.rkl_num_stages_method(lib.RKL_METHOD_RKL2, ratio) == orc.num_stages(ratio)
+    assert lib.rkl_num_stages_method(lib.RKL_METHOD_RKL1, ratio) == orc.num_stages_rkl1(ratio)
+    for nu in (1e-3, 1e-2, 0.2):
+        assert lib.rkl_num_stages_method(lib.RKL_METHOD_STS, ratio, nu) == orc.num_stages_sts(ratio, nu)
+
+
+@pytest.mark.parametrize("s", [1, 2, 5, 14, 40])
+def test_first_order_coefficients(lib, orc, s):
+    """RKL1: the Legendre recursion (mu_j = (2j-1)/j, nu_j = -(j-1)/j,
+    mut_j = mu_j w1, mut_1 = w1, gt = 0); AAG-STS: mu = 1, nu = 0, gt = 0 and
+    mut_j = the oracle's sub-steps of a unit super-step."""
+    mu, nu, mut, gt = lib.rkl_coeffs_method(lib.RKL_METHOD_RKL1, s)
+    w1 = 2.0 / (s * s + s)
+    j = np.arange(2, s + 1)
+    assert abs(mut[1] - w1) < 1e-16
+    assert np.allclose(mu[2:], (2 * j - 1) / j, rtol=1e-15, atol=0)
+    assert np.allclose(nu[2:], -(j - 1) / j, rtol=1e-15, atol=0)
+    assert np.allclose(mut[2:], (2 * j - 1) / j * w1, rtol=1e-15, atol=0)
+    assert not np.any(gt)
+    for nuv in (1e-3, 0.05):
+        mu, nu, mut, gt = lib.rkl_coeffs_method(lib.RKL_METHOD_STS, s, nuv)
+        assert np.all(mu[2:] == 1.0) and not np.any(nu) and not np.any(gt)
+        assert np.allclose(mut[1:], orc.sts_substeps(s, nuv, 1.0), rtol=1e-13, atol=0)
+    if s >= 2:
+        assert all(np.array_equal(a, b) for a, b in zip(lib.rkl_coeffs_method(lib.RKL_METHOD_RKL2, s),
+                                                         orc.coeffs(s)))
+
+
+def test_method_argument_checks(lib):
+    so = lib.load()
+    s = ctypes.c_int(0)
+    assert so.rkl_num_stages_method(7, 10.0, 1e-3, ctypes.byref(s)) == lib.RKL_ERR_INVALID_ARG
+    for nu in (0.0, 1.0, -0.1, float("nan")):
+        assert so.rkl_num_stages_method(lib.RKL_METHOD_STS, 10.0, nu, ctypes.byref(s)) == lib.RKL_ERR_INVALID_ARG
+    assert so.rkl_num_stages_method(lib.RKL_METHOD_STS, 1e12, 1e-3, ctypes.byref(s)) == lib.RKL_ERR_INVALID_ARG
+    arr = np.zeros(5)
+    p = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert so.rkl_coeffs_method(lib.RKL_METHOD_RKL2, 1, 1e-3, p, p, p, p) == lib.RKL_ERR_INVALID_ARG
+    assert so.rkl_coeffs_method(lib.RKL_METHOD_RKL1, 0, 1e-3, p, p, p, p) == lib.RKL_ERR_INVALID_ARG
+
+
 def test_host_argument_checks(lib):
     so = lib.load()
     s = ctypes.c_int(0)
