@@ -227,8 +227,11 @@ rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
  * f32x2 arithmetic; needs nx % 4 == 0) built for 2 (variant 3) or 3
  * (variant 4) resident CTAs per SM.  RKL_ERR_UNSUPPORTED if the kernel
  * does not apply to the grid.  nzchunk = planes per CTA of the paired-cell
- * kernel (<= 0: 32).  Drops cached graphs.  Results of all kernels agree
- * within FP32 rounding.
+ * kernels (0: chosen from the grid and the SM count so that the last wave
+ * of CTAs is nearly full); a negative value selects the balanced schedule instead:
+ * one launch of 2 (or 3) CTAs per SM in which every CTA marches an equal run
+ * of the grid's (tile column, plane) pairs.  Drops cached graphs.  Results
+ * of all kernels and schedules agree within FP32 rounding.
  */
 rkl_status rkl_plan_set_variant(rkl_plan *plan, int variant, int nzchunk);
 
@@ -243,8 +246,8 @@ rkl_status rkl_plan_set_method(rkl_plan *plan, int method, double sts_nu);
 /*
  * Autotuner: times one super-step of length dt (s from dt / dt_expl(T))
  * with every kernel variant and z-chunk that applies to the grid (generic;
- * tiled; paired-cell at 2 and 3 CTAs per SM with 8, 16, 32, 64 planes per
- * CTA) on a scratch copy of T (T is not changed), keeps the fastest with
+ * tiled; paired-cell at 2 and 3 CTAs per SM, balanced or with 8, 16, 32, 64
+ * planes per CTA) on a scratch copy of T (T is not changed), keeps the fastest with
  * rkl_plan_set_variant and returns it.  Allocates and frees one grid-sized
  * scratch array.  Synchronises.
  */

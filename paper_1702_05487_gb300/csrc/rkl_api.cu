@@ -47,9 +47,11 @@ struct rkl_plan {
     bool fast = false;                 // tiled kernel available for this grid
     bool x2ok = false;                 // paired-cell kernel available for this grid
     int variant = 0;                   // 0 auto, 1 generic, 2 tiled, 3/4 paired-cell (2/3 CTAs per SM)
-    int nzchunk = 32;                  // planes per CTA of the paired-cell kernel
+    int nzchunk = 0;                   // planes per CTA of the paired-cell kernel (0: automatic, < 0: balanced runs)
 
     void* ybuf[3] = {nullptr, nullptr, nullptr};
+    void* ybuf4 = nullptr;             // fourth stage buffer of the two-stage kernel (allocated on use)
+    bool pairok = false;               // two-stage kernel applies to the grid
     void* my0 = nullptr;
     double* d_partials = nullptr;
     double* d_scal = nullptr;          // {max, min, sum, status}
@@ -214,7 +216,7 @@ rkl_status launch_stage(rkl_plan* p, const StageIO& io, double mu, double nu, do
         KCoef<float> cf{(float)mu, (float)nu, (float)mt, (float)gt};
         bool al = aligned16(io.Y0) && aligned16(io.MY0) && aligned16(io.Yjm1) && aligned16(io.Yjm2) &&
                   aligned16(io.Yj) && aligned16(io.b);
-        if (p->x2ok && al && (p->variant == 0 || p->variant == 3 || p->variant == 4))
+        if (p->x2ok && al && (p->variant == 0 || p->variant == 3 || p->variant == 4 || p->variant == 5))
             e = launch_stage_x2(p->cfg, p->gf, p->pf, io, cf, p->d_status, p->nzchunk,
                                 p->variant == 4 ? 3 : 2, st);
         else if (p->fast && al && (p->variant == 0 || p->variant == 2))
@@ -249,6 +251,54 @@ rkl_status enqueue_stages(rkl_plan* p, int s, void* T, const void* b, bool with_
         return RKL_OK;
     }
     if (with_events) RKL_CK(p, cudaEventRecordWithFlags(p->ev_a, cs, cudaEventRecordExternal));
+    if (p->variant == 5 && p->pairok && p->ybuf4) {
+        // stages (j, j+1) in pairs, the last stage alone so that it may write
+        // T in place; pair outputs never alias the pair's inputs (4 buffers)
+        void* bufs[4] = {p->ybuf[0], p->ybuf[1], p->ybuf[2], p->ybuf4};
+        const void* prev2 = T;
+        void* prev1 = p->ybuf[0];
+        auto pick = [&](void* avoid) {
+            for (void* q : bufs)
+                if (q != prev1 && q != prev2 && q != avoid) return q;
+            return (void*)nullptr;
+        };
+        int j = 2;
+        for (; j + 1 <= s - 1; j += 2) {
+            StageIO q{};
+            q.b = b;
+            q.coef_tab = p->d_coef;
+            q.Y0 = T;
+            q.MY0 = p->my0;
+            q.Yjm1 = prev1;
+            q.Yjm2 = prev2;
+            q.Yj = pick(nullptr);
+            void* Yj1 = pick(q.Yj);
+            q.j = j;
+            q.mode = 2;
+            cudaError_t e = launch_stage_pair(p->cfg, p->gf, p->pf, q, Yj1, p->d_status, p->nzchunk, cs);
+            if (e != cudaSuccess) return cuda_fail(p, e, "two-stage launch");
+            prev2 = q.Yj;
+            prev1 = Yj1;
+        }
+        for (; j <= s; ++j) {
+            StageIO q{};
+            q.b = b;
+            q.coef_tab = p->d_coef;
+            q.Y0 = T;
+            q.MY0 = p->my0;
+            q.Yjm1 = prev1;
+            q.Yjm2 = prev2;
+            q.Yj = (j == s) ? T : pick(nullptr);
+            q.j = j;
+            q.mode = 2;
+            st = launch_stage(p, q, 0, 0, 0, 0, cs);
+            if (st != RKL_OK) return st;
+            prev2 = prev1;
+            prev1 = q.Yj;
+        }
+        if (with_events) RKL_CK(p, cudaEventRecordWithFlags(p->ev_b, cs, cudaEventRecordExternal));
+        return RKL_OK;
+    }
     for (int j = 2; j <= s; ++j) {
         StageIO q{};
         q.b = b;
@@ -541,6 +591,7 @@ rkl_status rkl_plan_create(const rkl_grid* grid, const rkl_phys* phys, void* cud
     fill(p->gd, p->pd);
     p->fast = g.dtype == RKL_F32 && fast_stage_supported(p->cfg, p->gf);
     p->x2ok = g.dtype == RKL_F32 && x2_stage_supported(p->cfg, p->gf);
+    p->pairok = g.dtype == RKL_F32 && pair_stage_supported(p->cfg, p->gf);
 
     rkl_plan* P = p;
     auto bail = [&](cudaError_t e, const char* where) {
@@ -586,6 +637,7 @@ rkl_status rkl_plan_destroy(rkl_plan* p)
     for (auto& g : p->cache)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     for (int k = 0; k < 3; ++k) cudaFree(p->ybuf[k]);
+    cudaFree(p->ybuf4);
     cudaFree(p->my0);
     cudaFree(p->d_partials);
     cudaFree(p->d_scal);
@@ -762,10 +814,12 @@ rkl_status rkl_plan_autotune(rkl_plan* p, double dt, const void* T, const void* 
     std::vector<Cand> cands = {{1, 0}};
     if (p->fast) cands.push_back({2, 0});
     if (p->x2ok)
-        for (int nz : {8, 16, 32, 64}) {
+        for (int nz : {0, -1, 16, 32, 64}) {
             cands.push_back({3, nz});
             cands.push_back({4, nz});
         }
+    if (p->x2ok && p->pairok)
+        for (int nz : {16, 32, 64}) cands.push_back({5, nz});
     void* scratch = nullptr;
     RKL_CK(p, cudaMalloc(&scratch, (size_t)p->ncell * p->esize));
     cudaEvent_t a = nullptr, e = nullptr;
@@ -808,12 +862,21 @@ rkl_status rkl_plan_autotune(rkl_plan* p, double dt, const void* T, const void* 
 rkl_status rkl_plan_set_variant(rkl_plan* p, int variant, int nzchunk)
 {
     if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
-    if (variant < 0 || variant > 4) return fail(p, RKL_ERR_INVALID_ARG, "variant must be 0 to 4");
+    if (variant < 0 || variant > 5) return fail(p, RKL_ERR_INVALID_ARG, "variant must be 0 to 5");
     if (nzchunk > 4096) return fail(p, RKL_ERR_INVALID_ARG, "nzchunk must be <= 4096");
     if (variant == 2 && !p->fast) return fail(p, RKL_ERR_UNSUPPORTED, "no tiled kernel for this grid");
     if ((variant == 3 || variant == 4) && !p->x2ok)
         return fail(p, RKL_ERR_UNSUPPORTED, "no paired-cell kernel for this grid");
-    p->nzchunk = nzchunk > 0 ? nzchunk : 32;
+    if (variant == 5 && !(p->pairok && p->x2ok))
+        return fail(p, RKL_ERR_UNSUPPORTED, "no two-stage kernel for this grid (periodic FP32 3D, nx % 4 == 0)");
+    if (variant == 5 && !p->ybuf4) {
+        DeviceGuard dg(p->device);
+        if (cudaMalloc(&p->ybuf4, (size_t)p->ncell * p->esize) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(p, RKL_ERR_NOMEM, "cudaMalloc(fourth stage buffer)");
+        }
+    }
+    p->nzchunk = nzchunk;
     DeviceGuard dg(p->device);
     cudaStreamSynchronize(p->stream);
     for (auto& g : p->cache)

@@ -51,6 +51,14 @@ cudaError_t launch_stage_x2(const LaunchCfg& c, const KGrid<float>& g, const KPh
                             const KCoef<float>& coef, unsigned* status, int nzchunk, int occupancy,
                             cudaStream_t st);
 
+// Two-stage paired-cell FP32 3D kernel: stages j (io, coefficients at
+// io.coef_tab[4 j]) and j + 1 (written to Yj1) in one pass, 60 x 7 tiles of
+// nzchunk planes.  Periodic grids with nx % 4 == 0 only.  Neither output may
+// alias an input: the pass reads Y_{j-1}, Y_{j-2} and Y0 around its tile.
+bool pair_stage_supported(const LaunchCfg& c, const KGrid<float>& g);
+cudaError_t launch_stage_pair(const LaunchCfg& c, const KGrid<float>& g, const KPhys<float>& p, const StageIO& io,
+                              void* Yj1, unsigned* status, int nzchunk, cudaStream_t st);
+
 // FP64 statistics of a grid array: max, min and sum (fixed-order, deterministic).
 // partials must hold 3 * kStatsBlocks + 1 doubles, the last one zero before
 // the first call (a ticket counter the pass leaves at zero); out receives {max, min, sum}

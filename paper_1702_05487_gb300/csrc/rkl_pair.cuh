@@ -1,0 +1,84 @@
+// Packed FP32 pair arithmetic, the paired-cell face flux and the
+// shared-memory copy helpers used by the paired-cell stage kernels (one
+// stage per pass, and two stages per pass).
+#pragma once
+
+#include "rkl_device.cuh"
+
+namespace rkl {
+namespace x2 {
+
+// --------------------------------------------------------------------------
+// packed FP32 pair arithmetic
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    unsigned long long r, x = *reinterpret_cast<unsigned long long*>(&a),
+                          y = *reinterpret_cast<unsigned long long*>(&b);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+    return *reinterpret_cast<float2*>(&r);
+}
+__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 sqrt2(float2 a) { return make_float2(dsqrt<float>(a.x), dsqrt<float>(a.y)); }
+
+// Normal flux on a pair of faces (the packed form of face_flux).
+template <bool SP, bool SAT>
+__device__ __forceinline__ float2 face2(float2 TL, float2 TR, float2 gn, float2 g1, float2 g2, float2 bn, float2 b1,
+                                        float2 b2, const KPhys<float>& p)
+{
+    const float2 Tf = mul2(bc2(0.5f), add2(TL, TR));
+    float2 nk;                                    // -kappa_par at the face
+    if (SP) nk = mul2(mul2(bc2(-p.kappa0), mul2(Tf, Tf)), sqrt2(Tf));
+    else nk = bc2(-p.kappa0);
+    const float2 nkp = mul2(bc2(p.kperp), nk);    // -kappa_perp
+    const float2 bdg = fma2(bn, gn, fma2(b1, g1, mul2(b2, g2)));
+    float2 Fn = fma2(mul2(nk, bn), bdg, mul2(nkp, gn));
+    if (SAT) {
+        const float2 F1 = fma2(mul2(nk, b1), bdg, mul2(nkp, g1));
+        const float2 F2 = fma2(mul2(nk, b2), bdg, mul2(nkp, g2));
+        const float2 F2s = fma2(Fn, Fn, fma2(F1, F1, mul2(F2, F2)));
+        const float2 Fmag = sqrt2(F2s);
+        float2 Tq = Tf;
+        if (p.upwind) {
+            Tq.x = Fn.x >= 0.f ? TL.x : TR.x;
+            Tq.y = Fn.y >= 0.f ? TL.y : TR.y;
+        }
+        const float2 q = mul2(mul2(bc2(p.q0), Tq), sqrt2(Tq));
+        const float2 den = add2(q, Fmag);
+        Fn = make_float2(ddiv<float>(q.x, den.x) * Fn.x, ddiv<float>(q.y, den.y) * Fn.y);
+    }
+    return Fn;
+}
+
+// --------------------------------------------------------------------------
+// shared memory and copies
+
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp16(unsigned d, const void* s)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(s));
+}
+__device__ __forceinline__ void st4(unsigned d, float v)
+{
+    asm volatile("st.shared.v4.f32 [%0], {%1, %1, %1, %1};\n" ::"r"(d), "f"(v));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ int pmod(int v, int n)
+{
+    int r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+
+}  // namespace x2
+}  // namespace rkl

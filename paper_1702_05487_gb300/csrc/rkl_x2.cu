@@ -11,85 +11,19 @@
 //
 // The per-tile body (tile_x2) is also the work item of the persistent
 // ensemble kernel (rkl_ensemble.cu).
+#include <algorithm>
+
 #include "rkl_launch.h"
+#include "rkl_pair.cuh"
 #include "rkl_x2.cuh"
 
 namespace rkl {
 namespace x2 {
 
 // --------------------------------------------------------------------------
-// packed FP32 pair arithmetic
-
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b)
-{
-    unsigned long long r, x = *reinterpret_cast<unsigned long long*>(&a),
-                          y = *reinterpret_cast<unsigned long long*>(&b);
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
-    return *reinterpret_cast<float2*>(&r);
-}
-__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
-__device__ __forceinline__ float2 sqrt2(float2 a) { return make_float2(dsqrt<float>(a.x), dsqrt<float>(a.y)); }
-
-// Normal flux on a pair of faces (the packed form of face_flux).
-template <bool SP, bool SAT>
-__device__ __forceinline__ float2 face2(float2 TL, float2 TR, float2 gn, float2 g1, float2 g2, float2 bn, float2 b1,
-                                        float2 b2, const KPhys<float>& p)
-{
-    const float2 Tf = mul2(bc2(0.5f), add2(TL, TR));
-    float2 nk;                                    // -kappa_par at the face
-    if (SP) nk = mul2(mul2(bc2(-p.kappa0), mul2(Tf, Tf)), sqrt2(Tf));
-    else nk = bc2(-p.kappa0);
-    const float2 nkp = mul2(bc2(p.kperp), nk);    // -kappa_perp
-    const float2 bdg = fma2(bn, gn, fma2(b1, g1, mul2(b2, g2)));
-    float2 Fn = fma2(mul2(nk, bn), bdg, mul2(nkp, gn));
-    if (SAT) {
-        const float2 F1 = fma2(mul2(nk, b1), bdg, mul2(nkp, g1));
-        const float2 F2 = fma2(mul2(nk, b2), bdg, mul2(nkp, g2));
-        const float2 F2s = fma2(Fn, Fn, fma2(F1, F1, mul2(F2, F2)));
-        const float2 Fmag = sqrt2(F2s);
-        float2 Tq = Tf;
-        if (p.upwind) {
-            Tq.x = Fn.x >= 0.f ? TL.x : TR.x;
-            Tq.y = Fn.y >= 0.f ? TL.y : TR.y;
-        }
-        const float2 q = mul2(mul2(bc2(p.q0), Tq), sqrt2(Tq));
-        const float2 den = add2(q, Fmag);
-        Fn = make_float2(ddiv<float>(q.x, den.x) * Fn.x, ddiv<float>(q.y, den.y) * Fn.y);
-    }
-    return Fn;
-}
-
-// --------------------------------------------------------------------------
 // shared memory and copies
 
 __device__ __forceinline__ int off(int r, int c) { return (r + 1) * SXS + c + 4; }
-
-__device__ __forceinline__ unsigned smem_u32(const void* p)
-{
-    return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void cp16(unsigned d, const void* s)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(s));
-}
-__device__ __forceinline__ void st4(unsigned d, float v)
-{
-    asm volatile("st.shared.v4.f32 [%0], {%1, %1, %1, %1};\n" ::"r"(d), "f"(v));
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
-__device__ __forceinline__ int pmod(int v, int n)
-{
-    int r = v % n;
-    return r < 0 ? r + n : r;
-}
-
-__device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
 // Copy tasks fixed per thread for the whole tile: a bundle is T and b
 // (4 arrays x 10 rows x 18 chunks of 16 B, halo ring included) plus Y0,
@@ -501,11 +435,42 @@ stage_x2_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int PD = OCC == 2 ? x2::kPD : 1;     // 3 CTAs per SM leave room for one plane in flight
     x2::SmemT<PD>& sm = *reinterpret_cast<x2::SmemT<PD>*>(smem_raw);
-    const int i0 = blockIdx.x * x2::TX;
-    const int j0 = blockIdx.y * x2::TY;
-    const int z0 = blockIdx.z * nzchunk;
-    const int nzc = min(nzchunk, g.n[2] - z0);
-    tile_x2<SP, SAT, MODE, PD>(sm, g, p, a, cf, status, i0, j0, z0, nzc);
+    if (nzchunk > 0) {
+        // one tile column, one chunk of nzchunk planes per CTA
+        const int z0 = blockIdx.z * nzchunk;
+        tile_x2<SP, SAT, MODE, PD>(sm, g, p, a, cf, status, blockIdx.x * x2::TX, blockIdx.y * x2::TY, z0,
+                                   min(nzchunk, g.n[2] - z0));
+        return;
+    }
+    // Balanced schedule: the column-planes (tile column, plane) in column-major
+    // order are split into gridDim.x equal runs; each CTA marches its run,
+    // switching columns where the run crosses one, so every CTA carries the
+    // same number of planes and no partial last wave is left.
+    const int ntx = (g.n[0] + x2::TX - 1) / x2::TX;
+    const int nz = g.n[2];
+    const int64_t U = (int64_t)ntx * ((g.n[1] + x2::TY - 1) / x2::TY) * nz;
+    int64_t u = U * blockIdx.x / gridDim.x;
+    const int64_t u1 = U * (blockIdx.x + 1) / gridDim.x;
+    while (u < u1) {
+        const int64_t col = u / nz;
+        const int z0 = (int)(u - col * nz);
+        const int nzc = (int)min((int64_t)(nz - z0), u1 - u);
+        tile_x2<SP, SAT, MODE, PD>(sm, g, p, a, cf, status, (int)(col % ntx) * x2::TX, (int)(col / ntx) * x2::TY,
+                                   z0, nzc);
+        u += nzc;
+    }
+}
+
+int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 152;
+    }
+    return n;
 }
 
 template <bool SP, bool SAT, int MODE, int OCC>
@@ -520,7 +485,14 @@ cudaError_t launch3(const KGrid<float>& g, const KPhys<float>& p, const x2::Fast
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    dim3 grid((g.n[0] + x2::TX - 1) / x2::TX, (g.n[1] + x2::TY - 1) / x2::TY, (g.n[2] + nzchunk - 1) / nzchunk);
+    const int ntx = (g.n[0] + x2::TX - 1) / x2::TX, nty = (g.n[1] + x2::TY - 1) / x2::TY;
+    dim3 grid(ntx, nty, nzchunk > 0 ? (g.n[2] + nzchunk - 1) / nzchunk : 1);
+    if (nzchunk <= 0) {
+        // balanced: OCC CTAs per SM, each run at least 8 planes long
+        const int64_t U = (int64_t)ntx * nty * g.n[2];
+        grid = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)OCC * sm_count(), U / 8)), 1, 1);
+        nzchunk = 0;
+    }
     stage_x2_kernel<SP, SAT, MODE, OCC><<<grid, x2::NTHREADS, smem, st>>>(g, p, a, cf, status, nzchunk);
     return cudaGetLastError();
 }
@@ -553,6 +525,27 @@ bool x2_stage_supported(const LaunchCfg& c, const KGrid<float>& g)
     return c.dtype == 0 && c.ndim == 3 && (g.n[0] % 4) == 0;
 }
 
+// Planes per CTA when none is given: the chunk length in [16, 48] that
+// minimises (rounds of resident CTAs) x (planes + halo cost) per CTA, so that
+// the last wave of CTAs is not left mostly empty.
+static int auto_nzchunk(const KGrid<float>& g, int occupancy)
+{
+    const int64_t cols = (int64_t)((g.n[0] + x2::TX - 1) / x2::TX) * ((g.n[1] + x2::TY - 1) / x2::TY);
+    const int64_t slots = (int64_t)occupancy * sm_count();
+    int best = 32;
+    double cost = 1e300;
+    for (int nzc = 16; nzc <= 48; ++nzc) {
+        const int64_t chunks = (g.n[2] + nzc - 1) / nzc;
+        const int64_t rounds = (cols * chunks + slots - 1) / slots;
+        const double c = (double)rounds * (std::min(nzc, g.n[2]) + 2.5);
+        if (c < cost - 1e-9) {
+            cost = c;
+            best = nzc;
+        }
+    }
+    return best;
+}
+
 x2::FastArgs x2_args(const StageIO& io)
 {
     x2::FastArgs a;
@@ -572,7 +565,8 @@ cudaError_t launch_stage_x2(const LaunchCfg& c, const KGrid<float>& g, const KPh
                             const KCoef<float>& coef, unsigned* status, int nzchunk, int occupancy, cudaStream_t st)
 {
     const x2::FastArgs a = x2_args(io);
-    if (nzchunk < 1) nzchunk = 32;
+    if (nzchunk == 0) nzchunk = auto_nzchunk(g, occupancy);
+    else if (nzchunk < 0) nzchunk = 0;
     if (occupancy == 3) return launch_phys<3>(c, io.mode, g, p, a, coef, status, nzchunk, st);
     return launch_phys<2>(c, io.mode, g, p, a, coef, status, nzchunk, st);
 }

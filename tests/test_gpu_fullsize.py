@@ -46,12 +46,13 @@ def test_ring_fp64_full_run(rk, orc):
     assert plan.check() == 0
 
 
-def _sampled_first_step(rk, orc, W, dtype, cells):
+def _sampled_first_step(rk, orc, W, dtype, cells, variant=0):
     import torch
     P = Problem(W.T.shape, **W.params)
     T = rounded(W.T, dtype)
     b = rounded(W.b, dtype)
     plan = rk.Plan(W.T.shape, dtype, params=W.params)
+    plan.set_variant(variant)
     Td, bd = torch_dev(T, dtype), torch_dev(b, dtype)
     e0 = orc.energy(P, T)
     dt = W.ratio * orc.dt_expl(P, T)
@@ -72,11 +73,15 @@ def _sampled_first_step(rk, orc, W, dtype, cells):
     return plan, Td, bd, dt, e0, P
 
 
-def test_tangled_256_sampled_and_conservation(rk, orc):
+@pytest.mark.parametrize("variant", [0, 5])
+def test_tangled_256_sampled_and_conservation(rk, orc, variant):
+    """The benchmark's 256^3 workload with the default single-stage kernel
+    and with the two-stage kernel (tile edges at multiples of 60 and 7)."""
     W = workloads.tangled(256, seed=2)
     rng = np.random.default_rng(0)
     cells = [tuple(int(v) for v in rng.integers(0, 256, 3)) for _ in range(5)] + [(0, 0, 0), (255, 128, 7)]
-    plan, Td, bd, dt, e0, P = _sampled_first_step(rk, orc, W, "f32", cells)
+    cells += [(31, 7, 60), (32, 13, 59), (255, 255, 240)]
+    plan, Td, bd, dt, e0, P = _sampled_first_step(rk, orc, W, "f32", cells, variant)
     for _ in range(W.n_super - 1):
         s, eb, ea = plan.super_step(dt, Td, bd, energies=True)
         assert abs(ea - eb) <= 1e-6 * abs(eb)

@@ -135,11 +135,15 @@ def _variant_cases():
     # grids with nx % 4 == 0 (the paired-cell kernel) and Dirichlet partial tiles
     spitz = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
     sat = dict(kappa_model="spitzer", kappa_par0=0.01, saturate=True, phi=0.3)
-    for v in (2, 3, 4):
-        out.append(("3d_x4_dirichlet", (21, 19, 36), dict(spitz, bc="dirichlet", bc_value=0.9), "f32", v))
+    for v in (2, 3, 4, 5):
+        if v != 5:      # the two-stage kernel is periodic only
+            out.append(("3d_x4_dirichlet", (21, 19, 36), dict(spitz, bc="dirichlet", bc_value=0.9), "f32", v))
         out.append(("3d_x4_sat", (18, 26, 68), sat, "f32", v))
         out.append(("3d_x4_sat_upwind", (10, 9, 132), dict(sat, phi=0.05, sat_upwind=True), "f32", v))
         out.append(("3d_x4_const", (33, 17, 44), dict(kappa_par0=0.02, kappa_perp_ratio=0.1), "f32", v))
+    # two-stage kernel: several 60 x 7 tiles with ragged edges in x, y and z
+    out.append(("3d_pair_spitzer", (45, 30, 128), spitz, "f32", 5))
+    out.append(("3d_pair_small", (5, 4, 8), spitz, "f32", 5))
     return out
 
 
@@ -169,18 +173,20 @@ def test_super_steps(rk, orc, case):
 
 @pytest.mark.parametrize("shape,nzchunk", [((32, 32, 32), 0), ((7, 9, 5), 0), ((40, 3, 70), 0),
                                            ((1, 33, 64), 0), ((65, 8, 36), 0), ((37, 24, 128), 5),
-                                           ((64, 16, 64), 64), ((9, 40, 4), 2), ((3, 8, 200), 1)])
+                                           ((64, 16, 64), 64), ((9, 40, 4), 2), ((3, 8, 200), 1),
+                                           ((37, 24, 128), -1), ((100, 16, 68), -1)])
 def test_tiled_kernels_match_generic(rk, orc, shape, nzchunk):
     """The tiled kernels (variants 2 and 3, the latter when nx % 4 == 0,
-    with several z-chunk lengths) and the generic kernel (variant 1) on
+    with several z-chunk lengths, and nzchunk -1 = the balanced schedule
+    whose runs cross tile columns) and the generic kernel (variant 1) on
     tile-aligned, ragged and degenerate shapes; all against the oracle."""
     params = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
-    variants = (1, 2, 3, 4) if shape[2] % 4 == 0 else (1, 2)
+    variants = (1, 2, 3, 4, 5) if shape[2] % 4 == 0 else (1, 2)
     res = {}
     for v in variants:
         P, plan, T, b, Td, bd = _setup(rk, "x", shape, params, "f32", v)
         if v >= 3:
-            plan.set_variant(v, nzchunk)
+            plan.set_variant(v, nzchunk if v < 5 else max(nzchunk, 0))
         dt = 40 * orc.dt_expl(P, T)
         for _ in range(2):
             plan.super_step(dt, Td, bd)
@@ -204,7 +210,7 @@ def test_autotune_keeps_input_and_parity(rk, orc):
     T_before = Td.clone()
     v, nz, ms = plan.autotune(dt, Td, bd)
     assert torch.equal(Td, T_before)
-    assert v in (1, 2, 3, 4) and ms > 0
+    assert v in (1, 2, 3, 4, 5) and ms > 0
     plan.super_step(dt, Td, bd)
     Tref, _ = orc.super_step(P, T, b, dt)
     assert rel_l2(host(Td), Tref) < F32_STATE_REL_L2
