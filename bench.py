@@ -183,6 +183,29 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def aggregate_over_ranks(dist, elapsed: float, units: float, device="cpu"):
+    """Replicas: the slowest rank's elapsed time and the units all ranks
+    processed (value = units / elapsed).  dist=None on one process."""
+    if dist is None:
+        return elapsed, units
+    import torch
+    t = torch.tensor([elapsed, units], device=device, dtype=torch.float64)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
+
+
+def stage_launches_per_step(variant: int, s: int) -> int:
+    """Stage-kernel launches of one super-step: s, or with the two-stage
+    kernel stage 1, the pairs (j, j+1) for j + 1 < s, then the rest singly."""
+    if variant != 5:
+        return s
+    pairs = max(0, (s - 2) // 2)
+    return 1 + pairs + (s - 1 - 2 * pairs)
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -205,6 +228,8 @@ def run_ours(args):
     T = T0.to(dev)
     b = b0.to(dev).contiguous()
     plan = rk.Plan(W.T.shape, dtype, stream=stream, params=W.params)
+    if args.variant or args.nzchunk:
+        plan.set_variant(args.variant, args.nzchunk)
     dt = W.ratio * plan.dt_expl(T)
     ncell = T.numel()
 
@@ -224,9 +249,11 @@ def run_ours(args):
         barrier()
         ev0.record(stream)
         stages = 0
+        launches = 0
         for _ in range(args.steps):
             s = plan.super_step(dt, T, b)
             stages += s
+            launches += stage_launches_per_step(args.variant, s)
         ev1.record(stream)
         barrier()
     ms = ev0.elapsed_time(ev1)
@@ -236,17 +263,8 @@ def run_ours(args):
     if status != 0:
         raise RuntimeError(f"device status {status} after the timed region")
 
-    # max over ranks
-    ms_max = ms
-    total_cell_stages = float(ncell) * stages
-    if dist is not None:
-        t = torch.tensor([ms, total_cell_stages], device=dev, dtype=torch.float64)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_max = float(mx[0])
-        total_cell_stages = float(sm[1])
+    # slowest rank's time, all ranks' cell-stages
+    ms_max, total_cell_stages = aggregate_over_ranks(dist, ms, float(ncell) * stages, dev)
     value = total_cell_stages / (ms_max * 1e-3) / 1e9
 
     # end to end through the public host-buffer API: every step copies T and
@@ -261,14 +279,7 @@ def run_ours(args):
         e_stages += plan.run_host(dt, 1, Th, bh)
     barrier()
     e_s = time.perf_counter() - t0
-    e_cell_stages = float(ncell) * e_stages
-    if dist is not None:
-        t = torch.tensor([e_s, e_cell_stages], device=dev, dtype=torch.float64)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        e_s, e_cell_stages = float(mx[0]), float(sm[1])
+    e_s, e_cell_stages = aggregate_over_ranks(dist, e_s, float(ncell) * e_stages, dev)
     e2e_value = e_cell_stages / e_s / 1e9
 
     if rank != 0:
@@ -296,7 +307,8 @@ def run_ours(args):
                    "dt_over_dtexpl": W.ratio, "step": "one RKL2 super-step (dt_expl pass + s stages)",
                    "l2": ("inputs larger than L2: 8 grid arrays per stage" if ncell * 32 > 129e6
                           else "working set fits in L2"),
-                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "kernel_variant": args.variant, "nzchunk": args.nzchunk},
         "roofline": {"bound": "hbm", "kernel": "rkl2 stage", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_cs * ncell,
@@ -304,7 +316,7 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "Gcell-stage/s",
                 "h2d_bytes_per_step": int(T0.numel() * T0.element_size() + b0.numel() * b0.element_size()),
                 "d2h_bytes_per_step": int(T0.numel() * T0.element_size())},
-        "gpu_launches": int(stages + 2 * args.steps),
+        "gpu_launches": int(launches + args.steps),     # stage launches + one statistics pass per step
         "clocks": clocks.summary(),
         "cpu_baseline": cpu,
     }
@@ -398,6 +410,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="stage kernel: 0 auto, 1 generic, 2 tiled, 3/4 paired-cell at 2/3 CTAs per SM, 5 two-stage")
+    ap.add_argument("--nzchunk", type=int, default=0, help="planes per CTA (0 automatic, < 0 balanced runs)")
     ap.add_argument("--workload", default="tangled256",
                     choices=list(WORKLOADS) + ["ensemble64", "surrogate128"])
     ap.add_argument("--pairs", type=int, default=20000, help="training pairs of the surrogate workload")

@@ -73,7 +73,17 @@ typedef struct rkl_phys {
     int sat_upwind;          /* 1: c_iso from the cell the normal flux leaves;
                                 0: from the face temperature                  */
     double cp;               /* parabolic Courant number C_p <= 1/2 (Eq. dt_exp) */
+    int limiter;             /* RKL_LIMITER_NONE: transverse gradients are the
+                                mean of the four one-sided differences (Eq. qT);
+                                RKL_LIMITER_MC: the monotonised-central limiter
+                                of Appendix C, MC(MC(up_L, down_L),
+                                MC(up_R, down_R)), at faces whose lower
+                                temperature is below limiter_floor (generic
+                                kernel only)                                  */
+    double limiter_floor;    /* +inf limits every face (Section 3.4: limiters
+                                only where T falls below a floor)            */
 } rkl_phys;
+enum { RKL_LIMITER_NONE = 0, RKL_LIMITER_MC = 1 };
 
 typedef struct rkl_plan rkl_plan;
 
@@ -225,7 +235,11 @@ rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
  * tiled FP32 3D kernel (32 x 8 tiles, one cell per thread), 3 and 4 = the
  * paired-cell FP32 3D kernel (64 x 8 tiles, two cells per thread in packed
  * f32x2 arithmetic; needs nx % 4 == 0) built for 2 (variant 3) or 3
- * (variant 4) resident CTAs per SM.  RKL_ERR_UNSUPPORTED if the kernel
+ * (variant 4) resident CTAs per SM, 5 = the two-stage kernel (stages j and
+ * j + 1 per pass over the grid, 60 x 7 tiles; periodic only; allocates a
+ * fourth stage buffer), 6 = the paired-cell kernel with its plane bundles
+ * copied by the TMA engine (cp.async.bulk rows with mbarrier completion;
+ * periodic grids with nx >= 72, else as 3).  RKL_ERR_UNSUPPORTED if the kernel
  * does not apply to the grid.  nzchunk = planes per CTA of the paired-cell
  * kernels (0: chosen from the grid and the SM count so that the last wave
  * of CTAs is nearly full); a negative value selects the balanced schedule instead:

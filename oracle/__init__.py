@@ -70,6 +70,8 @@ class _Problem(ctypes.Structure):
         ("rho", ctypes.c_double),
         ("sat_upwind", ctypes.c_int),
         ("cp", ctypes.c_double),
+        ("limiter", ctypes.c_int),
+        ("limiter_floor", ctypes.c_double),
     ]
 
 
@@ -132,6 +134,8 @@ class Problem:
     rho: float = 1.0
     sat_upwind: bool = False
     cp: float = 0.5
+    limiter: str = "none"            # "none" (arithmetic mean, Eq. qT) | "mc" (Appendix C)
+    limiter_floor: float = float("inf")
     _c: _Problem = field(default=None, repr=False)
 
     @property
@@ -161,6 +165,8 @@ class Problem:
         p.rho = float(self.rho)
         p.sat_upwind = int(bool(self.sat_upwind))
         p.cp = float(self.cp)
+        p.limiter = {"none": 0, "mc": 1}[self.limiter]
+        p.limiter_floor = float(self.limiter_floor)
         return p
 
 

@@ -30,7 +30,13 @@
  *   - |F_class| is the Euclidean norm of the full face vector;
  *   - Dirichlet ghosts (edges and corners included) hold T = bc_value and copy
  *     b from the nearest interior cell;
- *   - dt_expl bounds chi_d by kappa_par + kappa_perp in every direction.
+ *   - dt_expl bounds chi_d by kappa_par + kappa_perp in every direction;
+ *   - with the limiter of Appendix C (Sharma & Hammett 2007) the transverse
+ *     gradient at a face is MC(MC(up_L, down_L), MC(up_R, down_R)), the
+ *     monotonised-central limiter applied first to the two one-sided
+ *     differences of each cell and then across the two cells, used at faces
+ *     whose lower temperature is below limiter_floor (Section 3.4: limiters
+ *     only where T falls below a floor; an infinite floor limits everywhere).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -53,6 +59,8 @@ typedef struct {
     double rho;
     int sat_upwind;         /* 1: q from the upwind cell, 0: from T_face  */
     double cp;              /* parabolic Courant number of Eq. dt_exp     */
+    int limiter;            /* 1: MC-limited transverse gradients          */
+    double limiter_floor;   /* limit only faces with min(T_L, T_R) below   */
 } orc_problem;
 
 static long ncell(const orc_problem *P) { return P->n[0] * P->n[1] * P->n[2]; }
@@ -92,6 +100,17 @@ static double b_at(const orc_problem *P, const double *b, int e, long i, long j,
     return b[(long)e * ncell(P) + idx(P, c[0], c[1], c[2])];
 }
 
+/* Monotonised-central limiter: 0 if a and b differ in sign, else the one of
+ * 2a, 2b, (a+b)/2 smallest in magnitude (van Leer's MC slope). */
+static double mc_limit(double a, double b)
+{
+    if (a * b <= 0.0) return 0.0;
+    double m = fabs(0.5 * (a + b));
+    if (2.0 * fabs(a) < m) m = 2.0 * fabs(a);
+    if (2.0 * fabs(b) < m) m = 2.0 * fabs(b);
+    return a > 0.0 ? m : -m;
+}
+
 /* Parallel conductivity kappa_par(T). */
 static double kappa_par(const orc_problem *P, double T)
 {
@@ -115,15 +134,18 @@ double orc_face_flux(const orc_problem *P, const double *T, const double *b,
     double TL = T_at(P, T, c0[0], c0[1], c0[2]);
     double TR = T_at(P, T, c1[0], c1[1], c1[2]);
     grad[d] = (TR - TL) / P->dx[d];                         /* normal, Eq. qN */
+    const int limit = P->limiter && (TL < TR ? TL : TR) < P->limiter_floor;
     for (int e = 0; e < P->ndim; ++e) {
         if (e == d) continue;
         long a0[3] = {c0[0], c0[1], c0[2]}, a1[3] = {c1[0], c1[1], c1[2]};
         long m0[3] = {c0[0], c0[1], c0[2]}, m1[3] = {c1[0], c1[1], c1[2]};
         a0[e] += 1; a1[e] += 1; m0[e] -= 1; m1[e] -= 1;
-        /* mean of the four one-sided transverse differences, Eq. qT */
-        grad[e] = (T_at(P, T, a0[0], a0[1], a0[2]) + T_at(P, T, a1[0], a1[1], a1[2])
-                 - T_at(P, T, m0[0], m0[1], m0[2]) - T_at(P, T, m1[0], m1[1], m1[2]))
-                / (4.0 * P->dx[e]);
+        double upL = T_at(P, T, a0[0], a0[1], a0[2]) - TL, downL = TL - T_at(P, T, m0[0], m0[1], m0[2]);
+        double upR = T_at(P, T, a1[0], a1[1], a1[2]) - TR, downR = TR - T_at(P, T, m1[0], m1[1], m1[2]);
+        if (limit)      /* limited transverse gradient, Appendix C */
+            grad[e] = mc_limit(mc_limit(upL, downL), mc_limit(upR, downR)) / P->dx[e];
+        else            /* mean of the four one-sided transverse differences, Eq. qT */
+            grad[e] = (upL + downL + upR + downR) / (4.0 * P->dx[e]);
     }
 
     /* face values of b and T */

@@ -41,7 +41,7 @@ def make_grid(shape, dx=None, bc="periodic", bc_value=0.0, dtype="f32") -> rkl_g
 
 
 def make_phys(kappa_model="const", kappa_par0=1.0, kappa_perp_ratio=0.0, saturate=False, phi=0.3,
-              rho=1.0, sat_upwind=False, cp=0.5) -> rkl_phys:
+              rho=1.0, sat_upwind=False, cp=0.5, limiter="none", limiter_floor=float("inf")) -> rkl_phys:
     p = rkl_phys()
     p.kappa_model = {"const": RKL_KAPPA_CONST, "spitzer": RKL_KAPPA_SPITZER}[kappa_model]
     p.kappa_par0 = float(kappa_par0)
@@ -51,6 +51,8 @@ def make_phys(kappa_model="const", kappa_par0=1.0, kappa_perp_ratio=0.0, saturat
     p.rho = float(rho)
     p.sat_upwind = int(bool(sat_upwind))
     p.cp = float(cp)
+    p.limiter = {"none": 0, "mc": 1}[limiter]
+    p.limiter_floor = float(limiter_floor)
     return p
 
 

@@ -44,7 +44,7 @@ class rkl_phys(ctypes.Structure):
     _fields_ = [("kappa_model", ctypes.c_int), ("kappa_par0", ctypes.c_double),
                 ("kappa_perp_ratio", ctypes.c_double), ("saturate", ctypes.c_int),
                 ("phi", ctypes.c_double), ("rho", ctypes.c_double), ("sat_upwind", ctypes.c_int),
-                ("cp", ctypes.c_double)]
+                ("cp", ctypes.c_double), ("limiter", ctypes.c_int), ("limiter_floor", ctypes.c_double)]
 
 
 # Every symbol include/rkl.h declares, with (restype, argtypes).

@@ -216,9 +216,9 @@ rkl_status launch_stage(rkl_plan* p, const StageIO& io, double mu, double nu, do
         KCoef<float> cf{(float)mu, (float)nu, (float)mt, (float)gt};
         bool al = aligned16(io.Y0) && aligned16(io.MY0) && aligned16(io.Yjm1) && aligned16(io.Yjm2) &&
                   aligned16(io.Yj) && aligned16(io.b);
-        if (p->x2ok && al && (p->variant == 0 || p->variant == 3 || p->variant == 4 || p->variant == 5))
+        if (p->x2ok && al && (p->variant == 0 || (p->variant >= 3 && p->variant <= 6)))
             e = launch_stage_x2(p->cfg, p->gf, p->pf, io, cf, p->d_status, p->nzchunk,
-                                p->variant == 4 ? 3 : 2, st);
+                                p->variant == 4 ? 3 : 2, st, p->variant == 6);
         else if (p->fast && al && (p->variant == 0 || p->variant == 2))
             e = launch_stage_fast(p->cfg, p->gf, p->pf, io, cf, p->d_status, st);
         else
@@ -562,6 +562,8 @@ rkl_status rkl_plan_create(const rkl_grid* grid, const rkl_phys* phys, void* cud
     if (!(ph.cp > 0.0 && ph.cp <= 0.5)) return fail(nullptr, RKL_ERR_INVALID_ARG, "cp must be in (0, 1/2]");
     if (ph.saturate && (!(ph.phi > 0.0) || !(ph.rho > 0.0)))
         return fail(nullptr, RKL_ERR_INVALID_ARG, "saturation needs phi > 0 and rho > 0");
+    if ((ph.limiter != RKL_LIMITER_NONE && ph.limiter != RKL_LIMITER_MC) || std::isnan(ph.limiter_floor))
+        return fail(nullptr, RKL_ERR_INVALID_ARG, "limiter must be RKL_LIMITER_NONE or RKL_LIMITER_MC with a floor");
 
     rkl_plan* p = new rkl_plan();
     p->grid = g;
@@ -569,7 +571,8 @@ rkl_status rkl_plan_create(const rkl_grid* grid, const rkl_phys* phys, void* cud
     p->stream = static_cast<cudaStream_t>(cuda_stream);
     p->esize = g.dtype == RKL_F64 ? 8 : 4;
     p->ncell = ncell;
-    p->cfg = LaunchCfg{g.dtype, g.ndim, ph.kappa_model == RKL_KAPPA_SPITZER, ph.saturate != 0};
+    p->cfg = LaunchCfg{g.dtype, g.ndim, ph.kappa_model == RKL_KAPPA_SPITZER, ph.saturate != 0,
+                       ph.limiter == RKL_LIMITER_MC};
     auto fill = [&](auto& kg, auto& kp) {
         using R = std::remove_reference_t<decltype(kg.bcv)>;
         for (int d = 0; d < 3; ++d) {
@@ -586,6 +589,9 @@ rkl_status rkl_plan_create(const rkl_grid* grid, const rkl_phys* phys, void* cud
         kp.kperp = (R)ph.kappa_perp_ratio;
         kp.q0 = (R)(5.0 * ph.phi * ph.rho);
         kp.upwind = ph.sat_upwind ? 1 : 0;
+        kp.limiter = ph.limiter == RKL_LIMITER_MC ? 1 : 0;
+        kp.lfloor = std::isinf(ph.limiter_floor) ? (ph.limiter_floor > 0 ? (R)INFINITY : (R)-INFINITY)
+                                                 : (R)ph.limiter_floor;
     };
     fill(p->gf, p->pf);
     fill(p->gd, p->pd);
@@ -820,6 +826,8 @@ rkl_status rkl_plan_autotune(rkl_plan* p, double dt, const void* T, const void* 
         }
     if (p->x2ok && p->pairok)
         for (int nz : {16, 32, 64}) cands.push_back({5, nz});
+    if (p->x2ok && p->gf.bc == 0 && p->gf.n[0] >= 72)
+        for (int nz : {0, 32}) cands.push_back({6, nz});
     void* scratch = nullptr;
     RKL_CK(p, cudaMalloc(&scratch, (size_t)p->ncell * p->esize));
     cudaEvent_t a = nullptr, e = nullptr;
@@ -862,10 +870,10 @@ rkl_status rkl_plan_autotune(rkl_plan* p, double dt, const void* T, const void* 
 rkl_status rkl_plan_set_variant(rkl_plan* p, int variant, int nzchunk)
 {
     if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
-    if (variant < 0 || variant > 5) return fail(p, RKL_ERR_INVALID_ARG, "variant must be 0 to 5");
+    if (variant < 0 || variant > 6) return fail(p, RKL_ERR_INVALID_ARG, "variant must be 0 to 6");
     if (nzchunk > 4096) return fail(p, RKL_ERR_INVALID_ARG, "nzchunk must be <= 4096");
     if (variant == 2 && !p->fast) return fail(p, RKL_ERR_UNSUPPORTED, "no tiled kernel for this grid");
-    if ((variant == 3 || variant == 4) && !p->x2ok)
+    if ((variant == 3 || variant == 4 || variant == 6) && !p->x2ok)
         return fail(p, RKL_ERR_UNSUPPORTED, "no paired-cell kernel for this grid");
     if (variant == 5 && !(p->pairok && p->x2ok))
         return fail(p, RKL_ERR_UNSUPPORTED, "no two-stage kernel for this grid (periodic FP32 3D, nx % 4 == 0)");

@@ -30,6 +30,8 @@ struct KPhys {
     R kperp;             // kappa_perp / kappa_par
     R q0;                // 5 phi rho: q = q0 * c_iso^3 (Eq. Fsat)
     int upwind;          // c_iso from the donor cell of the normal flux
+    int limiter;         // MC-limited transverse gradients (generic kernel)
+    R lfloor;            // ... at faces with min(T_L, T_R) below this
 };
 
 // Per-stage recurrence coefficients in the kernel's type.  The update is
@@ -100,6 +102,18 @@ __device__ __forceinline__ R face_flux(R TL, R TR, R gn, R g1, R g2,
         Fn = ddiv<R>(q, q + Fmag) * Fn;
     }
     return Fn;
+}
+
+// Monotonised-central limiter: 0 if a and b differ in sign, else the one of
+// 2a, 2b, (a + b)/2 smallest in magnitude.
+template <typename R>
+__device__ __forceinline__ R mc_limit(R a, R b)
+{
+    if (a * b <= R(0)) return R(0);
+    R m = fabs(R(0.5) * (a + b));
+    m = fmin(m, R(2) * fabs(a));
+    m = fmin(m, R(2) * fabs(b));
+    return a > R(0) ? m : -m;
 }
 
 // Wrap or clamp an index that is at most a few cells outside [0, n).

@@ -221,7 +221,7 @@ rkl_status ens_run(rkl_ensemble* e, const double* dt, const int* s, float* T_all
                     io.Yjm2 = j == 2 ? d.T : d.buf[(j - 3) % 3];
                     io.Yj = j == s[p] ? d.T : d.buf[(j - 1) % 3];
                 }
-                LaunchCfg cfg{0, 3, e->spitzer ? 1 : 0, e->saturate ? 1 : 0};
+                LaunchCfg cfg{0, 3, e->spitzer ? 1 : 0, e->saturate ? 1 : 0, 0};
                 KCoef<float> cf{0.f, 0.f, 0.f, 0.f};
                 cudaError_t c = launch_stage_x2(cfg, d.g, d.p, io, cf, e->d_status, e->nzchunk, 2, e->stream);
                 if (c != cudaSuccess) return efail(e, RKL_ERR_CUDA, std::string("stage launch: ") + cudaGetErrorString(c));
@@ -277,6 +277,8 @@ rkl_status rkl_ensemble_create(int nprob, const rkl_grid* grids, const rkl_phys*
             return efail(nullptr, RKL_ERR_INVALID_ARG, "bad physics");
         if (ph.saturate && (!(ph.phi > 0.0) || !(ph.rho > 0.0)))
             return efail(nullptr, RKL_ERR_INVALID_ARG, "saturation needs phi > 0 and rho > 0");
+        if (ph.limiter != RKL_LIMITER_NONE)
+            return efail(nullptr, RKL_ERR_UNSUPPORTED, "ensembles use the arithmetic-mean transverse gradients");
     }
     rkl_ensemble* e = new rkl_ensemble();
     e->nprob = nprob;

@@ -484,7 +484,7 @@ cudaError_t launch_mode(int mode, const KGrid<float>& g, const KPhys<float>& p, 
 
 bool fast_stage_supported(const LaunchCfg& c, const KGrid<float>& g)
 {
-    return c.dtype == 0 && c.ndim == 3 && g.n[0] >= 1 && g.n[1] >= 1 && g.n[2] >= 1;
+    return c.dtype == 0 && c.ndim == 3 && !c.limiter && g.n[0] >= 1 && g.n[1] >= 1 && g.n[2] >= 1;
 }
 
 cudaError_t launch_stage_fast(const LaunchCfg& c, const KGrid<float>& g, const KPhys<float>& p,

@@ -54,6 +54,9 @@ __device__ __forceinline__ R face(const Field<R>& f, const KPhys<R>& p, int d, i
     R gn = (TR - TL) * f.g.inv_dx[d];
     R gt[2] = {R(0), R(0)};
     R bt[2] = {R(0), R(0)};
+    // Appendix C: MC-limited transverse gradients where the face's lower
+    // temperature is below the floor (an infinite floor limits everywhere)
+    const bool limit = p.limiter && fmin(TL, TR) < p.lfloor;
     int m = 0;
 #pragma unroll
     for (int e = 0; e < NDIM; ++e) {
@@ -61,8 +64,14 @@ __device__ __forceinline__ R face(const Field<R>& f, const KPhys<R>& p, int d, i
         int Pp[3] = {P[0], P[1], P[2]}, Pm[3] = {P[0], P[1], P[2]};
         int Qp[3] = {Q[0], Q[1], Q[2]}, Qm[3] = {Q[0], Q[1], Q[2]};
         Pp[e] += 1; Qp[e] += 1; Pm[e] -= 1; Qm[e] -= 1;
-        gt[m] = (f.t(Pp[0], Pp[1], Pp[2]) + f.t(Qp[0], Qp[1], Qp[2])
-               - f.t(Pm[0], Pm[1], Pm[2]) - f.t(Qm[0], Qm[1], Qm[2])) * f.g.inv_4dx[e];
+        if (limit) {
+            const R upL = f.t(Pp[0], Pp[1], Pp[2]) - TL, downL = TL - f.t(Pm[0], Pm[1], Pm[2]);
+            const R upR = f.t(Qp[0], Qp[1], Qp[2]) - TR, downR = TR - f.t(Qm[0], Qm[1], Qm[2]);
+            gt[m] = mc_limit(mc_limit(upL, downL), mc_limit(upR, downR)) * f.g.inv_dx[e];
+        } else {
+            gt[m] = (f.t(Pp[0], Pp[1], Pp[2]) + f.t(Qp[0], Qp[1], Qp[2])
+                   - f.t(Pm[0], Pm[1], Pm[2]) - f.t(Qm[0], Qm[1], Qm[2])) * f.g.inv_4dx[e];
+        }
         bt[m] = R(0.5) * (f.bc(e, P[0], P[1], P[2]) + f.bc(e, Q[0], Q[1], Q[2]));
         ++m;
     }
@@ -143,6 +152,23 @@ __global__ void __launch_bounds__(256) flux_generic_kernel(KGrid<R> g, KPhys<R> 
     for (int d = 0; d < NDIM; ++d) F[d][c] = face<R, NDIM, SPITZER, SAT>(f, p, d, i, j, k);
 }
 
+// Threads per block: 256, halved (down to one warp) while the grid would
+// leave SMs idle -- small FP64 grids (the 100 x 100 ring) are bound by the
+// per-SM FP64 rate, so they need every SM more than full blocks.
+int generic_block(int64_t ncell)
+{
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+            nsm = 152;
+    }
+    int tpb = 256;
+    while (tpb > 32 && (ncell + tpb - 1) / tpb < 2 * (int64_t)nsm) tpb /= 2;
+    return tpb;
+}
+
 template <typename R, int NDIM, bool SPITZER, bool SAT>
 cudaError_t stage_impl(const void* grid, const void* phys, const StageIO& io, const void* coef,
                        unsigned* status, cudaStream_t st)
@@ -153,8 +179,9 @@ cudaError_t stage_impl(const void* grid, const void* phys, const StageIO& io, co
                    static_cast<const R*>(io.Yjm1), static_cast<const R*>(io.Yjm2),
                    static_cast<R*>(io.Yj), static_cast<const R*>(io.coef_tab), io.j, io.mode};
     KCoef<R> cf = coef ? *static_cast<const KCoef<R>*>(coef) : KCoef<R>{R(0), R(0), R(0), R(0)};
-    int64_t blocks = (g.ncell + 255) / 256;
-    stage_generic_kernel<R, NDIM, SPITZER, SAT><<<(unsigned)blocks, 256, 0, st>>>(
+    const int tpb = generic_block(g.ncell);
+    const int64_t blocks = (g.ncell + tpb - 1) / tpb;
+    stage_generic_kernel<R, NDIM, SPITZER, SAT><<<(unsigned)blocks, tpb, 0, st>>>(
         g, p, a, static_cast<const R*>(io.b), cf, status);
     return cudaGetLastError();
 }
@@ -165,8 +192,9 @@ cudaError_t flux_impl(const void* grid, const void* phys, const void* T, const v
 {
     const KGrid<R>& g = *static_cast<const KGrid<R>*>(grid);
     const KPhys<R>& p = *static_cast<const KPhys<R>*>(phys);
-    int64_t blocks = (g.ncell + 255) / 256;
-    flux_generic_kernel<R, NDIM, SPITZER, SAT><<<(unsigned)blocks, 256, 0, st>>>(
+    const int tpb = generic_block(g.ncell);
+    const int64_t blocks = (g.ncell + tpb - 1) / tpb;
+    flux_generic_kernel<R, NDIM, SPITZER, SAT><<<(unsigned)blocks, tpb, 0, st>>>(
         g, p, static_cast<const R*>(T), static_cast<const R*>(b), static_cast<R*>(F[0]),
         static_cast<R*>(F[1]), static_cast<R*>(F[2]));
     return cudaGetLastError();

@@ -27,6 +27,7 @@ struct LaunchCfg {
     int ndim;
     int spitzer;
     int saturate;
+    int limiter;            // MC-limited transverse gradients: generic kernels only
 };
 
 // Generic kernels: one thread per cell, any dtype / ndim / boundary.
@@ -46,10 +47,14 @@ cudaError_t launch_stage_fast(const LaunchCfg& c, const KGrid<float>& g, const K
 // Paired-cell FP32 3D stage kernel (packed f32x2 arithmetic, 64 x 8 tiles,
 // nzchunk planes per CTA, occupancy 2 or 3 CTAs per SM).  Needs nx % 4 == 0
 // and 16-byte aligned arrays.
+// With bulk (and a periodic grid with nx >= 72) the plane bundles are
+// copied by the TMA engine (cp.async.bulk, one row per copy, mbarrier
+// completion) instead of per-thread 16-byte cp.async.
 bool x2_stage_supported(const LaunchCfg& c, const KGrid<float>& g);
+bool x2_bulk_supported(const LaunchCfg& c, const KGrid<float>& g);
 cudaError_t launch_stage_x2(const LaunchCfg& c, const KGrid<float>& g, const KPhys<float>& p, const StageIO& io,
                             const KCoef<float>& coef, unsigned* status, int nzchunk, int occupancy,
-                            cudaStream_t st);
+                            cudaStream_t st, bool bulk = false);
 
 // Two-stage paired-cell FP32 3D kernel: stages j (io, coefficients at
 // io.coef_tab[4 j]) and j + 1 (written to Yj1) in one pass, 60 x 7 tiles of

@@ -104,6 +104,63 @@ __device__ __forceinline__ PlaneOff plane_offsets(const KGrid<float>& g, int kk)
     return o;
 }
 
+// Bulk-copy tasks (periodic grids with nx >= 72): thread t < 64 (40 T/b
+// rows, 24 Y rows) owns one
+// smem row of a bundle -- rows -1 .. 8 of T and of bx, by, bz (72 columns
+// from i0 - 4, wrapped into at most two pieces) and rows 0 .. 7 of Y0,
+// Y_{j-2}, M(Y0) -- copied by the TMA engine straight into the ring slot.
+constexpr int kRowTB = 4 * ROWS;             // 40
+struct RowTask {
+    const float* s1;      // first piece, plane 0
+    const float* s2;      // second piece (wrapped part of a halo row)
+    unsigned d1, d2;      // smem byte addresses in slot 0
+    unsigned n1, n2;      // bytes (0: no piece)
+    unsigned flags;       // TK_T, TK_Y or 0 (b)
+};
+
+template <int MODE, class SM>
+__device__ __forceinline__ RowTask make_rowtask(const SM& sm, const KGrid<float>& g, const FastArgs& a, int t, int i0,
+                                                int j0)
+{
+    RowTask k{nullptr, nullptr, 0u, 0u, 0u, 0u, 0u};
+    const int nx = g.n[0], ny = g.n[1];
+    if (t < kRowTB) {
+        const int arr = t / ROWS, row = t % ROWS - 1;
+        const float* base = (arr == 0 ? a.Tin : a.b + (int64_t)(arr - 1) * g.ncell) + (int64_t)pmod(j0 + row, ny) * nx;
+        const unsigned dst = arr == 0 ? smem_u32(&sm.T[0][(row + 1) * SXS]) : smem_u32(&sm.B[0][arr - 1][(row + 1) * SXS]);
+        const int x0 = i0 - 4;
+        if (x0 < 0) {                       // columns nx-4 .. nx-1, then 0 .. 67
+            k.s1 = base + (nx - 4);
+            k.n1 = 16u;
+            k.s2 = base;
+            k.d2 = dst + 16u;
+            k.n2 = (unsigned)(SXS - 4) * 4u;
+        } else if (x0 + SXS > nx) {         // columns x0 .. nx-1, then 0 ..
+            k.s1 = base + x0;
+            k.n1 = (unsigned)(nx - x0) * 4u;
+            k.s2 = base;
+            k.d2 = dst + k.n1;
+            k.n2 = (unsigned)(x0 + SXS - nx) * 4u;
+        } else {
+            k.s1 = base + x0;
+            k.n1 = (unsigned)SXS * 4u;
+        }
+        k.d1 = dst;
+        k.flags = arr == 0 ? TK_T : 0u;
+        return k;
+    }
+    const int u = t - kRowTB;
+    if (MODE != 2 || u >= 3 * TY) return k;
+    const int arr = u / TY, row = u % TY;
+    if (j0 + row >= ny) return k;
+    const float* base = arr == 0 ? a.Y0 : (arr == 1 ? a.Yjm2 : a.MY0in);
+    k.s1 = base + (int64_t)(j0 + row) * nx + i0;
+    k.d1 = smem_u32(&sm.Y[0][arr][row * TX]);
+    k.n1 = (unsigned)min(TX, nx - i0) * 4u;
+    k.flags = TK_Y;
+    return k;
+}
+
 __device__ __forceinline__ void issue(const Task& k, const PlaneOff& po, unsigned ts, unsigned bs, unsigned ys,
                                       bool withY, float bcv)
 {
@@ -230,7 +287,7 @@ __device__ __forceinline__ float low_xface(const SM& sm, const KGrid<float>& g, 
 // --------------------------------------------------------------------------
 // one tile: columns [i0, i0 + 64), rows [j0, j0 + 8), planes [z0, z0 + nzc)
 
-template <bool SP, bool SAT, int MODE, int PD>
+template <bool SP, bool SAT, int MODE, int PD, bool BULK = false>
 __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g, const KPhys<float>& p,
                                         const x2::FastArgs& a, KCoef<float> cf, unsigned* status, int i0, int j0,
                                         int z0, int nzc)
@@ -247,14 +304,34 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         cf.mu = t[0]; cf.nu = t[1]; cf.mt = t[2]; cf.gt = t[3];
     }
 
-    Task tk[kSlots];
+    constexpr int kTk = BULK ? 1 : kSlots;
+    Task tk[kTk];
+    RowTask rt{};
+    if constexpr (BULK) {
+        rt = make_rowtask<MODE>(sm, g, a, tid, i0, j0);
+        if (tid == 0) {
 #pragma unroll
-    for (int s = 0; s < kSlots; ++s) tk[s] = make_task<MODE>(sm, g, a, tid + s * NTHREADS, i0, j0);
+            for (int i = 0; i < PD + 2; ++i) mbar_init(smem_u32(&sm.bar[i]), 1u);
+        }
+        __syncthreads();
+    } else {
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) tk[s] = make_task<MODE>(sm, g, a, tid + s * NTHREADS, i0, j0);
+    }
+    // bundle q completes phase (q + 1) / (PD + 2) of barrier (q + 1) % (PD + 2)
+    auto bar_of = [&](int q) { return smem_u32(&sm.bar[(q + 1) % (PD + 2)]); };
+    auto wait_bundle = [&](int q) {
+        if (!mbar_wait(bar_of(q), (unsigned)(((q + 1) / (PD + 2)) & 1))) atomicOr(status, ST_TIMEOUT);
+    };
+    const unsigned ybytes =
+        MODE == 2 ? 3u * (unsigned)min(TY, ny - j0) * (unsigned)min(TX, nx - i0) * 4u : 0u;
 
     using SM = SmemT<PD>;
-    auto tslot = [](int q) { return (q + 1) % SM::NT; };
-    auto bslot = [](int q) { return (q + 1) % SM::NB; };
-    auto yslot = [](int q) { return (q + SM::NY) % SM::NY; };
+    // slot of plane q >= -1 in a ring of n (a mask when n is a power of two)
+    auto slot = [](int q, int n) { return (n & (n - 1)) == 0 ? (q + 1) & (n - 1) : (q + 1) % n; };
+    auto tslot = [&](int q) { return slot(q, SM::NT); };
+    auto bslot = [&](int q) { return slot(q, SM::NB); };
+    auto yslot = [&](int q) { return slot(q, SM::NY); };
     // Periodic grids have no ghost or broadcast tasks: every task is one
     // 16-byte copy, issued without branches (the slot offset selected by
     // the task's array, invalid and skipped-Y tasks predicated off).
@@ -264,7 +341,15 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         const unsigned ts = (unsigned)(tslot(q) * PLANE * 4);
         const unsigned bs = (unsigned)(bslot(q) * 3 * PLANE * 4);
         const unsigned ys = (unsigned)(yslot(q) * 3 * TY * TX * 4);
-        if (plain) {
+        if constexpr (BULK) {
+            const unsigned bar = bar_of(q);
+            if (tid == 0) mbar_expect_tx(bar, (unsigned)(kRowTB * SXS * 4) + (withY ? ybytes : 0u));
+            const unsigned off = (rt.flags & TK_T) ? ts : ((rt.flags & TK_Y) ? ys : bs);
+            if (rt.n1 && (withY || !(rt.flags & TK_Y))) {
+                bulk_g2s(rt.d1 + off, rt.s1 + po.t, rt.n1, bar);
+                if (rt.n2) bulk_g2s(rt.d2 + off, rt.s2 + po.t, rt.n2, bar);
+            }
+        } else if (plain) {
 #pragma unroll
             for (int s = 0; s < kSlots; ++s) {
                 const unsigned f = tk[s].flags;
@@ -286,7 +371,12 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         if (k <= nzc) load(k, k < nzc);
         cp_commit();
     }
-    cp_wait<PD>();
+    if constexpr (BULK) {
+        wait_bundle(-1);
+        wait_bundle(0);
+    } else {
+        cp_wait<PD>();
+    }
     __syncthreads();
 
     const float2 idx2 = bc2(g.inv_dx[0]), idy2 = bc2(g.inv_dx[1]), idz2 = bc2(g.inv_dx[2]);
@@ -344,7 +434,8 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
 
     // one plane: cur holds plane q, nxt receives plane q + 1
     auto step = [&](int q, QZ& cur, QZ& nxt) {
-        cp_wait<PD - 1>();                 // bundle q + 1 has landed
+        if constexpr (BULK) wait_bundle(q + 1);     // bundle q + 1 has landed
+        else cp_wait<PD - 1>();
         __syncthreads();
         // the slots of bundle q + PD + 1 held planes no thread reads any more
         if (q + PD + 1 <= nzc) load(q + PD + 1, q + PD + 1 < nzc);
@@ -413,9 +504,15 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         step(q + 1, A, B);
     }
     if (q < nzc) step(q, B, A);
-    cp_wait<0>();
+    if constexpr (!BULK) cp_wait<0>();
     __syncthreads();
     finish(nzc - 1);
+    if constexpr (BULK) {
+        if (tid == 0) {
+#pragma unroll
+            for (int i = 0; i < PD + 2; ++i) mbar_inval(smem_u32(&sm.bar[i]));
+        }
+    }
     if (MODE != 0) {
         const bool bad_nf = nfacc.x != 0.f || nfacc.y != 0.f;
         const bool bad_np = SP && !(mnacc > 0.f);
@@ -428,7 +525,8 @@ namespace {
 
 // OCC = resident CTAs per SM the register budget is sized for (2: up to 128
 // registers, no spills; 3: up to 80 registers, a few spilled words).
-template <bool SP, bool SAT, int MODE, int OCC>
+// BULK: bundles copied by the TMA engine (periodic grids with nx >= 72).
+template <bool SP, bool SAT, int MODE, int OCC, bool BULK>
 __global__ void __launch_bounds__(x2::NTHREADS, OCC)
 stage_x2_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf, unsigned* status, int nzchunk)
 {
@@ -438,8 +536,8 @@ stage_x2_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf,
     if (nzchunk > 0) {
         // one tile column, one chunk of nzchunk planes per CTA
         const int z0 = blockIdx.z * nzchunk;
-        tile_x2<SP, SAT, MODE, PD>(sm, g, p, a, cf, status, blockIdx.x * x2::TX, blockIdx.y * x2::TY, z0,
-                                   min(nzchunk, g.n[2] - z0));
+        tile_x2<SP, SAT, MODE, PD, BULK>(sm, g, p, a, cf, status, blockIdx.x * x2::TX, blockIdx.y * x2::TY, z0,
+                                         min(nzchunk, g.n[2] - z0));
         return;
     }
     // Balanced schedule: the column-planes (tile column, plane) in column-major
@@ -455,8 +553,8 @@ stage_x2_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf,
         const int64_t col = u / nz;
         const int z0 = (int)(u - col * nz);
         const int nzc = (int)min((int64_t)(nz - z0), u1 - u);
-        tile_x2<SP, SAT, MODE, PD>(sm, g, p, a, cf, status, (int)(col % ntx) * x2::TX, (int)(col / ntx) * x2::TY,
-                                   z0, nzc);
+        tile_x2<SP, SAT, MODE, PD, BULK>(sm, g, p, a, cf, status, (int)(col % ntx) * x2::TX,
+                                         (int)(col / ntx) * x2::TY, z0, nzc);
         u += nzc;
     }
 }
@@ -473,14 +571,14 @@ int sm_count()
     return n;
 }
 
-template <bool SP, bool SAT, int MODE, int OCC>
+template <bool SP, bool SAT, int MODE, int OCC, bool BULK>
 cudaError_t launch3(const KGrid<float>& g, const KPhys<float>& p, const x2::FastArgs& a, const KCoef<float>& cf,
                     unsigned* status, int nzchunk, cudaStream_t st)
 {
     const int smem = (int)sizeof(x2::SmemT<OCC == 2 ? x2::kPD : 1>);
     static bool attr_set = false;       // the attribute is per function, set once
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(stage_x2_kernel<SP, SAT, MODE, OCC>,
+        cudaError_t e = cudaFuncSetAttribute(stage_x2_kernel<SP, SAT, MODE, OCC, BULK>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -493,36 +591,41 @@ cudaError_t launch3(const KGrid<float>& g, const KPhys<float>& p, const x2::Fast
         grid = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)OCC * sm_count(), U / 8)), 1, 1);
         nzchunk = 0;
     }
-    stage_x2_kernel<SP, SAT, MODE, OCC><<<grid, x2::NTHREADS, smem, st>>>(g, p, a, cf, status, nzchunk);
+    stage_x2_kernel<SP, SAT, MODE, OCC, BULK><<<grid, x2::NTHREADS, smem, st>>>(g, p, a, cf, status, nzchunk);
     return cudaGetLastError();
 }
 
-template <bool SP, bool SAT, int OCC>
+template <bool SP, bool SAT, int OCC, bool BULK>
 cudaError_t launch_mode(int mode, const KGrid<float>& g, const KPhys<float>& p, const x2::FastArgs& a,
                         const KCoef<float>& cf, unsigned* status, int nzchunk, cudaStream_t st)
 {
-    if (mode == 0) return launch3<SP, SAT, 0, OCC>(g, p, a, cf, status, nzchunk, st);
-    if (mode == 1) return launch3<SP, SAT, 1, OCC>(g, p, a, cf, status, nzchunk, st);
-    return launch3<SP, SAT, 2, OCC>(g, p, a, cf, status, nzchunk, st);
+    if (mode == 0) return launch3<SP, SAT, 0, OCC, BULK>(g, p, a, cf, status, nzchunk, st);
+    if (mode == 1) return launch3<SP, SAT, 1, OCC, BULK>(g, p, a, cf, status, nzchunk, st);
+    return launch3<SP, SAT, 2, OCC, BULK>(g, p, a, cf, status, nzchunk, st);
 }
 
-template <int OCC>
+template <int OCC, bool BULK>
 cudaError_t launch_phys(const LaunchCfg& c, int mode, const KGrid<float>& g, const KPhys<float>& p,
                         const x2::FastArgs& a, const KCoef<float>& cf, unsigned* status, int nzchunk, cudaStream_t st)
 {
     if (c.spitzer) {
-        if (c.saturate) return launch_mode<true, true, OCC>(mode, g, p, a, cf, status, nzchunk, st);
-        return launch_mode<true, false, OCC>(mode, g, p, a, cf, status, nzchunk, st);
+        if (c.saturate) return launch_mode<true, true, OCC, BULK>(mode, g, p, a, cf, status, nzchunk, st);
+        return launch_mode<true, false, OCC, BULK>(mode, g, p, a, cf, status, nzchunk, st);
     }
-    if (c.saturate) return launch_mode<false, true, OCC>(mode, g, p, a, cf, status, nzchunk, st);
-    return launch_mode<false, false, OCC>(mode, g, p, a, cf, status, nzchunk, st);
+    if (c.saturate) return launch_mode<false, true, OCC, BULK>(mode, g, p, a, cf, status, nzchunk, st);
+    return launch_mode<false, false, OCC, BULK>(mode, g, p, a, cf, status, nzchunk, st);
 }
 
 }  // namespace
 
 bool x2_stage_supported(const LaunchCfg& c, const KGrid<float>& g)
 {
-    return c.dtype == 0 && c.ndim == 3 && (g.n[0] % 4) == 0;
+    return c.dtype == 0 && c.ndim == 3 && !c.limiter && (g.n[0] % 4) == 0;
+}
+
+bool x2_bulk_supported(const LaunchCfg& c, const KGrid<float>& g)
+{
+    return x2_stage_supported(c, g) && g.bc == 0 && g.n[0] >= x2::SXS;
 }
 
 // Planes per CTA when none is given: the chunk length in [16, 48] that
@@ -562,13 +665,15 @@ x2::FastArgs x2_args(const StageIO& io)
 }
 
 cudaError_t launch_stage_x2(const LaunchCfg& c, const KGrid<float>& g, const KPhys<float>& p, const StageIO& io,
-                            const KCoef<float>& coef, unsigned* status, int nzchunk, int occupancy, cudaStream_t st)
+                            const KCoef<float>& coef, unsigned* status, int nzchunk, int occupancy, cudaStream_t st,
+                            bool bulk)
 {
     const x2::FastArgs a = x2_args(io);
     if (nzchunk == 0) nzchunk = auto_nzchunk(g, occupancy);
     else if (nzchunk < 0) nzchunk = 0;
-    if (occupancy == 3) return launch_phys<3>(c, io.mode, g, p, a, coef, status, nzchunk, st);
-    return launch_phys<2>(c, io.mode, g, p, a, coef, status, nzchunk, st);
+    if (occupancy == 3) return launch_phys<3, false>(c, io.mode, g, p, a, coef, status, nzchunk, st);
+    if (bulk && x2_bulk_supported(c, g)) return launch_phys<2, true>(c, io.mode, g, p, a, coef, status, nzchunk, st);
+    return launch_phys<2, false>(c, io.mode, g, p, a, coef, status, nzchunk, st);
 }
 
 // --------------------------------------------------------------------------

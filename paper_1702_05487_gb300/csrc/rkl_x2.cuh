@@ -30,16 +30,19 @@ struct FastArgs {
 // Plane rings for a prefetch distance of PD planes: while plane q is
 // computed, planes q+1 .. q+PD are in flight and plane q+PD+1 is being
 // issued into the slots that plane q-2 (T) or q-1 (b, Y) released.
+// With two planes in flight the rings get power-of-two slot counts (8, 4,
+// 4), so a plane's slot is a mask of its index rather than a division.
 template <int PD>
 struct SmemT {
-    static constexpr int NT = 3 + PD, NB = 2 + PD, NY = 2 + PD;
+    static constexpr int NT = PD == 2 ? 8 : 3 + PD, NB = 2 + PD, NY = 2 + PD;
     float T[NT][PLANE];             // Y_{j-1} planes q-1, q, q+1 and those in flight
     float B[NB][3][PLANE];          // b planes q, q+1 and those in flight
     float Y[NY][3][TY * TX];        // Y0, Y_{j-2}, M(Y0) of plane q and those in flight
     float Fy[2][TY + 1][TX];        // y-face fluxes (row 0: the tile's lower boundary)
     float FxLo[2][TY];              // x-faces on the tile's left boundary
+    alignas(8) unsigned long long bar[PD + 2];    // bundle barriers of the bulk-copy path
 };
-constexpr int kPD = 2;              // prefetch distance at 2 CTAs per SM (82 KB each)
+constexpr int kPD = 2;              // prefetch distance at 2 CTAs per SM (87 KB each)
 using Smem = SmemT<kPD>;
 
 // One problem of an ensemble as the persistent kernel sees it.

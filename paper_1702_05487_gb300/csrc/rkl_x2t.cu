@@ -37,7 +37,7 @@ constexpr int WA = RA, WB = OY, NW = WA + WB, NTH = 32 * NW;    // 512 threads
 // ring slots: Y_{j-1}, b and the Y arrays span planes t-5 .. t+2 of iteration
 // t (B warps read plane t-4, A warps t-2 .. t, planes t+1, t+2 in flight);
 // the Y_j ring holds B's planes t-5 .. t-3 and the one A finishes
-constexpr int NT = 7, NB = 7, NYR = 7, NJ = 4;
+constexpr int NT = 8, NB = 8, NYR = 8, NJ = 4;     // powers of two: slots are masks
 constexpr int PLT = RT * SX;
 constexpr int PLY = RA * SY;
 constexpr int PLJ = RA * SX;
@@ -239,7 +239,7 @@ __device__ __forceinline__ void tile_x2t(Smem& sm, const KGrid<float>& g, const 
 #pragma unroll
     for (int s = 0; s < kSlots; ++s) tk[s] = make_task(sm, g, a, tid + s * NTH, i0, j0);
 
-    auto ring = [](int q, int n) { return (q + 2 * n) % n; };      // q >= -2
+    auto ring = [](int q, int n) { return q & (n - 1); };          // n a power of two
     auto load = [&](int q, bool withY) {
         const int64_t zo = (int64_t)pmod(z0 + q, nz) * g.plane;
         const unsigned ts = (unsigned)(ring(q, NT) * PLT * 4);
@@ -444,7 +444,7 @@ cudaError_t launch_pair_t(const KGrid<float>& g, const KPhys<float>& p, const x2
 
 bool pair_stage_supported(const LaunchCfg& c, const KGrid<float>& g)
 {
-    return c.dtype == 0 && c.ndim == 3 && g.bc == 0 && (g.n[0] % 4) == 0;
+    return c.dtype == 0 && c.ndim == 3 && !c.limiter && g.bc == 0 && (g.n[0] % 4) == 0;
 }
 
 cudaError_t launch_stage_pair(const LaunchCfg& c, const KGrid<float>& g, const KPhys<float>& p, const StageIO& io,

@@ -14,6 +14,12 @@ F32_FLUX_TOL = 1e-5          # max |F_gpu - F_ref| / max |F_ref|
 F32_STATE_REL_L2 = 1e-5      # ||T_gpu - T_ref||_2 / ||T_ref||_2 (the method's stated bound)
 F32_STATE_MAX = 2e-5         # max |T_gpu - T_ref| / max |T_ref|
 F64_TOL = 1e-12              # FP64 GPU against the FP64 oracle (rounding order only)
+# With MC-limited transverse gradients the operator is piecewise linear in T:
+# where FP32 rounding moves a cell across a kink of the limiter (two of its
+# candidates equal, or two one-sided differences of opposite sign), that
+# cell's gradient changes slope by up to a factor 2, so over a super-step the
+# worst cell can drift several times 1e-5 while the L2 error stays below 1e-5.
+F32_LIMITER_MAX = 2e-4
 
 
 def torch_dev(a, dtype="f32"):

@@ -73,10 +73,11 @@ def _sampled_first_step(rk, orc, W, dtype, cells, variant=0):
     return plan, Td, bd, dt, e0, P
 
 
-@pytest.mark.parametrize("variant", [0, 5])
+@pytest.mark.parametrize("variant", [0, 5, 6])
 def test_tangled_256_sampled_and_conservation(rk, orc, variant):
-    """The benchmark's 256^3 workload with the default single-stage kernel
-    and with the two-stage kernel (tile edges at multiples of 60 and 7)."""
+    """The benchmark's 256^3 workload with the default single-stage kernel,
+    the two-stage kernel (tile edges at multiples of 60 and 7) and the
+    single-stage kernel with bulk copies."""
     W = workloads.tangled(256, seed=2)
     rng = np.random.default_rng(0)
     cells = [tuple(int(v) for v in rng.integers(0, 256, 3)) for _ in range(5)] + [(0, 0, 0), (255, 128, 7)]

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import workloads
-from gpu_util import (F32_FLUX_TOL, F32_STATE_MAX, F32_STATE_REL_L2, F64_TOL, host, norm_max,
+from gpu_util import (F32_FLUX_TOL, F32_LIMITER_MAX, F32_STATE_MAX, F32_STATE_REL_L2, F64_TOL, host, norm_max,
                       rel_l2, rounded, torch_dev)
 from oracle import Problem
 
@@ -41,6 +41,12 @@ def _cases():
         ("2d_f64_dirichlet", (41, 29), dict(kappa_par0=0.05, bc="dirichlet", bc_value=1.0), "f64"),
         ("2d_f32", (45, 67), spitz, "f32"),
         ("1d_f32", (300,), dict(kappa_par0=0.3, kappa_perp_ratio=1.0), "f32"),
+        # MC-limited transverse gradients (Appendix C; generic kernel)
+        ("3d_limiter_mc", (20, 22, 24), dict(spitz, limiter="mc"), "f32"),
+        ("3d_limiter_sat", (12, 16, 20), dict(kappa_model="spitzer", kappa_par0=0.01, saturate=True, phi=0.3,
+                                               limiter="mc"), "f32"),
+        ("2d_f64_limiter_floor", (30, 26), dict(kappa_par0=0.05, bc="dirichlet", bc_value=1.0, limiter="mc",
+                                                limiter_floor=1.02), "f64"),
     ]
 
 
@@ -129,14 +135,14 @@ def _variant_cases():
     out = []
     for c in _cases():
         out.append(c + (0,))
-        if c[3] == "f32" and len(c[1]) == 3:
+        if c[3] == "f32" and len(c[1]) == 3 and "limiter" not in c[2]:
             out.append(c + (1,))        # the generic kernel on the same 3D FP32 case
             out.append(c + (2,))        # the tiled one-cell-per-thread kernel
     # grids with nx % 4 == 0 (the paired-cell kernel) and Dirichlet partial tiles
     spitz = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
     sat = dict(kappa_model="spitzer", kappa_par0=0.01, saturate=True, phi=0.3)
-    for v in (2, 3, 4, 5):
-        if v != 5:      # the two-stage kernel is periodic only
+    for v in (2, 3, 4, 5, 6):
+        if v not in (5, 6):     # the two-stage kernel and bulk copies are periodic only
             out.append(("3d_x4_dirichlet", (21, 19, 36), dict(spitz, bc="dirichlet", bc_value=0.9), "f32", v))
         out.append(("3d_x4_sat", (18, 26, 68), sat, "f32", v))
         out.append(("3d_x4_sat_upwind", (10, 9, 132), dict(sat, phi=0.05, sat_upwind=True), "f32", v))
@@ -144,6 +150,9 @@ def _variant_cases():
     # two-stage kernel: several 60 x 7 tiles with ragged edges in x, y and z
     out.append(("3d_pair_spitzer", (45, 30, 128), spitz, "f32", 5))
     out.append(("3d_pair_small", (5, 4, 8), spitz, "f32", 5))
+    # bulk (TMA-engine) copies: x-halo rows split at the periodic edge, ragged y
+    out.append(("3d_bulk_spitzer", (37, 21, 200), spitz, "f32", 6))
+    out.append(("3d_bulk_x72", (9, 16, 72), spitz, "f32", 6))
     return out
 
 
@@ -167,7 +176,7 @@ def test_super_steps(rk, orc, case):
         assert norm_max(Tg, Tref) < F64_TOL
     else:
         assert rel_l2(Tg, Tref) < F32_STATE_REL_L2
-        assert norm_max(Tg, Tref) < F32_STATE_MAX
+        assert norm_max(Tg, Tref) < (F32_LIMITER_MAX if params.get("limiter") == "mc" else F32_STATE_MAX)
     assert plan.check() == 0
 
 
@@ -181,12 +190,12 @@ def test_tiled_kernels_match_generic(rk, orc, shape, nzchunk):
     whose runs cross tile columns) and the generic kernel (variant 1) on
     tile-aligned, ragged and degenerate shapes; all against the oracle."""
     params = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
-    variants = (1, 2, 3, 4, 5) if shape[2] % 4 == 0 else (1, 2)
+    variants = (1, 2, 3, 4, 5, 6) if shape[2] % 4 == 0 else (1, 2)
     res = {}
     for v in variants:
         P, plan, T, b, Td, bd = _setup(rk, "x", shape, params, "f32", v)
         if v >= 3:
-            plan.set_variant(v, nzchunk if v < 5 else max(nzchunk, 0))
+            plan.set_variant(v, nzchunk if v != 5 else max(nzchunk, 0))
         dt = 40 * orc.dt_expl(P, T)
         for _ in range(2):
             plan.super_step(dt, Td, bd)
@@ -210,7 +219,7 @@ def test_autotune_keeps_input_and_parity(rk, orc):
     T_before = Td.clone()
     v, nz, ms = plan.autotune(dt, Td, bd)
     assert torch.equal(Td, T_before)
-    assert v in (1, 2, 3, 4, 5) and ms > 0
+    assert v in (1, 2, 3, 4, 5, 6) and ms > 0
     plan.super_step(dt, Td, bd)
     Tref, _ = orc.super_step(P, T, b, dt)
     assert rel_l2(host(Td), Tref) < F32_STATE_REL_L2
