@@ -25,30 +25,36 @@ namespace x2 {
 
 __device__ __forceinline__ int off(int r, int c) { return (r + 1) * SXS + c + 4; }
 
-// Copy tasks fixed per thread for the whole tile: a bundle is T and b
-// (4 arrays x 10 rows x 18 chunks of 16 B, halo ring included) plus Y0,
-// Y_{j-2}, M(Y0) (3 arrays x 8 rows x 16 chunks).  Rows must start on a
+// Copy tasks fixed per thread for the whole tile, grouped by ring so that a
+// thread's slot s always feeds the same ring (its slot offset is known at
+// compile time): slot 0 a 16-byte chunk of T (10 rows x 18 chunks, halo
+// ring included), slots 1-3 chunks of bx, by, bz (3 x 180), slots 4-5
+// chunks of Y0, Y_{j-2}, M(Y0) (3 x 8 rows x 16).  Rows must start on a
 // 16-byte boundary (nx % 4 == 0); chunks past the grid edge wrap
-// (periodic), hold the ghost value (Dirichlet T) or are skipped (Y).
-enum : unsigned { TK_VALID = 1u, TK_T = 2u, TK_GHOST = 4u, TK_Y = 8u, TK_BCAST = 16u };
+// (periodic), hold the ghost value (Dirichlet T), repeat the nearest
+// interior b (Dirichlet, past the x edge) or are skipped (Y).  The smem
+// address is 16-byte aligned, so its low bits carry the task's flags.
+enum : unsigned { TK_VALID = 1u, TK_GHOST = 2u, TK_BCAST = 4u, TK_FLAGS = 15u, TK_T = 16u, TK_Y = 32u };
 struct Task {
     const float* src;     // chunk address in plane 0
-    unsigned dst;         // smem byte address in slot 0
-    unsigned flags;
+    unsigned dst;         // smem byte address in slot 0 | flags
 };
-constexpr int kTB = 4 * ROWS * CPR;          // 720
-constexpr int kY = 3 * TY * (TX / 4);        // 384
-constexpr int kTasks = kTB + kY;             // 1104
-constexpr int kSlots = (kTasks + NTHREADS - 1) / NTHREADS;   // 5
+constexpr int kTT = ROWS * CPR;                  // 180 T chunks
+constexpr int kTBc = 3 * ROWS * CPR;             // 540 b chunks
+constexpr int kY = 3 * TY * (TX / 4);            // 384 Y chunks
+constexpr int kSlotB = 1, kSlotY = 4, kSlots = 6;
+static_assert(kTT <= NTHREADS && kTBc <= 3 * NTHREADS && kY <= 2 * NTHREADS, "task slots");
 
 template <int MODE, class SM>
-__device__ __forceinline__ Task make_task(const SM& sm, const KGrid<float>& g, const FastArgs& a, int t, int i0,
-                                          int j0)
+__device__ __forceinline__ Task make_task(const SM& sm, const KGrid<float>& g, const FastArgs& a, int s, int tid,
+                                          int i0, int j0)
 {
-    Task k{nullptr, 0u, 0u};
+    Task k{nullptr, 0u};
     const int nx = g.n[0], ny = g.n[1];
-    if (t < kTB) {
-        const int arr = t / (ROWS * CPR), r = t % (ROWS * CPR);
+    if (s < kSlotY) {
+        const int t = s == 0 ? tid : tid + (s - kSlotB) * NTHREADS;
+        if (t >= (s == 0 ? kTT : kTBc)) return k;
+        const int arr = s == 0 ? 0 : 1 + t / (ROWS * CPR), r = t % (ROWS * CPR);
         const int row = r / CPR - 1, c = (r % CPR) * 4 - 4;
         int gy = j0 + row, gx = i0 + c;
         bool ghost = false;
@@ -62,27 +68,23 @@ __device__ __forceinline__ Task make_task(const SM& sm, const KGrid<float>& g, c
             if (g.bc == 1) { ghost = xghost = true; gx = gx < 0 ? 0 : nx - 1; } else gx = pmod(gx, nx);
         }
         const int64_t rowoff = (int64_t)gy * nx + gx;
-        k.flags = TK_VALID;
         if (arr == 0) {
-            k.flags |= TK_T | (ghost ? TK_GHOST : 0u);
             k.src = a.Tin + rowoff;
-            k.dst = smem_u32(&sm.T[0][off(row, c)]);
+            k.dst = smem_u32(&sm.T[0][off(row, c)]) | TK_VALID | (ghost ? TK_GHOST : 0u);
         } else {
-            k.flags |= xghost ? TK_BCAST : 0u;
             k.src = a.b + (int64_t)(arr - 1) * g.ncell + rowoff;
-            k.dst = smem_u32(&sm.B[0][arr - 1][off(row, c)]);
+            k.dst = smem_u32(&sm.B[0][arr - 1][off(row, c)]) | TK_VALID | (xghost ? TK_BCAST : 0u);
         }
         return k;
     }
-    t -= kTB;
+    const int t = tid + (s - kSlotY) * NTHREADS;
     if (MODE != 2 || t >= kY) return k;
     const int arr = t / (TY * (TX / 4)), r = t % (TY * (TX / 4));
     const int row = r / (TX / 4), c = (r % (TX / 4)) * 4;
     if (j0 + row >= ny || i0 + c >= nx) return k;
     const float* base = arr == 0 ? a.Y0 : (arr == 1 ? a.Yjm2 : a.MY0in);
     k.src = base + (int64_t)(j0 + row) * nx + i0 + c;
-    k.dst = smem_u32(&sm.Y[0][arr][row * TX + c]);
-    k.flags = TK_VALID | TK_Y;
+    k.dst = smem_u32(&sm.Y[0][arr][row * TX + c]) | TK_VALID;
     return k;
 }
 
@@ -161,22 +163,23 @@ __device__ __forceinline__ RowTask make_rowtask(const SM& sm, const KGrid<float>
     return k;
 }
 
-__device__ __forceinline__ void issue(const Task& k, const PlaneOff& po, unsigned ts, unsigned bs, unsigned ys,
-                                      bool withY, float bcv)
+// One task of slot s in the general (Dirichlet) case; off is the slot
+// offset of the task's ring.
+__device__ __forceinline__ void issue(const Task& k, int s, const PlaneOff& po, unsigned off, bool withY,
+                                      float bcv)
 {
-    const unsigned f = k.flags;
+    const unsigned f = k.dst & TK_FLAGS;
     if (!(f & TK_VALID)) return;
-    if (f & TK_Y) {
-        if (withY) cp16(k.dst + ys, k.src + po.t);
-        return;
+    const unsigned d = (k.dst & ~TK_FLAGS) + off;
+    if (s >= kSlotY) {
+        if (withY) cp16(d, k.src + po.t);
+    } else if (s == 0) {
+        if (po.zghost || (f & TK_GHOST)) st4(d, bcv);
+        else cp16(d, k.src + po.t);
+    } else {
+        if (f & TK_BCAST) st4(d, __ldcg(k.src + po.b));
+        else cp16(d, k.src + po.b);
     }
-    if (f & TK_T) {
-        if (po.zghost || (f & TK_GHOST)) st4(k.dst + ts, bcv);
-        else cp16(k.dst + ts, k.src + po.t);
-        return;
-    }
-    if (f & TK_BCAST) st4(k.dst + bs, __ldcg(k.src + po.b));
-    else cp16(k.dst + bs, k.src + po.b);
 }
 
 // --------------------------------------------------------------------------
@@ -316,7 +319,7 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         __syncthreads();
     } else {
 #pragma unroll
-        for (int s = 0; s < kSlots; ++s) tk[s] = make_task<MODE>(sm, g, a, tid + s * NTHREADS, i0, j0);
+        for (int s = 0; s < kSlots; ++s) tk[s] = make_task<MODE>(sm, g, a, s, tid, i0, j0);
     }
     // bundle q completes phase (q + 1) / (PD + 2) of barrier (q + 1) % (PD + 2)
     auto bar_of = [&](int q) { return smem_u32(&sm.bar[(q + 1) % (PD + 2)]); };
@@ -350,16 +353,16 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
                 if (rt.n2) bulk_g2s(rt.d2 + off, rt.s2 + po.t, rt.n2, bar);
             }
         } else if (plain) {
+            // periodic: only the valid flag is set, so dst + off - 1 is the address
 #pragma unroll
             for (int s = 0; s < kSlots; ++s) {
-                const unsigned f = tk[s].flags;
-                const unsigned off = (f & TK_T) ? ts : ((f & TK_Y) ? ys : bs);
-                const bool on = (f & TK_VALID) && (withY || !(f & TK_Y));
+                const unsigned off = (s == 0 ? ts : (s < kSlotY ? bs : ys)) - TK_VALID;
+                const bool on = (tk[s].dst & TK_VALID) && (s < kSlotY || withY);
                 if (on) cp16(tk[s].dst + off, tk[s].src + po.t);
             }
         } else {
 #pragma unroll
-            for (int s = 0; s < kSlots; ++s) issue(tk[s], po, ts, bs, ys, withY, g.bcv);
+            for (int s = 0; s < kSlots; ++s) issue(tk[s], s, po, s == 0 ? ts : (s < kSlotY ? bs : ys), withY, g.bcv);
         }
     };
 
@@ -471,7 +474,7 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         // the tile's bottom y-faces and left x-faces: one extra face each,
         // taken by warps on different schedulers from plane to plane
         const int par = q & 1;
-        const int wy = q & 3, wx = 4 + ((q + 2) & 3);
+        const int wy = q & (TY - 1), wx = (q + TY / 2) & (TY - 1);
         if (r == wy) {
             *reinterpret_cast<float2*>(&sm.Fy[par][0][c]) =
                 low_yface2<SP, SAT>(sm, g, p, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), c);
@@ -527,7 +530,7 @@ namespace {
 // registers, no spills; 3: up to 80 registers, a few spilled words).
 // BULK: bundles copied by the TMA engine (periodic grids with nx >= 72).
 template <bool SP, bool SAT, int MODE, int OCC, bool BULK>
-__global__ void __launch_bounds__(x2::NTHREADS, OCC)
+__global__ void __launch_bounds__(x2::NTHREADS, OCC * (8 / x2::TY))
 stage_x2_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf, unsigned* status, int nzchunk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -575,6 +578,7 @@ template <bool SP, bool SAT, int MODE, int OCC, bool BULK>
 cudaError_t launch3(const KGrid<float>& g, const KPhys<float>& p, const x2::FastArgs& a, const KCoef<float>& cf,
                     unsigned* status, int nzchunk, cudaStream_t st)
 {
+    constexpr int kCtasPerSm = OCC * (8 / x2::TY);     // resident CTAs per SM
     const int smem = (int)sizeof(x2::SmemT<OCC == 2 ? x2::kPD : 1>);
     static bool attr_set = false;       // the attribute is per function, set once
     if (!attr_set) {
@@ -588,7 +592,7 @@ cudaError_t launch3(const KGrid<float>& g, const KPhys<float>& p, const x2::Fast
     if (nzchunk <= 0) {
         // balanced: OCC CTAs per SM, each run at least 8 planes long
         const int64_t U = (int64_t)ntx * nty * g.n[2];
-        grid = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)OCC * sm_count(), U / 8)), 1, 1);
+        grid = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)kCtasPerSm * sm_count(), U / 8)), 1, 1);
         nzchunk = 0;
     }
     stage_x2_kernel<SP, SAT, MODE, OCC, BULK><<<grid, x2::NTHREADS, smem, st>>>(g, p, a, cf, status, nzchunk);
@@ -634,7 +638,7 @@ bool x2_bulk_supported(const LaunchCfg& c, const KGrid<float>& g)
 static int auto_nzchunk(const KGrid<float>& g, int occupancy)
 {
     const int64_t cols = (int64_t)((g.n[0] + x2::TX - 1) / x2::TX) * ((g.n[1] + x2::TY - 1) / x2::TY);
-    const int64_t slots = (int64_t)occupancy * sm_count();
+    const int64_t slots = (int64_t)occupancy * (8 / x2::TY) * sm_count();
     int best = 32;
     double cost = 1e300;
     for (int nzc = 16; nzc <= 48; ++nzc) {
@@ -696,7 +700,7 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
 }
 
 template <bool SP, bool SAT>
-__global__ void __launch_bounds__(x2::NTHREADS, 2)
+__global__ void __launch_bounds__(x2::NTHREADS, 2 * (8 / x2::TY))
 ensemble_x2_kernel(const x2::EnsProb* __restrict__ probs, const x2::EnsSeg* __restrict__ segs, int nseg,
                    int total, int* work, unsigned* done, unsigned* status, int* abort_flag, long long spin_limit)
 {
