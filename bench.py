@@ -38,18 +38,22 @@ SEED = 2
 BYTES_PER_CELL_STAGE = 32          # Y_{j-1}, Y_{j-2}, Y_0, M(Y_0), bx, by, bz read; Y_j written (FP32)
 WORKLOAD = "tangled256_spitzer_rkl2"
 
-# DRAM traffic of the stage kernel per launch from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel
-# source it was measured on (sha256 of the kernel files, first 16 hex).
-MEASURED_TRAFFIC = {"source_hash": None, "bytes_per_launch": None}
+# DRAM traffic of one stage launch (j >= 2) of the 256^3 workload from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, summarised in
+# profiles/stage_x2_tangled256.md), valid only while the stage kernel's
+# sources hash to source_hash (sha256 of STAGE_KERNEL_SOURCES, 16 hex).
+MEASURED_TRAFFIC = {"source_hash": "6f74f8c69264bd9d", "bytes_per_launch": 539581952}
+
+
+# the sources of the default stage kernel (stage_x2_kernel)
+STAGE_KERNEL_SOURCES = ("rkl_x2.cu", "rkl_x2.cuh", "rkl_pair.cuh", "rkl_device.cuh")
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1702_05487_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, fn), "rb").read())
+    for fn in STAGE_KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, fn), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -378,6 +382,83 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+def run_split(args):
+    """Operator splitting on the 256^3 tangled-field problem: one step =
+    donor-cell advection by an ABC flow over dt_h (Eq. dt_h, C_h = 0.8,
+    flow scaled so that dt_h = 100 dt_expl at t = 0) followed by the
+    conduction over dt_h.  Times the three strategies of Table 1 (RKL2
+    super-step, sub-cycled explicit conduction, fully explicit) and reports
+    the RKL2 one; the others and the Table 1 run-time model (from the
+    measured hyperbolic step and conduction stage) ride along."""
+    import torch
+    import paper_1702_05487_gb300 as rk
+    from paper_1702_05487_gb300.split import SplitDriver, table1_costs
+    W = make_inputs("tangled256")
+    n = N_GRID
+    c = 2 * math.pi * (np.arange(n) + 0.5) / n
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    u0 = np.stack([np.sin(z) + np.cos(y), np.sin(x) + np.cos(z), np.sin(y) + np.cos(x)])
+    stream = torch.cuda.current_stream()
+    T0 = torch.from_numpy(W.T.astype(np.float32)).cuda()
+    b = torch.from_numpy(W.b.astype(np.float32)).cuda().contiguous()
+    probe = rk.Plan(W.T.shape, "f32", stream=stream, params=W.params)
+    dte = probe.dt_expl(T0)
+    u_unit = torch.from_numpy(u0.astype(np.float32)).cuda().contiguous()
+    scale = probe.dt_hyperbolic(u_unit, 0.8) / (100.0 * dte)
+    u = (u_unit * scale).contiguous()
+    probe.close()
+    out = {}
+    for strategy in ("rkl2", "subcycle", "explicit"):
+        drv = SplitDriver(W.T.shape, "f32", params=W.params, stream=stream, ch=0.8, strategy=strategy)
+        Ta, Tb = T0.clone(), torch.empty_like(T0)
+        dth = drv.dt_h(u)
+        nsub = drv.substeps(dth, Ta)
+        steps = args.steps if strategy == "rkl2" else max(1, args.steps // 5)
+        cur, oth = Ta, Tb
+        for k in range(args.warmup + steps):
+            if k == args.warmup:
+                torch.cuda.synchronize()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+            new, _, stages = drv.step(cur, oth, b, u, dth, None if strategy == "rkl2" else nsub)
+            oth = cur if new is not cur else oth
+            cur = new
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        out[strategy] = {"ms_per_step": ev0.elapsed_time(ev1) / steps, "conduction_stages": int(stages)}
+        drv.close()
+    # Table 1 inputs: one advection step and one conduction stage
+    plan = rk.Plan(W.T.shape, "f32", stream=stream, params=W.params)
+    Tb = torch.empty_like(T0)
+    for _ in range(3):
+        plan.advect(dth, u, T0, Tb)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(20):
+        plan.advect(dth, u, T0, Tb)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_hyp = e0.elapsed_time(e1) / 20
+    s = out["rkl2"]["conduction_stages"]
+    t_stage = (out["rkl2"]["ms_per_step"] - t_hyp) / s
+    model = table1_costs(t_hyp, t_stage, nsub, s)
+    value = 1e3 / out["rkl2"]["ms_per_step"]
+    line = {"metric": "operator-split steps/s (advection + RKL2 conduction over dt_h)", "value": value,
+            "unit": "step/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["rkl2"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "split256", "shape": list(W.T.shape), "dt_h_over_dtexpl": nsub,
+                       "flow": "ABC, C_h = 0.8", "conduction": "Spitzer, tangled b"},
+            "strategies": out,
+            "table1": {"t_hyp_ms": t_hyp, "t_stage_ms": t_stage, "r": t_hyp / t_stage,
+                       "model_ms_per_step": model,
+                       "speedup_vs_explicit": out["explicit"]["ms_per_step"] / out["rkl2"]["ms_per_step"],
+                       "speedup_vs_subcycle": out["subcycle"]["ms_per_step"] / out["rkl2"]["ms_per_step"]}}
+    print(json.dumps(line), flush=True)
+
+
 def run_surrogate(args):
     """The learned surrogate on 128^3 patches: training on RKL2-generated
     pairs, threshold calibration at 1e-3 relative L2 on held-out pairs, then
@@ -414,7 +495,7 @@ def main():
                     help="stage kernel: 0 auto, 1 generic, 2 tiled, 3/4 paired-cell at 2/3 CTAs per SM, 5 two-stage")
     ap.add_argument("--nzchunk", type=int, default=0, help="planes per CTA (0 automatic, < 0 balanced runs)")
     ap.add_argument("--workload", default="tangled256",
-                    choices=list(WORKLOADS) + ["ensemble64", "surrogate128"])
+                    choices=list(WORKLOADS) + ["ensemble64", "surrogate128", "split256"])
     ap.add_argument("--pairs", type=int, default=20000, help="training pairs of the surrogate workload")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -423,6 +504,8 @@ def main():
         run_ensemble(args)
     elif args.workload == "surrogate128":
         run_surrogate(args)
+    elif args.workload == "split256":
+        run_split(args)
     else:
         run_ours(args)
 

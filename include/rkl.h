@@ -225,6 +225,26 @@ rkl_status rkl_super_step(rkl_plan *plan, double dt, void *T, const void *b,
 rkl_status rkl_super_step_s(rkl_plan *plan, double dt, int s, void *T, const void *b,
                             double *energy_before, double *energy_after);
 
+/*
+ * Operator splitting (Section 3: the hyperbolic step without the conduction
+ * flux, then Eq. scalar_diffusion).  The hyperbolic part provided here is
+ * the passive advection dT/dt = -div(u T) of the energy density by a
+ * cell-centred velocity u (device array [3][ncell] in the grid dtype, x, y,
+ * z components; ghosts copy the nearest interior cell).
+ *
+ * rkl_dt_hyperbolic: Eq. dt_h with lambda_d = |u_d| (a passive flow has no
+ * sound speed): C_h / max_cells sum_d |u_d| / dx_d, or 0 if u = 0.  Uses one
+ * stage buffer of the plan as scratch; synchronises.
+ *
+ * rkl_advect: one conservative first-order donor-cell step,
+ * T_out = T_in - dt sum_d (F_d(c + 1/2) - F_d(c - 1/2)) / dx_d with face
+ * flux F = u_f T(upwind cell), u_f the mean of the two cells' u; monotone
+ * and positive for dt <= rkl_dt_hyperbolic(C_h = 1).  T_out must not alias
+ * T_in.  Asynchronous.
+ */
+rkl_status rkl_dt_hyperbolic(rkl_plan *plan, const void *u, double C_h, double *dt_out);
+rkl_status rkl_advect(rkl_plan *plan, double dt, const void *u, const void *T_in, void *T_out);
+
 /* FP64 energy sum_c T_c dV of a device array.  Synchronises. */
 rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
 
@@ -233,9 +253,9 @@ rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
  * paired-cell kernel where it applies, else the tiled kernel, else the
  * generic kernel), 1 = the generic one-thread-per-cell kernel, 2 = the
  * tiled FP32 3D kernel (32 x 8 tiles, one cell per thread), 3 and 4 = the
- * paired-cell FP32 3D kernel (64 x 8 tiles, two cells per thread in packed
- * f32x2 arithmetic; needs nx % 4 == 0) built for 2 (variant 3) or 3
- * (variant 4) resident CTAs per SM, 5 = the two-stage kernel (stages j and
+ * paired-cell FP32 3D kernel (64 x 4 tiles, two cells per thread in packed
+ * f32x2 arithmetic; needs nx % 4 == 0) built for 16 (variant 3) or 24
+ * (variant 4) resident warps per SM, 5 = the two-stage kernel (stages j and
  * j + 1 per pass over the grid, 60 x 7 tiles; periodic only; allocates a
  * fourth stage buffer), 6 = the paired-cell kernel with its plane bundles
  * copied by the TMA engine (cp.async.bulk rows with mbarrier completion;

@@ -115,6 +115,9 @@ def _load():
         lib.orc_sts_substeps.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
         lib.orc_sts_super_step.argtypes = [P, ctypes.c_double, ctypes.c_int, ctypes.c_double, dp, dp]
         lib.orc_sts_super_step.restype = ctypes.c_int
+        lib.orc_dt_hyp.argtypes = [P, dp, ctypes.c_double]
+        lib.orc_dt_hyp.restype = ctypes.c_double
+        lib.orc_advect.argtypes = [P, ctypes.c_double, dp, dp, dp]
         _lib = lib
         return lib
 
@@ -335,3 +338,38 @@ def sts_super_step(P: Problem, T, b, dt: float, nu: float = 1e-3, N: int = 0):
     c = P.cstruct()
     _load().orc_sts_super_step(ctypes.byref(c), float(dt), int(N), float(nu), _ptr(T), _ptr(bb))
     return T, N
+
+
+# --- operator splitting (Section 3): passive advection, then conduction ----
+
+def dt_hyp(P: Problem, u, ch: float = 0.8) -> float:
+    """Eq. dt_h with lambda_d = |u_d|: C_h / max sum_d |u_d| / dx_d."""
+    uu = _bfield(P, u)
+    c = P.cstruct()
+    return _load().orc_dt_hyp(ctypes.byref(c), _ptr(uu), float(ch))
+
+
+def advect(P: Problem, T, u, dt: float) -> np.ndarray:
+    """One conservative donor-cell step of dT/dt = -div(u T)."""
+    T = _f64(T).reshape(P.shape)
+    uu = _bfield(P, u)
+    out = np.zeros(P.shape)
+    c = P.cstruct()
+    _load().orc_advect(ctypes.byref(c), float(dt), _ptr(T), _ptr(uu), _ptr(out))
+    return out
+
+
+def split_step(P: Problem, T, b, u, ch: float = 0.8, conduction: str = "rkl2", sub: int = 0):
+    """One operator-split step of length dt_h: advection, then conduction over
+    dt_h by one RKL2 super-step ("rkl2"), or by sub-cycled forward-Euler steps
+    of at most dt_expl ("subcycle"; sub = their number, 0: ceil(dt_h/dt_expl)).
+    Returns (T, dt_h, conduction stages)."""
+    dth = dt_hyp(P, u, ch)
+    T1 = advect(P, T, u, dth)
+    if conduction == "rkl2":
+        T2, s = super_step(P, T1, b, dth)
+        return T2, dth, s
+    n = sub if sub > 0 else int(np.ceil(dth / dt_expl(P, T1) - 1e-12))
+    for _ in range(n):
+        T1 = euler_step(P, T1, b, dth / n)
+    return T1, dth, n

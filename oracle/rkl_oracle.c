@@ -469,6 +469,62 @@ int orc_sts_super_step(const orc_problem *P, double dt, int N, double nu, double
     return N;
 }
 
+/* ------------------------------------------------------------------------
+ * Operator splitting (Section 3): a hyperbolic step without the conduction
+ * flux, then the conduction step of Eq. scalar_diffusion.  The hyperbolic
+ * part here is the passive advection of the energy density by a given
+ * cell-centred velocity u (3 arrays of grid size), dT/dt = -div(u T), by the
+ * conservative first-order donor-cell scheme: the face velocity is the mean
+ * of the two cells and the face flux carries T from the upwind cell.
+ * ---------------------------------------------------------------------- */
+
+/* Component e of u at a cell that may lie outside the grid (as b). */
+static double u_at(const orc_problem *P, const double *u, int e, long i, long j, long k)
+{
+    return b_at(P, u, e, i, j, k);
+}
+
+/* Eq. dt_h with lambda_d = |u_d| (no sound or magnetosonic speed in a
+ * passive advection): C_h / max_cells sum_d |u_d| / dx_d; 0 if u = 0. */
+double orc_dt_hyp(const orc_problem *P, const double *u, double ch)
+{
+    long N = ncell(P);
+    double best = 0.0;
+    for (long c = 0; c < N; ++c) {
+        double v = 0.0;
+        for (int d = 0; d < P->ndim; ++d) v += fabs(u[(long)d * N + c]) / P->dx[d];
+        if (v > best) best = v;
+    }
+    return best > 0.0 ? ch / best : 0.0;
+}
+
+/* Advective flux on the face between cell (i,j,k) and its +e_d neighbour. */
+static double adv_flux(const orc_problem *P, const double *T, const double *u, int d, long i, long j, long k)
+{
+    long c1[3] = {i, j, k};
+    c1[d] += 1;
+    double uf = 0.5 * (u_at(P, u, d, i, j, k) + u_at(P, u, d, c1[0], c1[1], c1[2]));
+    double Tup = uf >= 0.0 ? T_at(P, T, i, j, k) : T_at(P, T, c1[0], c1[1], c1[2]);
+    return uf * Tup;
+}
+
+/* One donor-cell step: T_out = T - dt sum_d (F_d(c+1/2) - F_d(c-1/2)) / dx_d. */
+void orc_advect(const orc_problem *P, double dt, const double *T, const double *u, double *Tout)
+{
+    #pragma omp parallel for collapse(2) schedule(static)
+    for (long k = 0; k < P->n[2]; ++k)
+        for (long j = 0; j < P->n[1]; ++j)
+            for (long i = 0; i < P->n[0]; ++i) {
+                double div = 0.0;
+                for (int d = 0; d < P->ndim; ++d) {
+                    long lo[3] = {i, j, k};
+                    lo[d] -= 1;
+                    div += (adv_flux(P, T, u, d, i, j, k) - adv_flux(P, T, u, d, lo[0], lo[1], lo[2])) / P->dx[d];
+                }
+                Tout[idx(P, i, j, k)] = T[idx(P, i, j, k)] - dt * div;
+            }
+}
+
 int orc_set_threads(int nthreads)
 {
 #ifdef _OPENMP

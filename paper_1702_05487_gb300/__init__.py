@@ -18,6 +18,7 @@ from ._lib import (  # noqa: F401  (the C ABI, same names)
     rkl_coeffs_method, rkl_dt_expl, rkl_energy, rkl_flux, rkl_grid, rkl_num_stages, rkl_num_stages_method,
     rkl_phys, rkl_plan_check, rkl_plan_create, rkl_plan_destroy, rkl_plan_set_method, rkl_plan_set_timing,
     rkl_plan_set_variant, rkl_plan_timing, rkl_run_host, rkl_stage, rkl_super_step, rkl_super_step_s,
+    rkl_advect, rkl_dt_hyperbolic,
 )
 
 __all__ = ["Plan", "make_grid", "make_phys", "RklError"]
@@ -112,6 +113,14 @@ class Plan:
 
     def set_variant(self, variant, nzchunk=0):
         rkl_plan_set_variant(self.handle, variant, nzchunk)
+
+    def dt_hyperbolic(self, u, ch=0.8):
+        """Eq. dt_h for the advection velocity u ([3][cells] device array)."""
+        return rkl_dt_hyperbolic(self.handle, u, ch)
+
+    def advect(self, dt, u, T_in, T_out):
+        """One donor-cell advection step of T_in into T_out (asynchronous)."""
+        rkl_advect(self.handle, dt, u, T_in, T_out)
 
     def set_method(self, method, sts_nu=1e-3):
         """"rkl2" (default), "rkl1" or "sts" (AAG-STS with damping sts_nu)."""

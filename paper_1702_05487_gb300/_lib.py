@@ -60,6 +60,8 @@ SIGNATURES = {
     "rkl_num_stages_method": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, _ip]),
     "rkl_coeffs_method": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp]),
     "rkl_plan_set_method": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double]),
+    "rkl_dt_hyperbolic": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _dp]),
+    "rkl_advect": (ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp, _vp]),
     "rkl_plan_create": (ctypes.c_int, [ctypes.POINTER(rkl_grid), ctypes.POINTER(rkl_phys), _vp,
                                        ctypes.POINTER(_vp)]),
     "rkl_plan_destroy": (ctypes.c_int, [_vp]),
@@ -179,6 +181,16 @@ def rkl_coeffs_method(method: int, s: int, sts_nu: float = 1e-3):
 
 def rkl_plan_set_method(plan, method: int, sts_nu: float = 1e-3):
     _check(load().rkl_plan_set_method(plan, int(method), float(sts_nu)), plan)
+
+
+def rkl_dt_hyperbolic(plan, u, ch: float) -> float:
+    dt = ctypes.c_double(0.0)
+    _check(load().rkl_dt_hyperbolic(plan, _ptr(u), float(ch), ctypes.byref(dt)), plan)
+    return dt.value
+
+
+def rkl_advect(plan, dt: float, u, T_in, T_out):
+    _check(load().rkl_advect(plan, float(dt), _ptr(u), _ptr(T_in), _ptr(T_out)), plan)
 
 
 def rkl_plan_create(grid: rkl_grid, phys: rkl_phys, stream=None):

@@ -803,6 +803,37 @@ rkl_status rkl_energy(rkl_plan* p, const void* T, double* E_out)
     return RKL_OK;
 }
 
+rkl_status rkl_dt_hyperbolic(rkl_plan* p, const void* u, double ch, double* dt_out)
+{
+    if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
+    if (!u || !dt_out) return fail(p, RKL_ERR_INVALID_ARG, "null argument");
+    if (!(ch > 0.0) || !std::isfinite(ch)) return fail(p, RKL_ERR_INVALID_ARG, "C_h must be finite and > 0");
+    DeviceGuard dg(p->device);
+    // the rates go to a stage buffer, free between super-steps
+    cudaError_t e = launch_hyp_rate(p->cfg, p->cfg.dtype == RKL_F64 ? (const void*)&p->gd : (const void*)&p->gf, u,
+                                    p->ybuf[0], p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "rate launch");
+    rkl_status st = stats(p, p->ybuf[0], false, false);
+    if (st != RKL_OK) return st;
+    const double mx = p->h_scal[0];
+    if (!std::isfinite(mx)) return fail(p, RKL_ERR_NONFINITE, "u holds NaN or Inf");
+    *dt_out = mx > 0.0 ? ch / mx : 0.0;
+    return RKL_OK;
+}
+
+rkl_status rkl_advect(rkl_plan* p, double dt, const void* u, const void* T_in, void* T_out)
+{
+    if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
+    if (!u || !T_in || !T_out) return fail(p, RKL_ERR_INVALID_ARG, "null argument");
+    if (T_out == T_in) return fail(p, RKL_ERR_INVALID_ARG, "T_out aliases T_in");
+    if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(p, RKL_ERR_INVALID_ARG, "dt must be finite and >= 0");
+    DeviceGuard dg(p->device);
+    cudaError_t e = launch_advect(p->cfg, p->cfg.dtype == RKL_F64 ? (const void*)&p->gd : (const void*)&p->gf, T_in,
+                                  u, T_out, dt, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "advect launch");
+    return RKL_OK;
+}
+
 rkl_status rkl_plan_autotune(rkl_plan* p, double dt, const void* T, const void* b, int* variant_out,
                              int* nzchunk_out, double* ms_out)
 {

@@ -200,6 +200,84 @@ cudaError_t flux_impl(const void* grid, const void* phys, const void* T, const v
     return cudaGetLastError();
 }
 
+// --------------------------------------------------------------------------
+// Operator splitting (Section 3): the hyperbolic step as the passive
+// advection dT/dt = -div(u T) of the energy density by a cell-centred
+// velocity u ([3][ncell], ghosts copy the nearest interior cell as b does),
+// conservative donor cell: face velocity = mean of the two cells, face flux
+// = u_f T(upwind cell).
+
+template <typename R>
+__device__ __forceinline__ R adv_flux(const Field<R>& f, int d, int i, int j, int k)
+{
+    int Q[3] = {i, j, k};
+    Q[d] += 1;
+    const R uf = R(0.5) * (f.bc(d, i, j, k) + f.bc(d, Q[0], Q[1], Q[2]));
+    return uf * (uf >= R(0) ? f.t(i, j, k) : f.t(Q[0], Q[1], Q[2]));
+}
+
+template <typename R, int NDIM>
+__global__ void __launch_bounds__(256) advect_kernel(KGrid<R> g, const R* __restrict__ T, const R* __restrict__ u,
+                                                     R* __restrict__ Tout, R dt)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.ncell) return;
+    const int i = (int)(c % g.n[0]);
+    const int64_t r = c / g.n[0];
+    const int j = (int)(r % g.n[1]);
+    const int k = (int)(r / g.n[1]);
+    const Field<R> f{T, u, g};
+    R div = R(0);
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        int lo[3] = {i, j, k};
+        lo[d] -= 1;
+        div += (adv_flux(f, d, i, j, k) - adv_flux(f, d, lo[0], lo[1], lo[2])) * g.inv_dx[d];
+    }
+    Tout[c] = T[c] - dt * div;
+}
+
+// lambda(c) = sum_d |u_d| / dx_d (the denominator of Eq. dt_h)
+template <typename R, int NDIM>
+__global__ void __launch_bounds__(256) hyp_rate_kernel(KGrid<R> g, const R* __restrict__ u, R* __restrict__ lam)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.ncell) return;
+    R v = R(0);
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) v += fabs(u[(int64_t)d * g.ncell + c]) * g.inv_dx[d];
+    lam[c] = v;
+}
+
+template <typename R>
+cudaError_t advect_impl(const LaunchCfg& c, const void* grid, const void* T, const void* u, void* Tout, double dt,
+                        cudaStream_t st)
+{
+    const KGrid<R>& g = *static_cast<const KGrid<R>*>(grid);
+    const int tpb = generic_block(g.ncell);
+    const unsigned blocks = (unsigned)((g.ncell + tpb - 1) / tpb);
+    const R* Tp = static_cast<const R*>(T);
+    const R* up = static_cast<const R*>(u);
+    R* op = static_cast<R*>(Tout);
+    if (c.ndim == 1) advect_kernel<R, 1><<<blocks, tpb, 0, st>>>(g, Tp, up, op, (R)dt);
+    else if (c.ndim == 2) advect_kernel<R, 2><<<blocks, tpb, 0, st>>>(g, Tp, up, op, (R)dt);
+    else advect_kernel<R, 3><<<blocks, tpb, 0, st>>>(g, Tp, up, op, (R)dt);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t hyp_rate_impl(const LaunchCfg& c, const void* grid, const void* u, void* lam, cudaStream_t st)
+{
+    const KGrid<R>& g = *static_cast<const KGrid<R>*>(grid);
+    const unsigned blocks = (unsigned)((g.ncell + 255) / 256);
+    const R* up = static_cast<const R*>(u);
+    R* lp = static_cast<R*>(lam);
+    if (c.ndim == 1) hyp_rate_kernel<R, 1><<<blocks, 256, 0, st>>>(g, up, lp);
+    else if (c.ndim == 2) hyp_rate_kernel<R, 2><<<blocks, 256, 0, st>>>(g, up, lp);
+    else hyp_rate_kernel<R, 3><<<blocks, 256, 0, st>>>(g, up, lp);
+    return cudaGetLastError();
+}
+
 template <typename R, int NDIM>
 cudaError_t stage_dispatch_phys(const LaunchCfg& c, const void* grid, const void* phys,
                                 const StageIO& io, const void* coef, unsigned* status, cudaStream_t st)
@@ -353,6 +431,19 @@ cudaError_t launch_stage_generic(const LaunchCfg& c, const void* grid, const voi
 {
     if (c.dtype == 1) return stage_dispatch_ndim<double>(c, grid, phys, io, coef, status, st);
     return stage_dispatch_ndim<float>(c, grid, phys, io, coef, status, st);
+}
+
+cudaError_t launch_advect(const LaunchCfg& c, const void* grid, const void* T, const void* u, void* Tout, double dt,
+                          cudaStream_t st)
+{
+    if (c.dtype == 1) return advect_impl<double>(c, grid, T, u, Tout, dt, st);
+    return advect_impl<float>(c, grid, T, u, Tout, dt, st);
+}
+
+cudaError_t launch_hyp_rate(const LaunchCfg& c, const void* grid, const void* u, void* lam, cudaStream_t st)
+{
+    if (c.dtype == 1) return hyp_rate_impl<double>(c, grid, u, lam, st);
+    return hyp_rate_impl<float>(c, grid, u, lam, st);
 }
 
 cudaError_t launch_flux_generic(const LaunchCfg& c, const void* grid, const void* phys, const void* T,

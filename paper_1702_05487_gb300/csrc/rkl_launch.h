@@ -37,6 +37,13 @@ cudaError_t launch_stage_generic(const LaunchCfg& c, const void* grid, const voi
 cudaError_t launch_flux_generic(const LaunchCfg& c, const void* grid, const void* phys,
                                 const void* T, const void* b, void* F[3], cudaStream_t st);
 
+// Operator splitting: one donor-cell advection step T_out = T - dt div(u T)
+// (u: [3][ncell] cell-centred velocity), and the per-cell rate
+// sum_d |u_d| / dx_d of Eq. dt_h into lam (grid-sized scratch).
+cudaError_t launch_advect(const LaunchCfg& c, const void* grid, const void* T, const void* u, void* Tout, double dt,
+                          cudaStream_t st);
+cudaError_t launch_hyp_rate(const LaunchCfg& c, const void* grid, const void* u, void* lam, cudaStream_t st);
+
 // Tiled FP32 3D stage kernel (shared-memory halo planes, z-march).
 // Returns cudaErrorNotSupported if the configuration is not covered.
 bool fast_stage_supported(const LaunchCfg& c, const KGrid<float>& g);
@@ -44,7 +51,7 @@ cudaError_t launch_stage_fast(const LaunchCfg& c, const KGrid<float>& g, const K
                               const StageIO& io, const KCoef<float>& coef, unsigned* status,
                               cudaStream_t st);
 
-// Paired-cell FP32 3D stage kernel (packed f32x2 arithmetic, 64 x 8 tiles,
+// Paired-cell FP32 3D stage kernel (packed f32x2 arithmetic, 64 x 4 tiles,
 // nzchunk planes per CTA, occupancy 2 or 3 CTAs per SM).  Needs nx % 4 == 0
 // and 16-byte aligned arrays.
 // With bulk (and a periodic grid with nx >= 72) the plane bundles are

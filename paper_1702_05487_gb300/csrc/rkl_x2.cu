@@ -1,8 +1,8 @@
 // Paired-cell FP32 3D stage kernel for the RKL2 conduction super-step.
 //
 // Same z-march and plane-bundle pipeline as the tiled kernel, but each
-// thread owns two neighbouring cells in x (columns 2l, 2l + 1 of a 64 x 8
-// tile) and evaluates their faces, divergence and recurrence with the packed
+// thread owns two neighbouring cells in x (columns 2l, 2l + 1 of a 64 x TY
+// tile, one warp per row; TY = 4 gives four CTAs per SM) and evaluates their faces, divergence and recurrence with the packed
 // FP32 pair instructions of sm_100+ (add/sub/mul/fma .f32x2), so one
 // instruction serves both cells.  Shared-memory reads are 64-bit pairs.
 // The x-face below a pair comes from the lane to the left by a warp shuffle
@@ -27,9 +27,9 @@ __device__ __forceinline__ int off(int r, int c) { return (r + 1) * SXS + c + 4;
 
 // Copy tasks fixed per thread for the whole tile, grouped by ring so that a
 // thread's slot s always feeds the same ring (its slot offset is known at
-// compile time): slot 0 a 16-byte chunk of T (10 rows x 18 chunks, halo
-// ring included), slots 1-3 chunks of bx, by, bz (3 x 180), slots 4-5
-// chunks of Y0, Y_{j-2}, M(Y0) (3 x 8 rows x 16).  Rows must start on a
+// compile time): slot 0 a 16-byte chunk of T (TY + 2 rows x 18 chunks, halo
+// ring included), slots 1-3 chunks of bx, by, bz, slots 4-5 chunks of Y0,
+// Y_{j-2}, M(Y0) (3 x TY rows x 16).  Rows must start on a
 // 16-byte boundary (nx % 4 == 0); chunks past the grid edge wrap
 // (periodic), hold the ghost value (Dirichlet T), repeat the nearest
 // interior b (Dirichlet, past the x edge) or are skipped (Y).  The smem
@@ -106,12 +106,12 @@ __device__ __forceinline__ PlaneOff plane_offsets(const KGrid<float>& g, int kk)
     return o;
 }
 
-// Bulk-copy tasks (periodic grids with nx >= 72): thread t < 64 (40 T/b
-// rows, 24 Y rows) owns one
-// smem row of a bundle -- rows -1 .. 8 of T and of bx, by, bz (72 columns
-// from i0 - 4, wrapped into at most two pieces) and rows 0 .. 7 of Y0,
-// Y_{j-2}, M(Y0) -- copied by the TMA engine straight into the ring slot.
-constexpr int kRowTB = 4 * ROWS;             // 40
+// Bulk-copy tasks (periodic grids with nx >= 72): thread t < 4 (TY + 2) +
+// 3 TY owns one smem row of a bundle -- rows -1 .. TY of T and of bx, by,
+// bz (72 columns from i0 - 4, wrapped into at most two pieces) and rows
+// 0 .. TY - 1 of Y0, Y_{j-2}, M(Y0) -- copied by the TMA engine straight
+// into the ring slot.
+constexpr int kRowTB = 4 * ROWS;
 struct RowTask {
     const float* s1;      // first piece, plane 0
     const float* s2;      // second piece (wrapped part of a halo row)
@@ -526,8 +526,9 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
 
 namespace {
 
-// OCC = resident CTAs per SM the register budget is sized for (2: up to 128
-// registers, no spills; 3: up to 80 registers, a few spilled words).
+// OCC = register budget: built so that OCC x 8 warps fit on an SM (2: up to
+// 128 registers, no spills; 3: up to 80 registers, a few spilled words),
+// i.e. OCC x 8 / TY resident CTAs of 64 x TY tiles.
 // BULK: bundles copied by the TMA engine (periodic grids with nx >= 72).
 template <bool SP, bool SAT, int MODE, int OCC, bool BULK>
 __global__ void __launch_bounds__(x2::NTHREADS, OCC * (8 / x2::TY))

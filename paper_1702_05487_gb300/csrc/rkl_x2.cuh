@@ -8,7 +8,7 @@ namespace rkl {
 namespace x2 {
 
 constexpr int TX = 64;                  // tile columns: 32 lanes x 2 cells
-constexpr int TY = 8;                   // tile rows: one warp per row
+constexpr int TY = 4;                   // tile rows: one warp per row (4 CTAs per SM)
 constexpr int NTHREADS = 32 * TY;
 constexpr int SXS = 72;                 // smem row: halo chunk (4), 64 interior, halo chunk (4)
 constexpr int CPR = SXS / 4;            // 16-byte chunks per smem row
