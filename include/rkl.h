@@ -410,6 +410,17 @@ rkl_status rkl_sur_get_grads(rkl_surrogate *sur, int layer, float *gw, float *gb
 /* input channels from device arrays T [cells] and b [3][cells] */
 rkl_status rkl_sur_features(rkl_surrogate *sur, const void *T, const void *b, double kappa_par0,
                             int spitzer, double dt_over_dtexpl);
+/*
+ * Convolution backend of the forward and backward-data passes: 0 (default)
+ * the warp-level mma.sync kernels, 1 the tcgen05 kernels (M = 128-voxel
+ * blocks of one plane, accumulators in tensor memory; needs W % 8 == 0 and
+ * H % 16 == 0, else RKL_ERR_UNSUPPORTED).  Weight gradients use the
+ * warp-level kernel either way.
+ */
+rkl_status rkl_sur_set_backend(rkl_surrogate *sur, int backend);
+/* waits for the stream; RKL_ERR_TIMEOUT if a tcgen05 kernel's bounded wait
+ * gave up since the last check (the word is then cleared) */
+rkl_status rkl_sur_check(rkl_surrogate *sur);
 /* forward pass; the increment dT goes to dT_out (device floats) if not NULL */
 rkl_status rkl_sur_forward(rkl_surrogate *sur, double head_scale, void *dT_out);
 /* MSE loss 0.5 mean((dT - target)^2) of the last forward and all gradients */

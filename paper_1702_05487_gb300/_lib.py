@@ -99,6 +99,8 @@ SIGNATURES = {
     "rkl_sur_get_params": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "rkl_sur_get_grads": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "rkl_sur_features": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_double]),
+    "rkl_sur_set_backend": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "rkl_sur_check": (ctypes.c_int, [_vp]),
     "rkl_sur_forward": (ctypes.c_int, [_vp, ctypes.c_double, _vp]),
     "rkl_sur_backward": (ctypes.c_int, [_vp, _vp, _dp]),
     "rkl_sur_adam": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
@@ -402,6 +404,15 @@ def rkl_sur_get_grads(sur, layer):
 
 def rkl_sur_features(sur, T, b, kappa_par0, spitzer, ratio):
     _scheck(load().rkl_sur_features(sur, _ptr(T), _ptr(b), float(kappa_par0), int(bool(spitzer)), float(ratio)), sur)
+
+
+def rkl_sur_set_backend(sur, backend: int):
+    """0: warp-level mma.sync convolutions, 1: tcgen05 convolutions."""
+    _scheck(load().rkl_sur_set_backend(sur, int(backend)), sur)
+
+
+def rkl_sur_check(sur):
+    _scheck(load().rkl_sur_check(sur), sur)
 
 
 def rkl_sur_forward(sur, head_scale, dT_out=None):

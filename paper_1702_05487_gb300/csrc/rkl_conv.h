@@ -13,6 +13,12 @@ namespace conv {
 // 2 no bias, result times (mask > 0), bf16 out.
 cudaError_t conv_forward(int cin, int cout, int mode, const void* in, const void* wt, const float* bias,
                          const void* mask, void* out, int D, int H, int W, cudaStream_t st);
+// The same convolutions on the 5th-generation tensor cores (tcgen05.mma,
+// accumulators in TMEM): W % 8 == 0, H % 16 == 0, nzc planes per CTA.  A
+// bounded wait that gives up sets ST_TIMEOUT in *status (may be NULL).
+cudaError_t conv_forward_tc(int cin, int cout, int mode, const void* in, const void* wt, const float* bias,
+                            const void* mask, void* out, int D, int H, int W, int nzc, unsigned* status,
+                            cudaStream_t st);
 // dW[27][cout][cin] += sum_v dz[v][cout] x[v + off][cin]; (cin, cout) in
 // {(16,32), (32,32), (32,16)}.  dW must be zeroed by the caller.
 cudaError_t conv_wgrad(int cin, int cout, const void* dz, const void* x, float* dW, int D, int H, int W, int nsplit,

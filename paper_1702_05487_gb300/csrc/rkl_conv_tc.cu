@@ -1,0 +1,304 @@
+// Periodic 3x3x3 convolution of the surrogate on the 5th-generation tensor
+// cores: tcgen05.mma with operands described in shared memory and the FP32
+// accumulator in tensor memory (TMEM).
+//
+// Implicit GEMM per output plane: M = 128 voxels (an 8 x 16 block of one z
+// plane, x fastest), N = Cout, K = 27 offsets x Cin.  A CTA marches such a
+// block through a chunk of planes.  Input planes with their one-voxel halo
+// (10 x 18 voxels) stream through a 5-slot shared-memory ring, each stored
+// chunk-major ([Cin/8][180 voxels][8 channels]): for an offset (dz, dy, dx)
+// the A operand is then a plain K-major no-swizzle matrix -- core matrix i
+// (rows y = i, x = 0..7) starts at voxel (dx, i + dy) of the halo plane and
+// the next one is one halo row (10 voxels) further -- so every offset reads
+// the same resident plane without any im2col copy.  The weights sit in
+// shared memory once per CTA as [27][Cin/8][Cout][8].  Thread 0 issues the
+// 27 x Cin/16 MMAs of a plane into one of two TMEM accumulators and commits
+// them to an mbarrier; while they run, the four warps (one TMEM lane quarter
+// each) drain the other accumulator of the previous plane (bias, ReLU or
+// mask, BF16 or FP32 store).  Every wait is bounded and reports ST_TIMEOUT.
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "rkl_conv.h"
+#include "rkl_pair.cuh"
+
+namespace rkl {
+namespace conv {
+namespace {
+
+using x2::cp16;
+using x2::cp_commit;
+using x2::cp_wait;
+using x2::mbar_init;
+using x2::mbar_inval;
+using x2::mbar_wait;
+using x2::smem_u32;
+
+constexpr int QX = 8, QY = 16;                 // output block of a plane: M = 128
+constexpr int HX = QX + 2, HY = QY + 2;         // halo plane
+constexpr int HP = HX * HY;                     // 180 voxels
+constexpr int NSLOT = 5;                        // planes p-2 .. p+2
+constexpr int NTHR_TC = 128;                    // 4 warps = the 4 TMEM lane quarters
+constexpr int TMEM_COLS = 64;                   // two accumulators of up to 32 columns
+
+template <int CIN, int COUT>
+struct TcSmem {
+    __nv_bfloat16 W[27][CIN / 8][COUT][8];      // B operands, K-major core matrices
+    __nv_bfloat16 A[NSLOT][CIN / 8][HP][8];     // A operands, one halo plane per slot
+    unsigned long long bar[2];                  // MMA completion, one per accumulator
+    unsigned tmem;                              // TMEM base column from tcgen05.alloc
+};
+
+// Shared-memory matrix descriptor (no swizzle, K-major): start address,
+// leading byte offset (next core matrix along K), stride byte offset (next
+// core matrix along M or N), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(unsigned addr, unsigned lbo, unsigned sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = COUT, M = 128.
+template <int COUT>
+__device__ __forceinline__ unsigned idesc()
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(COUT >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(unsigned dtmem, uint64_t a, uint64_t b, unsigned id, unsigned accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(id), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(unsigned bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float* v)
+{
+    unsigned r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v)
+{
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ int wrapi_tc(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// MODE 0: ReLU, bf16 out; 1: linear, f32 out; 2: no bias, times the ReLU
+// mask (mask > 0), bf16 out.  Grid: (W/8, H/16, ceil(D/nzc)).
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(NTHR_TC, 1)
+conv_tc_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ wt,
+               const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask, void* __restrict__ out,
+               int D, int H, int W, int nzc, unsigned* status)
+{
+    using S = TcSmem<CIN, COUT>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    S& sm = *reinterpret_cast<S*>(smem_raw);
+    constexpr int NCH = CIN / 8;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int x0 = blockIdx.x * QX, y0 = blockIdx.y * QY, z0 = blockIdx.z * nzc;
+    const int nz = min(nzc, D - z0);
+
+    // weights [27][COUT][CIN] -> [27][CIN/8][COUT][8]
+    for (int t = tid; t < 27 * COUT * NCH; t += NTHR_TC) {
+        const int o = t / (COUT * NCH), r = t % (COUT * NCH), n = r / NCH, ch = r % NCH;
+        cp16(smem_u32(&sm.W[o][ch][n][0]), wt + ((int64_t)o * COUT + n) * CIN + ch * 8);
+    }
+    // halo plane q (z0 + q, periodic) into its ring slot
+    auto load = [&](int q) {
+        const int gz = wrapi_tc(z0 + q, D);
+        const int s = (q + 2 * NSLOT) % NSLOT;
+        for (int t = tid; t < HP * NCH; t += NTHR_TC) {
+            const int hv = t / NCH, ch = t % NCH;
+            const int gy = wrapi_tc(y0 + hv / HX - 1, H), gx = wrapi_tc(x0 + hv % HX - 1, W);
+            cp16(smem_u32(&sm.A[s][ch][hv][0]), in + (((int64_t)gz * H + gy) * W + gx) * CIN + ch * 8);
+        }
+    };
+    load(-1);
+    cp_commit();                                // group: weights + plane -1
+    load(0);
+    cp_commit();
+    if (1 <= nz) load(1);
+    cp_commit();
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&sm.tmem)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(&sm.bar[0]), 1u);
+        mbar_init(smem_u32(&sm.bar[1]), 1u);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tbase = sm.tmem;
+    const unsigned id = idesc<COUT>();
+    bool ok = true;
+
+    auto epilogue = [&](int p) {
+        const int k = p & 1;
+        if (!mbar_wait(smem_u32(&sm.bar[k]), (unsigned)((p >> 1) & 1))) ok = false;
+        fence_after();
+        float v[COUT];
+        const unsigned taddr = tbase + ((unsigned)(warp * 32) << 16) + (unsigned)(k * 32);
+        if (COUT == 32) tmem_ld32(taddr, v);
+        else tmem_ld16(taddr, v);
+        fence_before();
+        const int m = warp * 32 + lane;          // TMEM lane = GEMM row = voxel of the block
+        const int64_t gv = ((int64_t)(z0 + p) * H + (y0 + m / QX)) * W + (x0 + m % QX);
+        if (MODE == 1) {
+            float* o = static_cast<float*>(out) + gv * COUT;
+#pragma unroll
+            for (int c = 0; c < COUT; c += 4)
+                *reinterpret_cast<float4*>(o + c) = make_float4(v[c] + bias[c], v[c + 1] + bias[c + 1],
+                                                                v[c + 2] + bias[c + 2], v[c + 3] + bias[c + 3]);
+        } else {
+            __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out) + gv * COUT;
+#pragma unroll
+            for (int c = 0; c < COUT; c += 8) {
+                float w[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    w[i] = v[c + i];
+                    if (MODE == 0) w[i] = fmaxf(w[i] + bias[c + i], 0.f);
+                }
+                if (MODE == 2) {
+                    const uint4 mk = *reinterpret_cast<const uint4*>(mask + gv * COUT + c);
+                    const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (!(__bfloat162float(mb[i]) > 0.f)) w[i] = 0.f;
+                }
+                uint4 pk;
+                __nv_bfloat162* ph = reinterpret_cast<__nv_bfloat162*>(&pk);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) ph[i] = __floats2bfloat162_rn(w[2 * i], w[2 * i + 1]);
+                *reinterpret_cast<uint4*>(o + c) = pk;
+            }
+        }
+    };
+
+    for (int p = 0; p < nz; ++p) {
+        // plane p+2 goes to the slot of plane p-3, whose MMAs (plane p-2)
+        // were waited for in the previous iteration's epilogue
+        if (p + 2 <= nz) load(p + 2);
+        cp_commit();
+        cp_wait<1>();                            // planes up to p + 1 have landed
+        fence_proxy_async();                     // generic-proxy writes -> tensor-core reads
+        fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            const unsigned dt = tbase + (unsigned)((p & 1) * 32);
+            unsigned acc = 0;
+#pragma unroll 1
+            for (int o = 0; o < 27; ++o) {
+                const int dz = o / 9 - 1, dy = (o / 3) % 3 - 1, dx = o % 3 - 1;
+                const int s = (p + dz + 2 * NSLOT) % NSLOT;
+                const unsigned abase = smem_u32(&sm.A[s][0][(dy + 1) * HX + (dx + 1)][0]);
+                const unsigned bbase = smem_u32(&sm.W[o][0][0][0]);
+#pragma unroll
+                for (int kk = 0; kk < CIN / 16; ++kk) {
+                    const uint64_t a = sdesc(abase + (unsigned)(2 * kk * HP * 16), HP * 16, HX * 16);
+                    const uint64_t b = sdesc(bbase + (unsigned)(2 * kk * COUT * 16), COUT * 16, 8 * 16);
+                    mma_f16(dt, a, b, id, acc);
+                    acc = 1;
+                }
+            }
+            mma_commit(smem_u32(&sm.bar[p & 1]));
+        }
+        __syncwarp();
+        if (p >= 1) epilogue(p - 1);
+    }
+    if (nz >= 1) epilogue(nz - 1);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tbase), "r"(TMEM_COLS)
+                     : "memory");
+    if (tid == 0) {
+        mbar_inval(smem_u32(&sm.bar[0]));
+        mbar_inval(smem_u32(&sm.bar[1]));
+    }
+    if (!ok && status) atomicOr(status, ST_TIMEOUT);
+}
+
+template <int CIN, int COUT, int MODE>
+cudaError_t conv_tc_t(const void* in, const void* wt, const float* bias, const void* mask, void* out, int D, int H,
+                      int W, int nzc, unsigned* status, cudaStream_t st)
+{
+    const int smem = (int)sizeof(TcSmem<CIN, COUT>);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<CIN, COUT, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid(W / QX, H / QY, (D + nzc - 1) / nzc);
+    conv_tc_kernel<CIN, COUT, MODE><<<grid, NTHR_TC, smem, st>>>(
+        static_cast<const __nv_bfloat16*>(in), static_cast<const __nv_bfloat16*>(wt), bias,
+        static_cast<const __nv_bfloat16*>(mask), out, D, H, W, nzc, status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t conv_forward_tc(int cin, int cout, int mode, const void* in, const void* wt, const float* bias,
+                            const void* mask, void* out, int D, int H, int W, int nzc, unsigned* status,
+                            cudaStream_t st)
+{
+    if (W % QX || H % QY || D < 1 || nzc < 1) return cudaErrorInvalidValue;
+    if (cin == 16 && cout == 32 && mode == 0)
+        return conv_tc_t<16, 32, 0>(in, wt, bias, mask, out, D, H, W, nzc, status, st);
+    if (cin == 32 && cout == 32 && mode == 0)
+        return conv_tc_t<32, 32, 0>(in, wt, bias, mask, out, D, H, W, nzc, status, st);
+    if (cin == 32 && cout == 16 && mode == 1)
+        return conv_tc_t<32, 16, 1>(in, wt, bias, mask, out, D, H, W, nzc, status, st);
+    if (cin == 32 && cout == 32 && mode == 2)
+        return conv_tc_t<32, 32, 2>(in, wt, bias, mask, out, D, H, W, nzc, status, st);
+    if (cin == 16 && cout == 32 && mode == 2)
+        return conv_tc_t<16, 32, 2>(in, wt, bias, mask, out, D, H, W, nzc, status, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace conv
+}  // namespace rkl

@@ -95,6 +95,8 @@ struct rkl_surrogate {
     float* Yp = nullptr;
     float* M0 = nullptr;
     float* Mp = nullptr;
+    int backend = 0;               // 0: warp-level mma.sync convolutions, 1: tcgen05
+    unsigned* d_tcst = nullptr;    // status word of the tcgen05 kernels' bounded waits
     double* d_part = nullptr;
     double* h_part = nullptr;      // pinned
     bool forward_done = false;
@@ -119,16 +121,25 @@ rkl_status sfail(rkl_surrogate* s, rkl_status st, const std::string& m)
 
 size_t wcount(int l) { return (size_t)27 * kCout[l] * kCin[l]; }
 
+// Forward (and backward-data) convolution on the selected backend.
+cudaError_t conv_fwd(rkl_surrogate* s, int cin, int cout, int mode, const void* in, const void* wt, const float* bias,
+                     const void* mask, void* out)
+{
+    if (s->backend == 1)
+        return conv::conv_forward_tc(cin, cout, mode, in, wt, bias, mask, out, s->D, s->H, s->W, 16, s->d_tcst,
+                                     s->stream);
+    return conv::conv_forward(cin, cout, mode, in, wt, bias, mask, out, s->D, s->H, s->W, s->stream);
+}
+
 rkl_status forward_impl(rkl_surrogate* s, double head_scale)
 {
     const int D = s->D, H = s->H, W = s->W;
     const void* in = s->X0;
     for (int l = 0; l < kLayers - 1; ++l) {
-        SUR_CK(s, conv::conv_forward(kCin[l], kCout[l], 0, in, s->wf[l], s->b[l], nullptr, s->A[l], D, H, W, s->stream));
+        SUR_CK(s, conv_fwd(s, kCin[l], kCout[l], 0, in, s->wf[l], s->b[l], nullptr, s->A[l]));
         in = s->A[l];
     }
-    SUR_CK(s, conv::conv_forward(32, 16, 1, in, s->wf[kLayers - 1], s->b[kLayers - 1], nullptr, s->G, D, H, W,
-                                 s->stream));
+    SUR_CK(s, conv_fwd(s, 32, 16, 1, in, s->wf[kLayers - 1], s->b[kLayers - 1], nullptr, s->G));
     SUR_CK(s, conv::head_div(s->G, D, H, W, (float)head_scale, s->inv_dx, s->dT, s->stream));
     s->forward_done = true;
     s->head_scale = head_scale;
@@ -149,7 +160,7 @@ rkl_status backward_impl(rkl_surrogate* s, const float* target, double* loss)
     const void* dz = s->dG;
     SUR_CK(s, conv::conv_wgrad(32, 16, dz, s->A[4], s->gw[5], D, H, W, 8, s->stream));
     SUR_CK(s, conv::conv_bgrad(16, dz, s->gb[5], s->V, s->stream));
-    SUR_CK(s, conv::conv_forward(16, 32, 2, dz, s->wb[5], nullptr, s->A[4], s->dZ[0], D, H, W, s->stream));
+    SUR_CK(s, conv_fwd(s, 16, 32, 2, dz, s->wb[5], nullptr, s->A[4], s->dZ[0]));
     int cur = 0;
     for (int l = kLayers - 2; l >= 0; --l) {
         dz = s->dZ[cur];
@@ -157,8 +168,7 @@ rkl_status backward_impl(rkl_surrogate* s, const float* target, double* loss)
         SUR_CK(s, conv::conv_wgrad(kCin[l], 32, dz, x, s->gw[l], D, H, W, 8, s->stream));
         SUR_CK(s, conv::conv_bgrad(32, dz, s->gb[l], s->V, s->stream));
         if (l > 0) {
-            SUR_CK(s, conv::conv_forward(32, 32, 2, dz, s->wb[l], nullptr, s->A[l - 1], s->dZ[1 - cur], D, H, W,
-                                         s->stream));
+            SUR_CK(s, conv_fwd(s, 32, 32, 2, dz, s->wb[l], nullptr, s->A[l - 1], s->dZ[1 - cur]));
             cur = 1 - cur;
         }
     }
@@ -239,6 +249,8 @@ rkl_status rkl_sur_create(int D, int H, int W, const double* dx, void* cuda_stre
     if ((c = cudaMalloc(&s->M0, (size_t)V * 4)) != cudaSuccess) return bail(c, "M0");
     if ((c = cudaMalloc(&s->Mp, (size_t)V * 4)) != cudaSuccess) return bail(c, "Mp");
     if ((c = cudaMalloc(&s->d_part, sizeof(double) * 2 * kPartials)) != cudaSuccess) return bail(c, "partials");
+    if ((c = cudaMalloc(&s->d_tcst, sizeof(unsigned))) != cudaSuccess) return bail(c, "status");
+    if ((c = cudaMemsetAsync(s->d_tcst, 0, sizeof(unsigned), s->stream)) != cudaSuccess) return bail(c, "status");
     if ((c = cudaMallocHost(&s->h_part, sizeof(double) * 2 * kPartials)) != cudaSuccess) return bail(c, "partials");
     if ((c = cudaStreamSynchronize(s->stream)) != cudaSuccess) return bail(c, "sync");
     for (int l = 0; l < kLayers; ++l)
@@ -262,6 +274,7 @@ rkl_status rkl_sur_destroy(rkl_surrogate* s)
     cudaFree(s->dZ[0]); cudaFree(s->dZ[1]);
     cudaFree(s->Yp); cudaFree(s->M0); cudaFree(s->Mp);
     cudaFree(s->d_part);
+    cudaFree(s->d_tcst);
     if (s->h_part) cudaFreeHost(s->h_part);
     delete s;
     return RKL_OK;
@@ -305,6 +318,27 @@ rkl_status rkl_sur_features(rkl_surrogate* s, const void* T, const void* b, doub
     SUR_CK(s, conv::features(static_cast<const float*>(T), static_cast<const float*>(b), s->V, (float)kappa0,
                              spitzer ? 1 : 0, (float)ratio, s->X0, s->stream));
     s->forward_done = false;
+    return RKL_OK;
+}
+
+rkl_status rkl_sur_set_backend(rkl_surrogate* s, int backend)
+{
+    if (!s) return RKL_ERR_INVALID_ARG;
+    if (backend != 0 && backend != 1) return sfail(s, RKL_ERR_INVALID_ARG, "backend must be 0 or 1");
+    if (backend == 1 && (s->W % 8 != 0 || s->H % 16 != 0))
+        return sfail(s, RKL_ERR_UNSUPPORTED, "the tcgen05 convolutions need W % 8 == 0 and H % 16 == 0");
+    s->backend = backend;
+    return RKL_OK;
+}
+
+rkl_status rkl_sur_check(rkl_surrogate* s)
+{
+    if (!s) return RKL_ERR_INVALID_ARG;
+    unsigned w = 0;
+    SUR_CK(s, cudaMemcpyAsync(&w, s->d_tcst, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream));
+    SUR_CK(s, cudaStreamSynchronize(s->stream));
+    SUR_CK(s, cudaMemsetAsync(s->d_tcst, 0, sizeof(unsigned), s->stream));
+    if (w & ST_TIMEOUT) return sfail(s, RKL_ERR_TIMEOUT, "a bounded wait of a tensor-core convolution gave up");
     return RKL_OK;
 }
 

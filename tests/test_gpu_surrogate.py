@@ -191,3 +191,49 @@ def test_surrogate_super_step_accept_and_fallback(rk):
     assert acc and s == 0
     assert torch.allclose(T3, Td + dT, rtol=0, atol=1e-6)
     rk._lib.rkl_sur_destroy(sur)
+
+
+def test_tcgen05_backend_matches_warp_mma_and_oracle(rk):
+    """The tcgen05 convolutions (TMEM accumulators) against the warp-level
+    mma.sync ones on the same BF16 inputs -- they differ only in the order
+    of the FP32 accumulation and in the BF16 rounding it can flip -- and
+    against the FP64 oracle with the same bounds as the forward test;
+    then the weight gradients of a backward pass whose backward-data
+    convolutions run on tcgen05."""
+    import torch
+    sur, params, T, b, Td, bd, dx = _setup(rk, shape=(8, 32, 16))
+    kappa0, ratio, hs = 0.01, 100.0, 2e-3
+    rk._lib.rkl_sur_features(sur, Td, bd, kappa0, True, ratio)
+    out = {}
+    for backend in (0, 1):
+        rk._lib.rkl_sur_set_backend(sur, backend)
+        dT = torch.empty_like(Td)
+        rk._lib.rkl_sur_forward(sur, hs, dT)
+        rk._lib.rkl_sur_check(sur)
+        out[backend] = host(dT)
+    rl2, cos = _stats(out[1], out[0])
+    print(f"tcgen05 vs mma.sync forward: rel-L2 {rl2:.3e}, cosine {cos:.6f}")
+    assert rl2 < 1e-2 and cos > 0.9999
+    x = S.features(T, b, kappa0, True, ratio)
+    ref, _ = S.forward(_oracle_params(params), x, hs, dx)
+    rl2, cos = _stats(out[1], ref)
+    assert rl2 < 5e-2 and cos > 0.998
+    assert abs(out[1].sum()) <= 1e-5 * np.abs(out[1]).sum()
+    # backward with tcgen05 backward-data against the oracle's gradients
+    rng = np.random.default_rng(5)
+    target = rng.normal(scale=1e-3, size=T.shape)
+    target -= target.mean()
+    rk._lib.rkl_sur_set_backend(sur, 1)
+    rk._lib.rkl_sur_forward(sur, hs)
+    rk._lib.rkl_sur_backward(sur, torch_dev(target))
+    rk._lib.rkl_sur_check(sur)
+    _, grads, _ = S.loss_and_grad(_oracle_params(params), x, target.astype(np.float32).astype(np.float64), hs, dx)
+    for l in range(5):
+        gw, gb = rk._lib.rkl_sur_get_grads(sur, l)
+        co, ci = gw.shape[1], gw.shape[2]
+        gw_or = gw.astype(np.float64).transpose(1, 2, 0).reshape(co, ci, 3, 3, 3)
+        rci = REAL_IN if l == 0 else ci
+        rl2, cos = _stats(gw_or[:, :rci], grads[l][0])
+        print(f"tcgen05 backward layer {l}: dW rel-L2 {rl2:.3e} cos {cos:.6f}")
+        assert rl2 < 1e-1 and cos > 0.995, l
+    rk._lib.rkl_sur_destroy(sur)
