@@ -411,11 +411,11 @@ rkl_status rkl_sur_get_grads(rkl_surrogate *sur, int layer, float *gw, float *gb
 rkl_status rkl_sur_features(rkl_surrogate *sur, const void *T, const void *b, double kappa_par0,
                             int spitzer, double dt_over_dtexpl);
 /*
- * Convolution backend of the forward and backward-data passes: 0 (default)
- * the warp-level mma.sync kernels, 1 the tcgen05 kernels (M = 128-voxel
- * blocks of one plane, accumulators in tensor memory; needs W % 8 == 0 and
- * H % 16 == 0, else RKL_ERR_UNSUPPORTED).  Weight gradients use the
- * warp-level kernel either way.
+ * Convolution backend of the forward and backward-data passes: 0 the
+ * warp-level mma.sync kernels, 1 the tcgen05 kernels (M = 128-voxel blocks
+ * of one plane, accumulators in tensor memory; needs W % 8 == 0 and
+ * H % 16 == 0, else RKL_ERR_UNSUPPORTED).  The default is 1 where the
+ * patch allows it.  Weight gradients use the warp-level kernel either way.
  */
 rkl_status rkl_sur_set_backend(rkl_surrogate *sur, int backend);
 /* waits for the stream; RKL_ERR_TIMEOUT if a tcgen05 kernel's bounded wait

@@ -11,11 +11,12 @@
 // (rows y = i, x = 0..7) starts at voxel (dx, i + dy) of the halo plane and
 // the next one is one halo row (10 voxels) further -- so every offset reads
 // the same resident plane without any im2col copy.  The weights sit in
-// shared memory once per CTA as [27][Cin/8][Cout][8].  Thread 0 issues the
-// 27 x Cin/16 MMAs of a plane into one of two TMEM accumulators and commits
-// them to an mbarrier; while they run, the four warps (one TMEM lane quarter
-// each) drain the other accumulator of the previous plane (bias, ReLU or
-// mask, BF16 or FP32 store).  Every wait is bounded and reports ST_TIMEOUT.
+// shared memory once per persistent CTA as [27][Cin/8][Cout][8].  Thread 0
+// issues the 27 x Cin/16 MMAs of a plane into one of two TMEM accumulators
+// and commits them to an mbarrier; while they run, four warps (one TMEM
+// lane quarter each) drain the other accumulator of the previous plane
+// (bias, ReLU or mask, BF16 or FP32 store).  Every wait is bounded and
+// reports ST_TIMEOUT.
 #include <cstdint>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -39,7 +40,7 @@ constexpr int QX = 8, QY = 16;                 // output block of a plane: M = 1
 constexpr int HX = QX + 2, HY = QY + 2;         // halo plane
 constexpr int HP = HX * HY;                     // 180 voxels
 constexpr int NSLOT = 5;                        // planes p-2 .. p+2
-constexpr int NTHR_TC = 128;                    // 4 warps = the 4 TMEM lane quarters
+constexpr int NTHR_TC = 256;                    // warps 4-7 = the 4 TMEM lane quarters
 constexpr int TMEM_COLS = 64;                   // two accumulators of up to 32 columns
 
 template <int CIN, int COUT>
@@ -117,7 +118,11 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v)
 __device__ __forceinline__ int wrapi_tc(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 // MODE 0: ReLU, bf16 out; 1: linear, f32 out; 2: no bias, times the ReLU
-// mask (mask > 0), bf16 out.  Grid: (W/8, H/16, ceil(D/nzc)).
+// mask (mask > 0), bf16 out.  Persistent: work item = (8 x 16 column block,
+// chunk of nzc planes), items blockIdx.x, blockIdx.x + gridDim.x, ...
+// Roles: all threads stream planes; thread 0 issues the MMAs; warps 4-7
+// drain TMEM (warp w reads lane quarter w - 4), so the MMA issue of a plane
+// overlaps the drain of the previous one.
 template <int CIN, int COUT, int MODE>
 __global__ void __launch_bounds__(NTHR_TC, 1)
 conv_tc_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ wt,
@@ -129,30 +134,19 @@ conv_tc_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __rest
     S& sm = *reinterpret_cast<S*>(smem_raw);
     constexpr int NCH = CIN / 8;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int x0 = blockIdx.x * QX, y0 = blockIdx.y * QY, z0 = blockIdx.z * nzc;
-    const int nz = min(nzc, D - z0);
+    const bool drainer = warp >= 4;
+    const int ncolx = W / QX, ncols = ncolx * (H / QY);
+    const int nitems = ncols * ((D + nzc - 1) / nzc);
 
-    // weights [27][COUT][CIN] -> [27][CIN/8][COUT][8]
+    // weights [27][COUT][CIN] -> [27][CIN/8][COUT][8], once per CTA
     for (int t = tid; t < 27 * COUT * NCH; t += NTHR_TC) {
         const int o = t / (COUT * NCH), r = t % (COUT * NCH), n = r / NCH, ch = r % NCH;
         cp16(smem_u32(&sm.W[o][ch][n][0]), wt + ((int64_t)o * COUT + n) * CIN + ch * 8);
     }
-    // halo plane q (z0 + q, periodic) into its ring slot
-    auto load = [&](int q) {
-        const int gz = wrapi_tc(z0 + q, D);
-        const int s = (q + 2 * NSLOT) % NSLOT;
-        for (int t = tid; t < HP * NCH; t += NTHR_TC) {
-            const int hv = t / NCH, ch = t % NCH;
-            const int gy = wrapi_tc(y0 + hv / HX - 1, H), gx = wrapi_tc(x0 + hv % HX - 1, W);
-            cp16(smem_u32(&sm.A[s][ch][hv][0]), in + (((int64_t)gz * H + gy) * W + gx) * CIN + ch * 8);
-        }
-    };
-    load(-1);
-    cp_commit();                                // group: weights + plane -1
-    load(0);
     cp_commit();
-    if (1 <= nz) load(1);
-    cp_commit();
+    float bs[COUT];
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) bs[c] = (MODE != 2 && drainer) ? bias[c] : 0.f;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&sm.tmem)),
@@ -170,87 +164,105 @@ conv_tc_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __rest
     fence_after();
     const unsigned tbase = sm.tmem;
     const unsigned id = idesc<COUT>();
+    const uint64_t bdesc0 = sdesc(smem_u32(&sm.W[0][0][0][0]), COUT * 16, 8 * 16);
     bool ok = true;
+    unsigned gp = 0;                             // planes issued by this CTA (accumulator and phase)
 
-    auto epilogue = [&](int p) {
-        const int k = p & 1;
-        if (!mbar_wait(smem_u32(&sm.bar[k]), (unsigned)((p >> 1) & 1))) ok = false;
-        fence_after();
-        float v[COUT];
-        const unsigned taddr = tbase + ((unsigned)(warp * 32) << 16) + (unsigned)(k * 32);
-        if (COUT == 32) tmem_ld32(taddr, v);
-        else tmem_ld16(taddr, v);
-        fence_before();
-        const int m = warp * 32 + lane;          // TMEM lane = GEMM row = voxel of the block
-        const int64_t gv = ((int64_t)(z0 + p) * H + (y0 + m / QX)) * W + (x0 + m % QX);
-        if (MODE == 1) {
-            float* o = static_cast<float*>(out) + gv * COUT;
-#pragma unroll
-            for (int c = 0; c < COUT; c += 4)
-                *reinterpret_cast<float4*>(o + c) = make_float4(v[c] + bias[c], v[c + 1] + bias[c + 1],
-                                                                v[c + 2] + bias[c + 2], v[c + 3] + bias[c + 3]);
-        } else {
-            __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out) + gv * COUT;
-#pragma unroll
-            for (int c = 0; c < COUT; c += 8) {
-                float w[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    w[i] = v[c + i];
-                    if (MODE == 0) w[i] = fmaxf(w[i] + bias[c + i], 0.f);
-                }
-                if (MODE == 2) {
-                    const uint4 mk = *reinterpret_cast<const uint4*>(mask + gv * COUT + c);
-                    const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        if (!(__bfloat162float(mb[i]) > 0.f)) w[i] = 0.f;
-                }
-                uint4 pk;
-                __nv_bfloat162* ph = reinterpret_cast<__nv_bfloat162*>(&pk);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) ph[i] = __floats2bfloat162_rn(w[2 * i], w[2 * i + 1]);
-                *reinterpret_cast<uint4*>(o + c) = pk;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int col = item % ncols, chunk = item / ncols;
+        const int x0 = (col % ncolx) * QX, y0 = (col / ncolx) * QY, z0 = chunk * nzc;
+        const int nz = min(nzc, D - z0);
+        // halo plane q (z0 + q, periodic) into its ring slot
+        auto load = [&](int q) {
+            const int gz = wrapi_tc(z0 + q, D);
+            const int sl = (q + 2 * NSLOT) % NSLOT;
+            for (int t = tid; t < HP * NCH; t += NTHR_TC) {
+                const int hv = t / NCH, ch = t % NCH;
+                const int gy = wrapi_tc(y0 + hv / HX - 1, H), gx = wrapi_tc(x0 + hv % HX - 1, W);
+                cp16(smem_u32(&sm.A[sl][ch][hv][0]), in + (((int64_t)gz * H + gy) * W + gx) * CIN + ch * 8);
             }
-        }
-    };
-
-    for (int p = 0; p < nz; ++p) {
-        // plane p+2 goes to the slot of plane p-3, whose MMAs (plane p-2)
-        // were waited for in the previous iteration's epilogue
-        if (p + 2 <= nz) load(p + 2);
-        cp_commit();
-        cp_wait<1>();                            // planes up to p + 1 have landed
-        fence_proxy_async();                     // generic-proxy writes -> tensor-core reads
-        fence_before();
-        __syncthreads();
-        if (tid == 0) {
+        };
+        auto drain = [&](int p, unsigned g) {
+            const int k = (int)(g & 1u);
+            if (!mbar_wait(smem_u32(&sm.bar[k]), (g >> 1) & 1u)) ok = false;
             fence_after();
-            const unsigned dt = tbase + (unsigned)((p & 1) * 32);
-            unsigned acc = 0;
-#pragma unroll 1
-            for (int o = 0; o < 27; ++o) {
-                const int dz = o / 9 - 1, dy = (o / 3) % 3 - 1, dx = o % 3 - 1;
-                const int s = (p + dz + 2 * NSLOT) % NSLOT;
-                const unsigned abase = smem_u32(&sm.A[s][0][(dy + 1) * HX + (dx + 1)][0]);
-                const unsigned bbase = smem_u32(&sm.W[o][0][0][0]);
+            float v[COUT];
+            const int q4 = warp - 4;
+            const unsigned taddr = tbase + ((unsigned)(q4 * 32) << 16) + (unsigned)(k * 32);
+            if (COUT == 32) tmem_ld32(taddr, v);
+            else tmem_ld16(taddr, v);
+            fence_before();
+            const int m = q4 * 32 + lane;         // TMEM lane = GEMM row = voxel of the block
+            const int64_t gv = ((int64_t)(z0 + p) * H + (y0 + m / QX)) * W + (x0 + m % QX);
+            if (MODE == 1) {
+                float* o = static_cast<float*>(out) + gv * COUT;
 #pragma unroll
-                for (int kk = 0; kk < CIN / 16; ++kk) {
-                    const uint64_t a = sdesc(abase + (unsigned)(2 * kk * HP * 16), HP * 16, HX * 16);
-                    const uint64_t b = sdesc(bbase + (unsigned)(2 * kk * COUT * 16), COUT * 16, 8 * 16);
-                    mma_f16(dt, a, b, id, acc);
-                    acc = 1;
+                for (int c = 0; c < COUT; c += 4)
+                    *reinterpret_cast<float4*>(o + c) =
+                        make_float4(v[c] + bs[c], v[c + 1] + bs[c + 1], v[c + 2] + bs[c + 2], v[c + 3] + bs[c + 3]);
+            } else {
+                __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out) + gv * COUT;
+#pragma unroll
+                for (int c = 0; c < COUT; c += 8) {
+                    float w[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) w[i] = MODE == 0 ? fmaxf(v[c + i] + bs[c + i], 0.f) : v[c + i];
+                    if (MODE == 2) {
+                        const uint4 mk = *reinterpret_cast<const uint4*>(mask + gv * COUT + c);
+                        const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            if (!(__bfloat162float(mb[i]) > 0.f)) w[i] = 0.f;
+                    }
+                    uint4 pk;
+                    __nv_bfloat162* ph = reinterpret_cast<__nv_bfloat162*>(&pk);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) ph[i] = __floats2bfloat162_rn(w[2 * i], w[2 * i + 1]);
+                    *reinterpret_cast<uint4*>(o + c) = pk;
                 }
             }
-            mma_commit(smem_u32(&sm.bar[p & 1]));
+        };
+
+        load(-1);
+        load(0);
+        if (1 <= nz) load(1);
+        cp_commit();
+        for (int p = 0; p < nz; ++p) {
+            cp_wait<0>();                        // planes up to p + 1 (and the weights) have landed
+            fence_proxy_async();                 // generic-proxy writes -> tensor-core reads
+            fence_before();
+            __syncthreads();                     // also: the MMAs of plane p-2 were drained
+            if (tid == 0) {
+                fence_after();
+                const unsigned dt = tbase + (gp & 1u) * 32u;
+                uint64_t ab[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    ab[d] = sdesc(smem_u32(&sm.A[(p - 1 + d + 2 * NSLOT) % NSLOT][0][0][0]), HP * 16, HX * 16);
+#pragma unroll
+                for (int o = 0; o < 27; ++o) {
+                    const int dz = o / 9, dy = (o / 3) % 3, dx = o % 3;
+#pragma unroll
+                    for (int kk = 0; kk < CIN / 16; ++kk) {
+                        const uint64_t a = ab[dz] + (uint64_t)(((dy * HX + dx) * 16 + 2 * kk * HP * 16) >> 4);
+                        const uint64_t b = bdesc0 + (uint64_t)(((o * NCH + 2 * kk) * COUT * 16) >> 4);
+                        mma_f16(dt, a, b, id, (o | kk) != 0 ? 1u : 0u);
+                    }
+                }
+                mma_commit(smem_u32(&sm.bar[gp & 1u]));
+            }
+            // plane p+2 into the slot of plane p-3, last read by the MMAs of
+            // plane p-2, which the drainers waited for before this barrier
+            if (p + 2 <= nz) load(p + 2);
+            cp_commit();
+            if (drainer && p >= 1) drain(p - 1, gp - 1);
+            ++gp;
         }
-        __syncwarp();
-        if (p >= 1) epilogue(p - 1);
+        if (drainer && nz >= 1) drain(nz - 1, gp - 1);
+        fence_before();
+        __syncthreads();                         // ring slots and accumulators free for the next item
+        fence_after();
     }
-    if (nz >= 1) epilogue(nz - 1);
-    fence_before();
-    __syncthreads();
-    fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tbase), "r"(TMEM_COLS)
                      : "memory");
@@ -259,6 +271,18 @@ conv_tc_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __rest
         mbar_inval(smem_u32(&sm.bar[1]));
     }
     if (!ok && status) atomicOr(status, ST_TIMEOUT);
+}
+
+int sm_count_tc()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 152;
+    }
+    return n;
 }
 
 template <int CIN, int COUT, int MODE>
@@ -273,7 +297,9 @@ cudaError_t conv_tc_t(const void* in, const void* wt, const float* bias, const v
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid(W / QX, H / QY, (D + nzc - 1) / nzc);
+    const int nitems = (W / QX) * (H / QY) * ((D + nzc - 1) / nzc);
+    const int per_sm = smem <= 113 * 1024 ? 2 : 1;
+    const int grid = nitems < per_sm * sm_count_tc() ? nitems : per_sm * sm_count_tc();
     conv_tc_kernel<CIN, COUT, MODE><<<grid, NTHR_TC, smem, st>>>(
         static_cast<const __nv_bfloat16*>(in), static_cast<const __nv_bfloat16*>(wt), bias,
         static_cast<const __nv_bfloat16*>(mask), out, D, H, W, nzc, status);

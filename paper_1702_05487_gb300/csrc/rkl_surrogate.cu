@@ -126,7 +126,7 @@ cudaError_t conv_fwd(rkl_surrogate* s, int cin, int cout, int mode, const void* 
                      const void* mask, void* out)
 {
     if (s->backend == 1)
-        return conv::conv_forward_tc(cin, cout, mode, in, wt, bias, mask, out, s->D, s->H, s->W, 16, s->d_tcst,
+        return conv::conv_forward_tc(cin, cout, mode, in, wt, bias, mask, out, s->D, s->H, s->W, 8, s->d_tcst,
                                      s->stream);
     return conv::conv_forward(cin, cout, mode, in, wt, bias, mask, out, s->D, s->H, s->W, s->stream);
 }
@@ -207,6 +207,7 @@ rkl_status rkl_sur_create(int D, int H, int W, const double* dx, void* cuda_stre
         if (!(dx[d] > 0.0) || !std::isfinite(dx[d])) return sfail(nullptr, RKL_ERR_INVALID_ARG, "bad dx");
     rkl_surrogate* s = new rkl_surrogate();
     s->D = D; s->H = H; s->W = W;
+    s->backend = (W % 8 == 0 && H % 16 == 0) ? 1 : 0;     // tcgen05 where the blocks tile the patch
     s->V = (int64_t)D * H * W;
     for (int d = 0; d < 3; ++d) {
         s->dx[d] = dx[d];
