@@ -2,20 +2,25 @@
 // cores: tcgen05.mma with operands described in shared memory and the FP32
 // accumulator in tensor memory (TMEM).
 //
-// Implicit GEMM per output plane: M = 128 voxels (an 8 x 16 block of one z
-// plane, x fastest), N = Cout, K = 27 offsets x Cin.  A CTA marches such a
-// block through a chunk of planes.  Input planes with their one-voxel halo
-// (10 x 18 voxels) stream through a 5-slot shared-memory ring, each stored
-// chunk-major ([Cin/8][180 voxels][8 channels]): for an offset (dz, dy, dx)
-// the A operand is then a plain K-major no-swizzle matrix -- core matrix i
-// (rows y = i, x = 0..7) starts at voxel (dx, i + dy) of the halo plane and
-// the next one is one halo row (10 voxels) further -- so every offset reads
-// the same resident plane without any im2col copy.  The weights sit in
-// shared memory once per persistent CTA as [27][Cin/8][Cout][8].  Thread 0
-// issues the 27 x Cin/16 MMAs of a plane into one of two TMEM accumulators
-// and commits them to an mbarrier; while they run, four warps (one TMEM
-// lane quarter each) drain the other accumulator of the previous plane
-// (bias, ReLU or mask, BF16 or FP32 store).  Every wait is bounded and
+// Implicit GEMM, input-plane major: M = 128 voxels (an 8 x 16 block of a z
+// plane, x fastest), K = 9 in-plane offsets x Cin per input plane, and
+// N = 3 Cout: one MMA multiplies a shifted copy of input plane q by the
+// weights of dz = +1, 0, -1 side by side and so adds q's contribution to
+// output planes q - 1, q and q + 1 at once (each output plane owns Cout
+// TMEM columns; a chunk of nz planes holds nz + 2 of them).  A resident
+// input plane is therefore read by the tensor cores once per in-plane
+// offset instead of three times, and a plane needs 9 Cin/16 MMAs instead of
+// 27 Cin/16.  Input planes with their one-voxel halo (10 x 18 voxels)
+// stream through a 5-slot shared-memory ring, each stored chunk-major
+// ([Cin/8][180 voxels][8 channels]): for an offset (dy, dx) the A operand
+// is then a plain K-major no-swizzle matrix -- core matrix i (rows y = i,
+// x = 0..7) starts at voxel (dx, i + dy) of the halo plane and the next one
+// is one halo row (10 voxels) further.  The weights sit in shared memory
+// once per persistent CTA as [9][Cin/8][3 Cout][8].  Thread 0 issues the
+// MMAs of an input plane and commits them to an mbarrier; while they run,
+// four warps (one TMEM lane quarter each) drain the output plane that the
+// previous input plane completed (bias, ReLU or mask, BF16 or FP32 store)
+// and clear the columns the next one starts.  Every wait is bounded and
 // reports ST_TIMEOUT.
 #include <cstdint>
 #include <cuda_bf16.h>
@@ -39,15 +44,16 @@ using x2::smem_u32;
 constexpr int QX = 8, QY = 16;                 // output block of a plane: M = 128
 constexpr int HX = QX + 2, HY = QY + 2;         // halo plane
 constexpr int HP = HX * HY;                     // 180 voxels
-constexpr int NSLOT = 5;                        // planes p-2 .. p+2
+constexpr int NSLOT = 5;                        // input planes q-3 .. q+1 (and q+2 in flight)
 constexpr int NTHR_TC = 256;                    // warps 4-7 = the 4 TMEM lane quarters
-constexpr int TMEM_COLS = 64;                   // two accumulators of up to 32 columns
+constexpr int NZC_TC = 6;                       // output planes per work item
+constexpr int TMEM_COLS = 256;                  // 32 (NZC_TC + 2) columns
 
 template <int CIN, int COUT>
 struct TcSmem {
-    __nv_bfloat16 W[27][CIN / 8][COUT][8];      // B operands, K-major core matrices
+    __nv_bfloat16 W[9][CIN / 8][3 * COUT][8];   // B operands: per (dy, dx) the dz = +1, 0, -1 blocks
     __nv_bfloat16 A[NSLOT][CIN / 8][HP][8];     // A operands, one halo plane per slot
-    unsigned long long bar[2];                  // MMA completion, one per accumulator
+    unsigned long long bar[2];                  // MMA completion of alternate input planes
     unsigned tmem;                              // TMEM base column from tcgen05.alloc
 };
 
@@ -61,11 +67,11 @@ __device__ __forceinline__ uint64_t sdesc(unsigned addr, unsigned lbo, unsigned 
 }
 
 // Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, N = COUT, M = 128.
-template <int COUT>
+// K-major, M = 128, N given.
+template <int N>
 __device__ __forceinline__ unsigned idesc()
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(COUT >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_f16(unsigned dtmem, uint64_t a, uint64_t b, unsigned id, unsigned accumulate)
@@ -115,19 +121,38 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v)
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// zero 32 / 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_zero32(unsigned taddr)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};\n" ::"r"(taddr),
+        "r"(0u)
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_zero16(unsigned taddr)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1};\n" ::"r"(taddr),
+        "r"(0u)
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+}
+
 __device__ __forceinline__ int wrapi_tc(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 // MODE 0: ReLU, bf16 out; 1: linear, f32 out; 2: no bias, times the ReLU
 // mask (mask > 0), bf16 out.  Persistent: work item = (8 x 16 column block,
-// chunk of nzc planes), items blockIdx.x, blockIdx.x + gridDim.x, ...
-// Roles: all threads stream planes; thread 0 issues the MMAs; warps 4-7
-// drain TMEM (warp w reads lane quarter w - 4), so the MMA issue of a plane
-// overlaps the drain of the previous one.
+// chunk of NZC_TC output planes).  Roles: all threads stream input planes;
+// thread 0 issues the MMAs; warps 4-7 drain and clear TMEM (warp w: lane
+// quarter w - 4).
 template <int CIN, int COUT, int MODE>
 __global__ void __launch_bounds__(NTHR_TC, 1)
 conv_tc_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ wt,
                const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask, void* __restrict__ out,
-               int D, int H, int W, int nzc, unsigned* status)
+               int D, int H, int W, unsigned* status)
 {
     using S = TcSmem<CIN, COUT>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -135,13 +160,17 @@ conv_tc_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __rest
     constexpr int NCH = CIN / 8;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool drainer = warp >= 4;
+    const int q4 = warp - 4;
     const int ncolx = W / QX, ncols = ncolx * (H / QY);
-    const int nitems = ncols * ((D + nzc - 1) / nzc);
+    const int nitems = ncols * ((D + NZC_TC - 1) / NZC_TC);
 
-    // weights [27][COUT][CIN] -> [27][CIN/8][COUT][8], once per CTA
+    // weights [27][COUT][CIN] (o = (dz+1) 9 + (dy+1) 3 + dx+1) -> [9][CIN/8][3 COUT][8]
+    // with block j of the N dimension holding dz = 1 - j
     for (int t = tid; t < 27 * COUT * NCH; t += NTHR_TC) {
-        const int o = t / (COUT * NCH), r = t % (COUT * NCH), n = r / NCH, ch = r % NCH;
-        cp16(smem_u32(&sm.W[o][ch][n][0]), wt + ((int64_t)o * COUT + n) * CIN + ch * 8);
+        const int e = t / (3 * COUT * NCH), r = t % (3 * COUT * NCH);
+        const int jn = r / NCH, ch = r % NCH, j = jn / COUT, n = jn % COUT;
+        const int o = (2 - j) * 9 + e;
+        cp16(smem_u32(&sm.W[e][ch][jn][0]), wt + ((int64_t)o * COUT + n) * CIN + ch * 8);
     }
     cp_commit();
     float bs[COUT];
@@ -163,16 +192,19 @@ conv_tc_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __rest
     __syncthreads();
     fence_after();
     const unsigned tbase = sm.tmem;
-    const unsigned id = idesc<COUT>();
-    const uint64_t bdesc0 = sdesc(smem_u32(&sm.W[0][0][0][0]), COUT * 16, 8 * 16);
+    const unsigned id3 = idesc<3 * COUT>(), id1 = idesc<COUT>();
+    const uint64_t bdesc0 = sdesc(smem_u32(&sm.W[0][0][0][0]), 3 * COUT * 16, 8 * 16);
+    const unsigned tlane = tbase + ((unsigned)(q4 * 32) << 16);     // drainers' lane quarter
     bool ok = true;
-    unsigned gp = 0;                             // planes issued by this CTA (accumulator and phase)
+    unsigned g = 0;                              // input planes committed by this CTA (phase)
 
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int col = item % ncols, chunk = item / ncols;
-        const int x0 = (col % ncolx) * QX, y0 = (col / ncolx) * QY, z0 = chunk * nzc;
-        const int nz = min(nzc, D - z0);
-        // halo plane q (z0 + q, periodic) into its ring slot
+        const int x0 = (col % ncolx) * QX, y0 = (col / ncolx) * QY, z0 = chunk * NZC_TC;
+        const int nz = min(NZC_TC, D - z0);
+        // output plane r (z0 + r, -1 <= r <= nz) owns columns COUT (r + 1) ...
+        auto col_of = [&](int r) { return (unsigned)(COUT * (r + 1)); };
+        // input plane q (z0 + q, periodic, -1 <= q <= nz) into its ring slot
         auto load = [&](int q) {
             const int gz = wrapi_tc(z0 + q, D);
             const int sl = (q + 2 * NSLOT) % NSLOT;
@@ -182,18 +214,19 @@ conv_tc_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __rest
                 cp16(smem_u32(&sm.A[sl][ch][hv][0]), in + (((int64_t)gz * H + gy) * W + gx) * CIN + ch * 8);
             }
         };
-        auto drain = [&](int p, unsigned g) {
-            const int k = (int)(g & 1u);
-            if (!mbar_wait(smem_u32(&sm.bar[k]), (g >> 1) & 1u)) ok = false;
+        auto clear = [&](int r) {
+            if (COUT == 32) tmem_zero32(tlane + col_of(r));
+            else tmem_zero16(tlane + col_of(r));
+        };
+        // drain output plane r once the MMAs of input plane r + 1 (commit k) are done
+        auto drain = [&](int r, unsigned k) {
+            if (!mbar_wait(smem_u32(&sm.bar[k & 1u]), (k >> 1) & 1u)) ok = false;
             fence_after();
             float v[COUT];
-            const int q4 = warp - 4;
-            const unsigned taddr = tbase + ((unsigned)(q4 * 32) << 16) + (unsigned)(k * 32);
-            if (COUT == 32) tmem_ld32(taddr, v);
-            else tmem_ld16(taddr, v);
-            fence_before();
+            if (COUT == 32) tmem_ld32(tlane + col_of(r), v);
+            else tmem_ld16(tlane + col_of(r), v);
             const int m = q4 * 32 + lane;         // TMEM lane = GEMM row = voxel of the block
-            const int64_t gv = ((int64_t)(z0 + p) * H + (y0 + m / QX)) * W + (x0 + m % QX);
+            const int64_t gv = ((int64_t)(z0 + r) * H + (y0 + m / QX)) * W + (x0 + m % QX);
             if (MODE == 1) {
                 float* o = static_cast<float*>(out) + gv * COUT;
 #pragma unroll
@@ -225,42 +258,63 @@ conv_tc_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __rest
 
         load(-1);
         load(0);
-        if (1 <= nz) load(1);
         cp_commit();
-        for (int p = 0; p < nz; ++p) {
-            cp_wait<0>();                        // planes up to p + 1 (and the weights) have landed
+        // output plane 1 is first reached by input plane 0 (accumulating)
+        if (drainer && nz >= 2) clear(1);
+        for (int q = -1; q <= nz; ++q) {
+            cp_wait<0>();                        // input plane q (and the weights) has landed
             fence_proxy_async();                 // generic-proxy writes -> tensor-core reads
             fence_before();
-            __syncthreads();                     // also: the MMAs of plane p-2 were drained
+            __syncthreads();                     // also: cleared columns and drained planes are done
             if (tid == 0) {
                 fence_after();
-                const unsigned dt = tbase + (gp & 1u) * 32u;
-                uint64_t ab[3];
+                const uint64_t ab = sdesc(smem_u32(&sm.A[(q + 2 * NSLOT) % NSLOT][0][0][0]), HP * 16, HX * 16);
+                if (q == -1 || q == nz) {
+                    // edge planes reach one output plane: dz = -1 (q = -1 -> r = 0) or dz = +1 (q = nz -> r = nz - 1)
+                    const int j = q == -1 ? 2 : 0;
+                    const unsigned dt = tbase + col_of(q == -1 ? 0 : nz - 1);
 #pragma unroll
-                for (int d = 0; d < 3; ++d)
-                    ab[d] = sdesc(smem_u32(&sm.A[(p - 1 + d + 2 * NSLOT) % NSLOT][0][0][0]), HP * 16, HX * 16);
+                    for (int e = 0; e < 9; ++e)
 #pragma unroll
-                for (int o = 0; o < 27; ++o) {
-                    const int dz = o / 9, dy = (o / 3) % 3, dx = o % 3;
+                        for (int kk = 0; kk < CIN / 16; ++kk) {
+                            const uint64_t a = ab + (uint64_t)((((e / 3) * HX + e % 3) * 16 + 2 * kk * HP * 16) >> 4);
+                            const uint64_t b =
+                                bdesc0 + (uint64_t)((((e * NCH + 2 * kk) * 3 * COUT) + j * COUT) * 16 >> 4);
+                            mma_f16(dt, a, b, id1, (q == -1 && (e | kk) == 0) ? 0u : 1u);
+                        }
+                } else {
+                    const unsigned dt = tbase + col_of(q - 1);
 #pragma unroll
-                    for (int kk = 0; kk < CIN / 16; ++kk) {
-                        const uint64_t a = ab[dz] + (uint64_t)(((dy * HX + dx) * 16 + 2 * kk * HP * 16) >> 4);
-                        const uint64_t b = bdesc0 + (uint64_t)(((o * NCH + 2 * kk) * COUT * 16) >> 4);
-                        mma_f16(dt, a, b, id, (o | kk) != 0 ? 1u : 0u);
-                    }
+                    for (int e = 0; e < 9; ++e)
+#pragma unroll
+                        for (int kk = 0; kk < CIN / 16; ++kk) {
+                            const uint64_t a = ab + (uint64_t)((((e / 3) * HX + e % 3) * 16 + 2 * kk * HP * 16) >> 4);
+                            const uint64_t b = bdesc0 + (uint64_t)(((e * NCH + 2 * kk) * 3 * COUT) * 16 >> 4);
+                            mma_f16(dt, a, b, id3, 1u);
+                        }
                 }
-                mma_commit(smem_u32(&sm.bar[gp & 1u]));
+                mma_commit(smem_u32(&sm.bar[g & 1u]));
             }
-            // plane p+2 into the slot of plane p-3, last read by the MMAs of
-            // plane p-2, which the drainers waited for before this barrier
-            if (p + 2 <= nz) load(p + 2);
+            // input plane q + 2 into the slot of plane q - 3, whose MMAs
+            // completed before the drain of the previous iteration
+            if (q + 2 <= nz) load(q + 2);
             cp_commit();
-            if (drainer && p >= 1) drain(p - 1, gp - 1);
-            ++gp;
+            if (drainer) {
+                // output plane q - 1 is complete once input plane q's MMAs are;
+                // drain r = q - 2 (input q - 1 done) and clear the columns that
+                // input plane q + 1 starts (r = q + 2)
+                if (q >= 1 && q - 2 >= 0) drain(q - 2, g - 1);
+                if (q + 2 <= nz - 1 && q + 2 >= 2) clear(q + 2);
+                fence_before();
+            }
+            ++g;
         }
-        if (drainer && nz >= 1) drain(nz - 1, gp - 1);
-        fence_before();
-        __syncthreads();                         // ring slots and accumulators free for the next item
+        // the last output plane, complete with input plane nz
+        if (drainer) {
+            drain(nz - 1, g - 1);
+            fence_before();
+        }
+        __syncthreads();                         // ring slots and TMEM columns free for the next item
         fence_after();
     }
     if (warp == 0)
@@ -287,7 +341,7 @@ int sm_count_tc()
 
 template <int CIN, int COUT, int MODE>
 cudaError_t conv_tc_t(const void* in, const void* wt, const float* bias, const void* mask, void* out, int D, int H,
-                      int W, int nzc, unsigned* status, cudaStream_t st)
+                      int W, unsigned* status, cudaStream_t st)
 {
     const int smem = (int)sizeof(TcSmem<CIN, COUT>);
     static bool attr = false;
@@ -297,12 +351,12 @@ cudaError_t conv_tc_t(const void* in, const void* wt, const float* bias, const v
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const int nitems = (W / QX) * (H / QY) * ((D + nzc - 1) / nzc);
-    const int per_sm = smem <= 113 * 1024 ? 2 : 1;
+    const int nitems = (W / QX) * (H / QY) * ((D + NZC_TC - 1) / NZC_TC);
+    const int per_sm = smem <= 113 * 1024 ? 2 : 1;         // and 2 x 256 TMEM columns
     const int grid = nitems < per_sm * sm_count_tc() ? nitems : per_sm * sm_count_tc();
     conv_tc_kernel<CIN, COUT, MODE><<<grid, NTHR_TC, smem, st>>>(
         static_cast<const __nv_bfloat16*>(in), static_cast<const __nv_bfloat16*>(wt), bias,
-        static_cast<const __nv_bfloat16*>(mask), out, D, H, W, nzc, status);
+        static_cast<const __nv_bfloat16*>(mask), out, D, H, W, status);
     return cudaGetLastError();
 }
 
@@ -312,17 +366,18 @@ cudaError_t conv_forward_tc(int cin, int cout, int mode, const void* in, const v
                             const void* mask, void* out, int D, int H, int W, int nzc, unsigned* status,
                             cudaStream_t st)
 {
-    if (W % QX || H % QY || D < 1 || nzc < 1) return cudaErrorInvalidValue;
+    (void)nzc;                                   // the chunk length is fixed by the TMEM columns
+    if (W % QX || H % QY || D < 1) return cudaErrorInvalidValue;
     if (cin == 16 && cout == 32 && mode == 0)
-        return conv_tc_t<16, 32, 0>(in, wt, bias, mask, out, D, H, W, nzc, status, st);
+        return conv_tc_t<16, 32, 0>(in, wt, bias, mask, out, D, H, W, status, st);
     if (cin == 32 && cout == 32 && mode == 0)
-        return conv_tc_t<32, 32, 0>(in, wt, bias, mask, out, D, H, W, nzc, status, st);
+        return conv_tc_t<32, 32, 0>(in, wt, bias, mask, out, D, H, W, status, st);
     if (cin == 32 && cout == 16 && mode == 1)
-        return conv_tc_t<32, 16, 1>(in, wt, bias, mask, out, D, H, W, nzc, status, st);
+        return conv_tc_t<32, 16, 1>(in, wt, bias, mask, out, D, H, W, status, st);
     if (cin == 32 && cout == 32 && mode == 2)
-        return conv_tc_t<32, 32, 2>(in, wt, bias, mask, out, D, H, W, nzc, status, st);
+        return conv_tc_t<32, 32, 2>(in, wt, bias, mask, out, D, H, W, status, st);
     if (cin == 16 && cout == 32 && mode == 2)
-        return conv_tc_t<16, 32, 2>(in, wt, bias, mask, out, D, H, W, nzc, status, st);
+        return conv_tc_t<16, 32, 2>(in, wt, bias, mask, out, D, H, W, status, st);
     return cudaErrorInvalidValue;
 }
 
