@@ -257,12 +257,13 @@ conv_tc_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __rest
         };
 
         load(-1);
+        cp_commit();
         load(0);
         cp_commit();
         // output plane 1 is first reached by input plane 0 (accumulating)
         if (drainer && nz >= 2) clear(1);
         for (int q = -1; q <= nz; ++q) {
-            cp_wait<0>();                        // input plane q (and the weights) has landed
+            cp_wait<1>();                        // input plane q (and the weights) has landed; q + 1 may be in flight
             fence_proxy_async();                 // generic-proxy writes -> tensor-core reads
             fence_before();
             __syncthreads();                     // also: cleared columns and drained planes are done
