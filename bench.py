@@ -459,6 +459,83 @@ def run_split(args):
     print(json.dumps(line), flush=True)
 
 
+def measured_bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (cuBLAS bf16 burst)"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+# channels (cin, cout) of the six surrogate convolutions as the network uses
+# them, and as the kernels compute them (layer 0 input and layer 5 output
+# padded to 16 channels)
+SUR_CH_USED = [(6, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 3)]
+SUR_CH_RUN = [(16, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 16)]
+
+
+def surrogate_forward_timing(n=128, reps=10):
+    """Device time of one surrogate forward pass (six 3x3x3 convolutions,
+    features already in place) on an n^3 patch with each convolution
+    backend, CUDA events on the surrogate's stream after three warm-up
+    passes.  Returns {backend: ms} and the FLOPs per pass (used, run)."""
+    import torch
+    import paper_1702_05487_gb300 as rk
+    L = rk._lib
+    stream = torch.cuda.current_stream()
+    sur = L.rkl_sur_create(n, n, n, (1.0 / n,) * 3, stream.cuda_stream)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    T = 1.0 + 0.2 * torch.rand(n, n, n, device="cuda", generator=g)
+    b = torch.randn(3, n, n, n, device="cuda", generator=g)
+    b = (b / b.norm(dim=0, keepdim=True)).contiguous()
+    L.rkl_sur_features(sur, T, b, 0.01, True, 100.0)
+    out = {}
+    for backend in (0, 1):
+        L.rkl_sur_set_backend(sur, backend)
+        for _ in range(3):
+            L.rkl_sur_forward(sur, 2e-3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            L.rkl_sur_forward(sur, 2e-3)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        L.rkl_sur_check(sur)
+        out[backend] = e0.elapsed_time(e1) / reps
+    L.rkl_sur_destroy(sur)
+    cells = n ** 3
+    flops = tuple(2.0 * 27 * cells * sum(ci * co for ci, co in ch) for ch in (SUR_CH_USED, SUR_CH_RUN))
+    return out, flops
+
+
+def surrogate_roofline(fwd_ms, flops):
+    peak, kind = measured_bf16_peak()
+    achieved = flops[0] / (fwd_ms[1] * 1e-3) / 1e12
+    return {"bound": "tensor", "kernel": "surrogate forward (tcgen05 convolutions)", "achieved": achieved,
+            "peak": peak, "peak_kind": kind, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "algorithmic_flops_per_pass": flops[0], "executed_flops_per_pass": flops[1],
+            "executed_tflops": flops[1] / (fwd_ms[1] * 1e-3) / 1e12, "forward_ms": fwd_ms[1],
+            "forward_ms_mma_sync": fwd_ms[0]}
+
+
+def run_surrogate_forward(args):
+    """Surrogate inference kernels alone: one forward pass on a 128^3 patch
+    with the tcgen05 convolutions and with the warp-level mma.sync ones."""
+    import torch
+    torch.cuda.set_device(0)
+    with ClockSampler(0) as clocks:
+        fwd, flops = surrogate_forward_timing(128, max(args.steps, 10))
+    line = {"metric": "surrogate forward passes/s (128^3 patch)", "value": 1e3 / fwd[1], "unit": "pass/s",
+            "n_gpus": 1, "steps": max(args.steps, 10), "warmup": 3, "ms_per_step": fwd[1],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f32",
+            "data": "synthetic", "config": {"workload": "surrogate128-forward", "shape": [128, 128, 128],
+                                            "l2": "activations 128 MB per layer in BF16 (L2-sized)"},
+            "roofline": surrogate_roofline(fwd, flops), "clocks": clocks.summary(),
+            "gpu_launches": int(max(args.steps, 10) * 7)}
+    print(json.dumps(line), flush=True)
+
+
 def run_surrogate(args):
     """The learned surrogate on 128^3 patches: training on RKL2-generated
     pairs, threshold calibration at 1e-3 relative L2 on held-out pairs, then
@@ -473,6 +550,7 @@ def run_surrogate(args):
     thr, rows = sur.calibrate(64, accuracy=1e-3)
     errs = [e for _, e in rows]
     tts = sur.time_to_solution(10, accuracy=1e-3)
+    fwd, flops = surrogate_forward_timing(128)
     line = {"metric": "surrogate vs RKL2 time-to-solution @1e-3 L2", "value": tts["speedup"],
             "unit": "x (RKL2 time / surrogate+fallback time)", "n_gpus": 1, "higher_is_better": True,
             "dtype": "bf16/f32", "data": "synthetic",
@@ -480,7 +558,7 @@ def run_surrogate(args):
                        "final_loss": float(np.mean(losses[-50:])), "threshold": thr,
                        "heldout_rel_l2_median": float(np.median(errs)), "heldout_rel_l2_min": float(min(errs)),
                        "heldout_within_1e-3": int(sum(e <= 1e-3 for e in errs)), "heldout": len(errs)},
-            "time_to_solution": tts}
+            "time_to_solution": tts, "roofline": surrogate_roofline(fwd, flops)}
     print(json.dumps(line), flush=True)
 
 
@@ -497,13 +575,15 @@ def main():
     ap.add_argument("--workload", default="tangled256",
                     choices=list(WORKLOADS) + ["ensemble64", "surrogate128", "split256"])
     ap.add_argument("--pairs", type=int, default=20000, help="training pairs of the surrogate workload")
+    ap.add_argument("--forward-only", action="store_true",
+                    help="surrogate128: time the inference convolutions only (no training)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "ensemble64":
         run_ensemble(args)
     elif args.workload == "surrogate128":
-        run_surrogate(args)
+        run_surrogate_forward(args) if args.forward_only else run_surrogate(args)
     elif args.workload == "split256":
         run_split(args)
     else:
