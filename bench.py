@@ -42,7 +42,7 @@ WORKLOAD = "tangled256_spitzer_rkl2"
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, summarised in
 # profiles/stage_x2_tangled256.md), valid only while the stage kernel's
 # sources hash to source_hash (sha256 of STAGE_KERNEL_SOURCES, 16 hex).
-MEASURED_TRAFFIC = {"source_hash": "6f74f8c69264bd9d", "bytes_per_launch": 539581952}
+MEASURED_TRAFFIC = {"source_hash": "4af2e30714ca98d2", "bytes_per_launch": 542256128}
 
 
 # the sources of the default stage kernel (stage_x2_kernel)
@@ -570,7 +570,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", type=int, default=0,
-                    help="stage kernel: 0 auto, 1 generic, 2 tiled, 3/4 paired-cell at 2/3 CTAs per SM, 5 two-stage")
+                    help="stage kernel: 0 auto, 1 generic, 2 tiled, 3/4 paired-cell at 5/6 CTAs per SM, 5 two-stage, 6 bulk copies")
     ap.add_argument("--nzchunk", type=int, default=0, help="planes per CTA (0 automatic, < 0 balanced runs)")
     ap.add_argument("--workload", default="tangled256",
                     choices=list(WORKLOADS) + ["ensemble64", "surrogate128", "split256"])

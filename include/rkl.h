@@ -254,16 +254,17 @@ rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
  * generic kernel), 1 = the generic one-thread-per-cell kernel, 2 = the
  * tiled FP32 3D kernel (32 x 8 tiles, one cell per thread), 3 and 4 = the
  * paired-cell FP32 3D kernel (64 x 4 tiles, two cells per thread in packed
- * f32x2 arithmetic; needs nx % 4 == 0) built for 16 (variant 3) or 24
+ * f32x2 arithmetic; needs nx % 4 == 0) built for 20 (variant 3) or 24
  * (variant 4) resident warps per SM, 5 = the two-stage kernel (stages j and
  * j + 1 per pass over the grid, 60 x 7 tiles; periodic only; allocates a
  * fourth stage buffer), 6 = the paired-cell kernel with its plane bundles
  * copied by the TMA engine (cp.async.bulk rows with mbarrier completion;
  * periodic grids with nx >= 72, else as 3).  RKL_ERR_UNSUPPORTED if the kernel
  * does not apply to the grid.  nzchunk = planes per CTA of the paired-cell
- * kernels (0: chosen from the grid and the SM count so that the last wave
- * of CTAs is nearly full); a negative value selects the balanced schedule instead:
- * one launch of 2 (or 3) CTAs per SM in which every CTA marches an equal run
+ * kernels (0: chosen from the grid and the SM count, at least 3.5 waves of
+ * CTAs where the grid has that many and a last wave that is nearly full); a
+ * negative value selects the balanced schedule instead: one launch of 5 (or
+ * 6) CTAs per SM in which every CTA marches an equal run
  * of the grid's (tile column, plane) pairs.  Drops cached graphs.  Results
  * of all kernels and schedules agree within FP32 rounding.
  */
@@ -280,7 +281,7 @@ rkl_status rkl_plan_set_method(rkl_plan *plan, int method, double sts_nu);
 /*
  * Autotuner: times one super-step of length dt (s from dt / dt_expl(T))
  * with every kernel variant and z-chunk that applies to the grid (generic;
- * tiled; paired-cell at 2 and 3 CTAs per SM, balanced or with 8, 16, 32, 64
+ * tiled; paired-cell at 5 and 6 CTAs per SM, balanced or with 8, 16, 32, 64
  * planes per CTA) on a scratch copy of T (T is not changed), keeps the fastest with
  * rkl_plan_set_variant and returns it.  Allocates and frees one grid-sized
  * scratch array.  Synchronises.

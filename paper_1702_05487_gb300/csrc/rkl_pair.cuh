@@ -53,6 +53,55 @@ __device__ __forceinline__ float2 face2(float2 TL, float2 TR, float2 gn, float2 
     return Fn;
 }
 
+// Constants of the folded face flux below.  With Bn = b_L,n + b_R,n (a sum,
+// not the average) and Ts = T_L + T_R, the flux of Eq. qN is
+//   F = -kappa_par(Ts / 2) / 4 * (Bn (B . g) + 4 (kappa_perp / kappa_par) gn),
+// so the halves of the face averages and the whole prefactor become one
+// constant per launch.  Without saturation face2s returns F / fscale and the
+// divergence absorbs fscale; with saturation the blend needs |F|, so it
+// returns F itself and fscale = 1.
+struct FaceK {
+    float nk;         // -kappa_par0 / 4 (x 2^-2.5 under Spitzer: (Ts / 2)^2.5)
+    float kp4;        // 4 kappa_perp / kappa_par
+    float fscale;     // true flux = fscale x returned value
+};
+
+template <bool SP, bool SAT>
+__device__ __forceinline__ FaceK face_consts(const KPhys<float>& p)
+{
+    FaceK k;
+    k.nk = -0.25f * p.kappa0 * (SP ? 0.17677669529663688f : 1.f);    // 2^-2.5
+    k.kp4 = 4.f * p.kperp;
+    k.fscale = SAT ? 1.f : k.nk;
+    return k;
+}
+
+template <bool SP, bool SAT>
+__device__ __forceinline__ float2 face2s(float2 TL, float2 TR, float2 gn, float2 g1, float2 g2, float2 Bn, float2 B1,
+                                         float2 B2, const FaceK& k, const KPhys<float>& p)
+{
+    const float2 Ts = add2(TL, TR);
+    const float2 bdg = fma2(Bn, gn, fma2(B1, g1, mul2(B2, g2)));
+    const float2 X = fma2(Bn, bdg, mul2(bc2(k.kp4), gn));
+    if (!SAT) {
+        if (SP) return mul2(mul2(mul2(Ts, Ts), sqrt2(Ts)), X);
+        return X;
+    }
+    const float2 nk = SP ? mul2(mul2(bc2(k.nk), mul2(Ts, Ts)), sqrt2(Ts)) : bc2(k.nk);
+    float2 Fn = mul2(nk, X);
+    const float2 F1 = mul2(nk, fma2(B1, bdg, mul2(bc2(k.kp4), g1)));
+    const float2 F2 = mul2(nk, fma2(B2, bdg, mul2(bc2(k.kp4), g2)));
+    const float2 Fmag = sqrt2(fma2(Fn, Fn, fma2(F1, F1, mul2(F2, F2))));
+    float2 Tq = mul2(bc2(0.5f), Ts);
+    if (p.upwind) {
+        Tq.x = Fn.x >= 0.f ? TL.x : TR.x;
+        Tq.y = Fn.y >= 0.f ? TL.y : TR.y;
+    }
+    const float2 q = mul2(mul2(bc2(p.q0), Tq), sqrt2(Tq));
+    const float2 den = add2(q, Fmag);
+    return make_float2(ddiv<float>(q.x, den.x) * Fn.x, ddiv<float>(q.y, den.y) * Fn.y);
+}
+
 // --------------------------------------------------------------------------
 // shared memory and copies
 

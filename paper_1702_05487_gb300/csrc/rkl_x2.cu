@@ -2,7 +2,8 @@
 //
 // Same z-march and plane-bundle pipeline as the tiled kernel, but each
 // thread owns two neighbouring cells in x (columns 2l, 2l + 1 of a 64 x TY
-// tile, one warp per row; TY = 4 gives four CTAs per SM) and evaluates their faces, divergence and recurrence with the packed
+// tile, one warp per row, five CTAs per SM) and evaluates their faces,
+// divergence and recurrence with the packed
 // FP32 pair instructions of sm_100+ (add/sub/mul/fma .f32x2), so one
 // instruction serves both cells.  Shared-memory reads are 64-bit pairs.
 // The x-face below a pair comes from the lane to the left by a warp shuffle
@@ -249,8 +250,8 @@ __device__ __forceinline__ QXY read_qxy(const SM& sm, int ts, int bs, int c, int
 // row -1 and row 0 at columns (c, c+1), and the x-face between columns -1
 // and 0 at row r.
 template <bool SP, bool SAT, class SM>
-__device__ __forceinline__ float2 low_yface2(const SM& sm, const KGrid<float>& g, const KPhys<float>& p, int tm,
-                                             int tc, int tp, int bs, int c)
+__device__ __forceinline__ float2 low_yface2(const SM& sm, const KGrid<float>& g, const KPhys<float>& p,
+                                             const FaceK& fk, int tm, int tc, int tp, int bs, int c)
 {
     const float* T = sm.T[tc];
     const float2 TL = lds2(&T[off(-1, c)]), TR = lds2(&T[off(0, c)]);
@@ -262,15 +263,14 @@ __device__ __forceinline__ float2 low_yface2(const SM& sm, const KGrid<float>& g
     const float2 gzR = sub2(lds2(&sm.T[tp][off(0, c)]), lds2(&sm.T[tm][off(0, c)]));
     float2 b[3];
 #pragma unroll
-    for (int e = 0; e < 3; ++e)
-        b[e] = mul2(bc2(0.5f), add2(lds2(&sm.B[bs][e][off(-1, c)]), lds2(&sm.B[bs][e][off(0, c)])));
-    return face2<SP, SAT>(TL, TR, mul2(sub2(TR, TL), bc2(g.inv_dx[1])), mul2(add2(gxL, gxR), bc2(g.inv_4dx[0])),
-                          mul2(add2(gzL, gzR), bc2(g.inv_4dx[2])), b[1], b[0], b[2], p);
+    for (int e = 0; e < 3; ++e) b[e] = add2(lds2(&sm.B[bs][e][off(-1, c)]), lds2(&sm.B[bs][e][off(0, c)]));
+    return face2s<SP, SAT>(TL, TR, mul2(sub2(TR, TL), bc2(g.inv_dx[1])), mul2(add2(gxL, gxR), bc2(g.inv_4dx[0])),
+                           mul2(add2(gzL, gzR), bc2(g.inv_4dx[2])), b[1], b[0], b[2], fk, p);
 }
 
 template <bool SP, bool SAT, class SM>
-__device__ __forceinline__ float low_xface(const SM& sm, const KGrid<float>& g, const KPhys<float>& p, int tm,
-                                           int tc, int tp, int bs, int r)
+__device__ __forceinline__ float low_xface(const SM& sm, const KGrid<float>& g, const KPhys<float>& p,
+                                           const FaceK& fk, int tm, int tc, int tp, int bs, int r)
 {
     const float* T = sm.T[tc];
     const float TL = T[off(r, -1)], TR = T[off(r, 0)];
@@ -280,9 +280,11 @@ __device__ __forceinline__ float low_xface(const SM& sm, const KGrid<float>& g, 
     const float gzR = sm.T[tp][off(r, 0)] - sm.T[tm][off(r, 0)];
     float b[3];
 #pragma unroll
-    for (int e = 0; e < 3; ++e) b[e] = 0.5f * (sm.B[bs][e][off(r, -1)] + sm.B[bs][e][off(r, 0)]);
-    return face_flux<float, SP, SAT>(TL, TR, (TR - TL) * g.inv_dx[0], (gyL + gyR) * g.inv_4dx[1],
-                                     (gzL + gzR) * g.inv_4dx[2], b[0], b[1], b[2], p);
+    for (int e = 0; e < 3; ++e) b[e] = sm.B[bs][e][off(r, -1)] + sm.B[bs][e][off(r, 0)];
+    // the packed form on a duplicated scalar costs what the scalar form does
+    return face2s<SP, SAT>(bc2(TL), bc2(TR), bc2((TR - TL) * g.inv_dx[0]), bc2((gyL + gyR) * g.inv_4dx[1]),
+                           bc2((gzL + gzR) * g.inv_4dx[2]), bc2(b[0]), bc2(b[1]), bc2(b[2]), fk, p)
+        .x;
 }
 
 }  // namespace x2
@@ -384,13 +386,16 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
 
     const float2 idx2 = bc2(g.inv_dx[0]), idy2 = bc2(g.inv_dx[1]), idz2 = bc2(g.inv_dx[2]);
     const float2 i4x = bc2(g.inv_4dx[0]), i4y = bc2(g.inv_4dx[1]), i4z = bc2(g.inv_4dx[2]);
-    const float2 half = bc2(0.5f);
+    // fluxes in face2s units; cm = -fscale / dx turns their differences into M
+    const FaceK fk = face_consts<SP, SAT>(p);
+    const float2 cmx = bc2(-fk.fscale * g.inv_dx[0]), cmy = bc2(-fk.fscale * g.inv_dx[1]);
+    const float2 cmz = bc2(-fk.fscale * g.inv_dx[2]);
 
     QZ A = read_qz(sm, tslot(-1), bslot(-1), c, r);
     QZ B = read_qz(sm, tslot(0), bslot(0), c, r);
-    float2 Fz_lo = face2<SP, SAT>(A.To, B.To, mul2(sub2(B.To, A.To), idz2), mul2(add2(A.gxo, B.gxo), i4x),
-                                  mul2(add2(A.gyo, B.gyo), i4y), mul2(half, add2(A.bo[2], B.bo[2])),
-                                  mul2(half, add2(A.bo[0], B.bo[0])), mul2(half, add2(A.bo[1], B.bo[1])), p);
+    float2 Fz_lo = face2s<SP, SAT>(A.To, B.To, mul2(sub2(B.To, A.To), idz2), mul2(add2(A.gxo, B.gxo), i4x),
+                                   mul2(add2(A.gyo, B.gyo), i4y), add2(A.bo[2], B.bo[2]), add2(A.bo[0], B.bo[0]),
+                                   add2(A.bo[1], B.bo[1]), fk, p);
     float2 TmO = A.To, TmU = A.TU;
     float TmR = A.Tr;
 
@@ -411,9 +416,8 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
     float mnacc = INFINITY;
     auto finish = [&](int qp) {
         const int par = qp & 1;
-        float2 div = sub2(pend, mul2(lds2(&sm.Fy[par][r][c]), idy2));
-        if (lane == 0) div.x -= sm.FxLo[par][r] * g.inv_dx[0];
-        const float2 M = mul2(bc2(-1.f), div);
+        float2 M = fma2(lds2(&sm.Fy[par][r][c]), bc2(-cmy.x), pend);
+        if (lane == 0) M.x = fmaf(sm.FxLo[par][r], -cmx.x, M.x);
         if (in0) {
             float2* out = reinterpret_cast<float2*>(a.out + pcb);
             if (MODE == 0) {
@@ -455,21 +459,20 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         const float2 TR = make_float2(cur.To.y, cur.Tr);
 
         // +x faces of the pair
-        const float2 Fx = face2<SP, SAT>(
+        const float2 Fx = face2s<SP, SAT>(
             cur.To, TR, mul2(sub2(TR, cur.To), idx2), mul2(add2(cur.gyo, cx.gyR), i4y), mul2(add2(gzo, gzR), i4z),
-            mul2(half, add2(cur.bo[0], make_float2(cur.bo[0].y, cx.bR[0]))),
-            mul2(half, add2(cur.bo[1], make_float2(cur.bo[1].y, cx.bR[1]))),
-            mul2(half, add2(cur.bo[2], make_float2(cur.bo[2].y, cx.bR[2]))), p);
+            add2(cur.bo[0], make_float2(cur.bo[0].y, cx.bR[0])), add2(cur.bo[1], make_float2(cur.bo[1].y, cx.bR[1])),
+            add2(cur.bo[2], make_float2(cur.bo[2].y, cx.bR[2])), fk, p);
         // +y faces
-        const float2 Fy = face2<SP, SAT>(cur.To, cur.TU, mul2(sub2(cur.TU, cur.To), idy2),
-                                         mul2(add2(cur.gxo, cx.gxU), i4x), mul2(add2(gzo, gzU), i4z),
-                                         mul2(half, add2(cur.bo[1], cx.bU[1])), mul2(half, add2(cur.bo[0], cx.bU[0])),
-                                         mul2(half, add2(cur.bo[2], cx.bU[2])), p);
+        const float2 Fy = face2s<SP, SAT>(cur.To, cur.TU, mul2(sub2(cur.TU, cur.To), idy2),
+                                          mul2(add2(cur.gxo, cx.gxU), i4x), mul2(add2(gzo, gzU), i4z),
+                                          add2(cur.bo[1], cx.bU[1]), add2(cur.bo[0], cx.bU[0]),
+                                          add2(cur.bo[2], cx.bU[2]), fk, p);
         // +z faces
-        const float2 Fz = face2<SP, SAT>(cur.To, nxt.To, mul2(sub2(nxt.To, cur.To), idz2),
-                                         mul2(add2(cur.gxo, nxt.gxo), i4x), mul2(add2(cur.gyo, nxt.gyo), i4y),
-                                         mul2(half, add2(cur.bo[2], nxt.bo[2])), mul2(half, add2(cur.bo[0], nxt.bo[0])),
-                                         mul2(half, add2(cur.bo[1], nxt.bo[1])), p);
+        const float2 Fz = face2s<SP, SAT>(cur.To, nxt.To, mul2(sub2(nxt.To, cur.To), idz2),
+                                          mul2(add2(cur.gxo, nxt.gxo), i4x), mul2(add2(cur.gyo, nxt.gyo), i4y),
+                                          add2(cur.bo[2], nxt.bo[2]), add2(cur.bo[0], nxt.bo[0]),
+                                          add2(cur.bo[1], nxt.bo[1]), fk, p);
 
         // the tile's bottom y-faces and left x-faces: one extra face each,
         // taken by warps on different schedulers from plane to plane
@@ -477,9 +480,9 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         const int wy = q & (TY - 1), wx = (q + TY / 2) & (TY - 1);
         if (r == wy) {
             *reinterpret_cast<float2*>(&sm.Fy[par][0][c]) =
-                low_yface2<SP, SAT>(sm, g, p, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), c);
+                low_yface2<SP, SAT>(sm, g, p, fk, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), c);
         } else if (r == wx && lane < TY) {
-            sm.FxLo[par][lane] = low_xface<SP, SAT>(sm, g, p, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), lane);
+            sm.FxLo[par][lane] = low_xface<SP, SAT>(sm, g, p, fk, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), lane);
         }
         if (MODE == 2) {
             const int ys = yslot(q);
@@ -491,7 +494,7 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         const float fxl = __shfl_up_sync(0xffffffffu, Fx.y, 1);
         // divergence without the y-face below (and, on lane 0, the left face)
         const float2 Fx_lo = make_float2(lane == 0 ? 0.f : fxl, Fx.x);
-        pend = fma2(sub2(Fx, Fx_lo), idx2, fma2(Fy, idy2, mul2(sub2(Fz, Fz_lo), idz2)));
+        pend = fma2(sub2(Fx, Fx_lo), cmx, fma2(Fy, cmy, mul2(sub2(Fz, Fz_lo), cmz)));
         pTo = cur.To;
         pcb = cbase;
         cbase += g.plane;
@@ -526,12 +529,14 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
 
 namespace {
 
-// OCC = register budget: built so that OCC x 8 warps fit on an SM (2: up to
-// 128 registers, no spills; 3: up to 80 registers, a few spilled words),
-// i.e. OCC x 8 / TY resident CTAs of 64 x TY tiles.
+// OCC selects the build: 2 the default (x2::kCtasPerSm CTAs per SM, two
+// planes in flight), 3 six CTAs per SM at up to 80 registers with one plane
+// in flight.
 // BULK: bundles copied by the TMA engine (periodic grids with nx >= 72).
+constexpr int ctas_per_sm(int occ) { return occ == 2 ? x2::kCtasPerSm : 6; }
+
 template <bool SP, bool SAT, int MODE, int OCC, bool BULK>
-__global__ void __launch_bounds__(x2::NTHREADS, OCC * (8 / x2::TY))
+__global__ void __launch_bounds__(x2::NTHREADS, ctas_per_sm(OCC))
 stage_x2_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf, unsigned* status, int nzchunk)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -579,7 +584,7 @@ template <bool SP, bool SAT, int MODE, int OCC, bool BULK>
 cudaError_t launch3(const KGrid<float>& g, const KPhys<float>& p, const x2::FastArgs& a, const KCoef<float>& cf,
                     unsigned* status, int nzchunk, cudaStream_t st)
 {
-    constexpr int kCtasPerSm = OCC * (8 / x2::TY);     // resident CTAs per SM
+    constexpr int kCtasPerSm = ctas_per_sm(OCC);
     const int smem = (int)sizeof(x2::SmemT<OCC == 2 ? x2::kPD : 1>);
     static bool attr_set = false;       // the attribute is per function, set once
     if (!attr_set) {
@@ -591,7 +596,7 @@ cudaError_t launch3(const KGrid<float>& g, const KPhys<float>& p, const x2::Fast
     const int ntx = (g.n[0] + x2::TX - 1) / x2::TX, nty = (g.n[1] + x2::TY - 1) / x2::TY;
     dim3 grid(ntx, nty, nzchunk > 0 ? (g.n[2] + nzchunk - 1) / nzchunk : 1);
     if (nzchunk <= 0) {
-        // balanced: OCC CTAs per SM, each run at least 8 planes long
+        // balanced: one wave of resident CTAs, each run at least 8 planes long
         const int64_t U = (int64_t)ntx * nty * g.n[2];
         grid = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)kCtasPerSm * sm_count(), U / 8)), 1, 1);
         nzchunk = 0;
@@ -635,15 +640,20 @@ bool x2_bulk_supported(const LaunchCfg& c, const KGrid<float>& g)
 
 // Planes per CTA when none is given: the chunk length in [16, 48] that
 // minimises (rounds of resident CTAs) x (planes + halo cost) per CTA, so that
-// the last wave of CTAs is not left mostly empty.
+// the last wave of CTAs is not left mostly empty, among the lengths that
+// give at least 3.5 waves of CTAs where the grid has that many.  Measured
+// on the 256^3 grid at five CTAs per SM: chunks of 20-24 planes (3.7-4.4
+// waves) 113 us per stage, 28-37 planes (2.4-3.4 waves) 116 us.
 static int auto_nzchunk(const KGrid<float>& g, int occupancy)
 {
     const int64_t cols = (int64_t)((g.n[0] + x2::TX - 1) / x2::TX) * ((g.n[1] + x2::TY - 1) / x2::TY);
-    const int64_t slots = (int64_t)occupancy * (8 / x2::TY) * sm_count();
+    const int64_t slots = (int64_t)ctas_per_sm(occupancy) * sm_count();
+    const bool many = cols * ((g.n[2] + 15) / 16) * 2 >= 7 * slots;
     int best = 32;
     double cost = 1e300;
     for (int nzc = 16; nzc <= 48; ++nzc) {
         const int64_t chunks = (g.n[2] + nzc - 1) / nzc;
+        if (many && cols * chunks * 2 < 7 * slots) continue;
         const int64_t rounds = (cols * chunks + slots - 1) / slots;
         const double c = (double)rounds * (std::min(nzc, g.n[2]) + 2.5);
         if (c < cost - 1e-9) {
@@ -701,7 +711,7 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
 }
 
 template <bool SP, bool SAT>
-__global__ void __launch_bounds__(x2::NTHREADS, 2 * (8 / x2::TY))
+__global__ void __launch_bounds__(x2::NTHREADS, x2::kCtasPerSm)
 ensemble_x2_kernel(const x2::EnsProb* __restrict__ probs, const x2::EnsSeg* __restrict__ segs, int nseg,
                    int total, int* work, unsigned* done, unsigned* status, int* abort_flag, long long spin_limit)
 {

@@ -8,8 +8,12 @@ namespace rkl {
 namespace x2 {
 
 constexpr int TX = 64;                  // tile columns: 32 lanes x 2 cells
-constexpr int TY = 4;                   // tile rows: one warp per row (4 CTAs per SM)
+constexpr int TY = 4;                   // tile rows: one warp per row
 constexpr int NTHREADS = 32 * TY;
+// Resident CTAs per SM of the default build: 5 x 4 warps at up to 102
+// registers a thread and 5 x 44 KB of shared memory.  Five short CTAs keep
+// more warps eligible than four (fewer barrier and dependency stalls).
+constexpr int kCtasPerSm = 5;
 constexpr int SXS = 72;                 // smem row: halo chunk (4), 64 interior, halo chunk (4)
 constexpr int CPR = SXS / 4;            // 16-byte chunks per smem row
 constexpr int ROWS = TY + 2;
@@ -30,11 +34,9 @@ struct FastArgs {
 // Plane rings for a prefetch distance of PD planes: while plane q is
 // computed, planes q+1 .. q+PD are in flight and plane q+PD+1 is being
 // issued into the slots that plane q-2 (T) or q-1 (b, Y) released.
-// With two planes in flight the rings get power-of-two slot counts (8, 4,
-// 4), so a plane's slot is a mask of its index rather than a division.
 template <int PD>
 struct SmemT {
-    static constexpr int NT = PD == 2 ? 8 : 3 + PD, NB = 2 + PD, NY = 2 + PD;
+    static constexpr int NT = 3 + PD, NB = 2 + PD, NY = 2 + PD;
     float T[NT][PLANE];             // Y_{j-1} planes q-1, q, q+1 and those in flight
     float B[NB][3][PLANE];          // b planes q, q+1 and those in flight
     float Y[NY][3][TY * TX];        // Y0, Y_{j-2}, M(Y0) of plane q and those in flight
@@ -42,7 +44,7 @@ struct SmemT {
     float FxLo[2][TY];              // x-faces on the tile's left boundary
     alignas(8) unsigned long long bar[PD + 2];    // bundle barriers of the bulk-copy path
 };
-constexpr int kPD = 2;              // prefetch distance at 2 CTAs per SM (87 KB each)
+constexpr int kPD = 2;              // prefetch distance of the default build
 using Smem = SmemT<kPD>;
 
 // One problem of an ensemble as the persistent kernel sees it.
