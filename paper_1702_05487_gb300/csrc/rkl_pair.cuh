@@ -87,17 +87,21 @@ __device__ __forceinline__ float2 face2s(float2 TL, float2 TR, float2 gn, float2
         if (SP) return mul2(mul2(mul2(Ts, Ts), sqrt2(Ts)), X);
         return X;
     }
-    const float2 nk = SP ? mul2(mul2(bc2(k.nk), mul2(Ts, Ts)), sqrt2(Ts)) : bc2(k.nk);
+    const float2 sTs = sqrt2(Ts);
+    const float2 nk = SP ? mul2(mul2(bc2(k.nk), mul2(Ts, Ts)), sTs) : bc2(k.nk);
     float2 Fn = mul2(nk, X);
     const float2 F1 = mul2(nk, fma2(B1, bdg, mul2(bc2(k.kp4), g1)));
     const float2 F2 = mul2(nk, fma2(B2, bdg, mul2(bc2(k.kp4), g2)));
     const float2 Fmag = sqrt2(fma2(Fn, Fn, fma2(F1, F1, mul2(F2, F2))));
-    float2 Tq = mul2(bc2(0.5f), Ts);
+    float2 q;
     if (p.upwind) {
-        Tq.x = Fn.x >= 0.f ? TL.x : TR.x;
-        Tq.y = Fn.y >= 0.f ? TL.y : TR.y;
+        // c_iso^3 from the donor cell of the normal flux
+        const float2 Tq = make_float2(Fn.x >= 0.f ? TL.x : TR.x, Fn.y >= 0.f ? TL.y : TR.y);
+        q = mul2(mul2(bc2(p.q0), Tq), sqrt2(Tq));
+    } else {
+        // (Ts / 2)^1.5 = 2^-1.5 Ts sqrt(Ts), the square root shared with kappa
+        q = mul2(mul2(bc2(p.q0 * 0.35355339059327373f), Ts), sTs);
     }
-    const float2 q = mul2(mul2(bc2(p.q0), Tq), sqrt2(Tq));
     const float2 den = add2(q, Fmag);
     return make_float2(ddiv<float>(q.x, den.x) * Fn.x, ddiv<float>(q.y, den.y) * Fn.y);
 }
