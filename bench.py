@@ -231,7 +231,11 @@ def run_ours(args):
     b0 = torch.from_numpy(W.b.astype(npdt))
     T = T0.to(dev)
     b = b0.to(dev).contiguous()
-    plan = rk.Plan(W.T.shape, dtype, stream=stream, params=W.params)
+    params = dict(W.params)
+    if args.limiter != "none":
+        # Appendix C: MC-limited transverse gradients (generic kernel)
+        params.update(limiter=args.limiter, limiter_floor=float("inf"))
+    plan = rk.Plan(W.T.shape, dtype, stream=stream, params=params)
     if args.variant or args.nzchunk:
         plan.set_variant(args.variant, args.nzchunk)
     dt = W.ratio * plan.dt_expl(T)
@@ -295,7 +299,8 @@ def run_ours(args):
     avg_launch_ms = stage_ms / max(1, stage_launches)
     achieved = bytes_per_cs * ncell / (avg_launch_ms * 1e-3) / 1e9
     traffic = None
-    if args.workload == "tangled256" and MEASURED_TRAFFIC["source_hash"] == kernel_source_hash():
+    default_kernel = args.variant in (0, 3) and args.nzchunk == 0 and args.limiter == "none"
+    if args.workload == "tangled256" and default_kernel and MEASURED_TRAFFIC["source_hash"] == kernel_source_hash():
         traffic = MEASURED_TRAFFIC["bytes_per_launch"]
     cpu = None
     if world == 1 and not args.no_cpu_baseline and args.workload == "tangled256":
@@ -312,7 +317,7 @@ def run_ours(args):
                    "l2": ("inputs larger than L2: 8 grid arrays per stage" if ncell * 32 > 129e6
                           else "working set fits in L2"),
                    "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "kernel_variant": args.variant, "nzchunk": args.nzchunk},
+                   "kernel_variant": args.variant, "nzchunk": args.nzchunk, "limiter": args.limiter},
         "roofline": {"bound": "hbm", "kernel": "rkl2 stage", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_cs * ncell,
@@ -572,6 +577,8 @@ def main():
     ap.add_argument("--variant", type=int, default=0,
                     help="stage kernel: 0 auto, 1 generic, 2 tiled, 3/4 paired-cell at 5/6 CTAs per SM, 5 two-stage, 6 bulk copies")
     ap.add_argument("--nzchunk", type=int, default=0, help="planes per CTA (0 automatic, < 0 balanced runs)")
+    ap.add_argument("--limiter", default="none", choices=["none", "mc"],
+                    help="transverse gradients: plain averages, or MC-limited at every face (Appendix C)")
     ap.add_argument("--workload", default="tangled256",
                     choices=list(WORKLOADS) + ["ensemble64", "surrogate128", "split256"])
     ap.add_argument("--pairs", type=int, default=20000, help="training pairs of the surrogate workload")
