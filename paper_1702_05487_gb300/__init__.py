@@ -17,8 +17,8 @@ from ._lib import (  # noqa: F401  (the C ABI, same names)
     RKL_METHOD_STS, RKL_OK, RKL_PERIODIC, RklError, load, library_path, rkl_apply_M, rkl_coeffs,
     rkl_coeffs_method, rkl_dt_expl, rkl_energy, rkl_flux, rkl_grid, rkl_num_stages, rkl_num_stages_method,
     rkl_phys, rkl_plan_check, rkl_plan_create, rkl_plan_destroy, rkl_plan_set_method, rkl_plan_set_timing,
-    rkl_plan_set_variant, rkl_plan_timing, rkl_run_host, rkl_stage, rkl_super_step, rkl_super_step_s,
-    rkl_advect, rkl_dt_hyperbolic,
+    rkl_plan_set_variant, rkl_plan_timing, rkl_run_host, rkl_run_host_batch, rkl_stage, rkl_super_step,
+    rkl_super_step_s, rkl_advect, rkl_dt_hyperbolic,
 )
 
 __all__ = ["Plan", "make_grid", "make_phys", "RklError"]
@@ -139,6 +139,9 @@ class Plan:
 
     def run_host(self, dt, n_super, T_host, b_host):
         return rkl_run_host(self.handle, dt, n_super, T_host, b_host)
+
+    def run_host_batch(self, dt, n_super, T_hosts, b_hosts):
+        return rkl_run_host_batch(self.handle, dt, n_super, T_hosts, b_hosts)
 
 
 class Ensemble:

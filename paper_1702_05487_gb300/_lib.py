@@ -79,6 +79,8 @@ SIGNATURES = {
     "rkl_plan_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "rkl_plan_timing": (ctypes.c_int, [_vp, _dp, _i64p]),
     "rkl_run_host": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _vp, _vp, _ip]),
+    "rkl_run_host_batch": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(_vp), ctypes.POINTER(_vp), _ip]),
     "rkl_dt_expl_energy_noalloc": (ctypes.c_int, [ctypes.POINTER(rkl_grid), ctypes.POINTER(rkl_phys), _vp,
                                                   _vp, _dp, _dp]),
     "rkl_ensemble_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(rkl_grid), ctypes.POINTER(rkl_phys), _vp,
@@ -283,6 +285,19 @@ def rkl_run_host(plan, dt, n_super, T_host, b_host) -> int:
     _check(load().rkl_run_host(plan, float(dt), int(n_super), _ptr(T_host), _ptr(b_host),
                                ctypes.byref(s)), plan)
     return s.value
+
+
+def rkl_run_host_batch(plan, dt, n_super, T_hosts, b_hosts) -> list:
+    """Jobs (T_hosts[i], b_hosts[i]) streamed through the GPU with copies
+    overlapping compute; returns each job's last s."""
+    n = len(T_hosts)
+    if len(b_hosts) != n:
+        raise ValueError("one b array per T array")
+    Tp = (_vp * max(n, 1))(*[_ptr(t) for t in T_hosts])
+    bp = (_vp * max(n, 1))(*[_ptr(b) for b in b_hosts])
+    s = (ctypes.c_int * max(n, 1))()
+    _check(load().rkl_run_host_batch(plan, float(dt), int(n_super), n, Tp, bp, s), plan)
+    return list(s)[:n]
 
 
 def rkl_dt_expl_energy_noalloc(grid: rkl_grid, phys: rkl_phys, T, stream=None):

@@ -77,6 +77,12 @@ struct rkl_plan {
 
     void* host_T = nullptr;            // device staging for rkl_run_host
     void* host_b = nullptr;
+    // rkl_run_host_batch: a second staging set, copy-in / copy-out streams and
+    // the events that order them around the plan's stream
+    void* batch_T = nullptr;
+    void* batch_b = nullptr;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_in[2] = {}, ev_comp[2] = {}, ev_out[2] = {};
 
     std::string err;
 };
@@ -645,6 +651,17 @@ rkl_status rkl_plan_destroy(rkl_plan* p)
     for (int k = 0; k < 3; ++k) cudaFree(p->ybuf[k]);
     cudaFree(p->ybuf4);
     cudaFree(p->my0);
+    if (p->s_in) cudaStreamSynchronize(p->s_in);
+    if (p->s_out) cudaStreamSynchronize(p->s_out);
+    cudaFree(p->batch_T);
+    cudaFree(p->batch_b);
+    for (int k = 0; k < 2; ++k) {
+        if (p->ev_in[k]) cudaEventDestroy(p->ev_in[k]);
+        if (p->ev_comp[k]) cudaEventDestroy(p->ev_comp[k]);
+        if (p->ev_out[k]) cudaEventDestroy(p->ev_out[k]);
+    }
+    if (p->s_in) cudaStreamDestroy(p->s_in);
+    if (p->s_out) cudaStreamDestroy(p->s_out);
     cudaFree(p->d_partials);
     cudaFree(p->d_scal);
     if (p->h_scal) cudaFreeHost(p->h_scal);
@@ -981,6 +998,61 @@ rkl_status rkl_run_host(rkl_plan* p, double dt, int n_super, void* T_host, const
     RKL_CK(p, cudaMemcpyAsync(T_host, p->host_T, bytes, cudaMemcpyDeviceToHost, p->stream));
     RKL_CK(p, cudaStreamSynchronize(p->stream));
     if (s_last) *s_last = s;
+    return rkl_plan_check(p);
+}
+
+rkl_status rkl_run_host_batch(rkl_plan* p, double dt, int n_super, int n_jobs, void* const* T_host,
+                              const void* const* b_host, int* s_last)
+{
+    if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
+    if (!T_host || !b_host || n_super < 0 || n_jobs < 0) return fail(p, RKL_ERR_INVALID_ARG, "bad argument");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(p, RKL_ERR_INVALID_ARG, "dt must be finite and > 0");
+    for (int i = 0; i < n_jobs; ++i)
+        if (!T_host[i] || !b_host[i]) return fail(p, RKL_ERR_INVALID_ARG, "null host buffer");
+    DeviceGuard dg(p->device);
+    const size_t bytes = (size_t)p->ncell * p->esize, bbytes = bytes * p->grid.ndim;
+    if (!p->host_T) RKL_CK(p, cudaMalloc(&p->host_T, bytes));
+    if (!p->host_b) RKL_CK(p, cudaMalloc(&p->host_b, bbytes));
+    if (!p->batch_T) RKL_CK(p, cudaMalloc(&p->batch_T, bytes));
+    if (!p->batch_b) RKL_CK(p, cudaMalloc(&p->batch_b, bbytes));
+    if (!p->s_in) RKL_CK(p, cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking));
+    if (!p->s_out) RKL_CK(p, cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+        if (!p->ev_in[k]) RKL_CK(p, cudaEventCreateWithFlags(&p->ev_in[k], cudaEventDisableTiming));
+        if (!p->ev_comp[k]) RKL_CK(p, cudaEventCreateWithFlags(&p->ev_comp[k], cudaEventDisableTiming));
+        if (!p->ev_out[k]) RKL_CK(p, cudaEventCreateWithFlags(&p->ev_out[k], cudaEventDisableTiming));
+    }
+    void* dT[2] = {p->host_T, p->batch_T};
+    void* db[2] = {p->host_b, p->batch_b};
+    // work already queued on the plan's stream may still use the staging set
+    RKL_CK(p, cudaEventRecord(p->ev_comp[0], p->stream));
+    RKL_CK(p, cudaStreamWaitEvent(p->s_in, p->ev_comp[0], 0));
+    for (int i = 0; i < n_jobs; ++i) {
+        const int k = i & 1;
+        // copy-in of job i after the copy-out of job i - 2, which used the same set
+        if (i >= 2) RKL_CK(p, cudaStreamWaitEvent(p->s_in, p->ev_out[k], 0));
+        RKL_CK(p, cudaMemcpyAsync(dT[k], T_host[i], bytes, cudaMemcpyHostToDevice, p->s_in));
+        RKL_CK(p, cudaMemcpyAsync(db[k], b_host[i], bbytes, cudaMemcpyHostToDevice, p->s_in));
+        RKL_CK(p, cudaEventRecord(p->ev_in[k], p->s_in));
+        RKL_CK(p, cudaStreamWaitEvent(p->stream, p->ev_in[k], 0));
+        int s = 0;
+        for (int n = 0; n < n_super; ++n) {
+            rkl_status st = rkl_super_step(p, dt, dT[k], db[k], &s, nullptr, nullptr);
+            if (st != RKL_OK) {
+                cudaStreamSynchronize(p->s_in);
+                cudaStreamSynchronize(p->s_out);
+                return st;
+            }
+        }
+        RKL_CK(p, cudaEventRecord(p->ev_comp[k], p->stream));
+        RKL_CK(p, cudaStreamWaitEvent(p->s_out, p->ev_comp[k], 0));
+        RKL_CK(p, cudaMemcpyAsync(T_host[i], dT[k], bytes, cudaMemcpyDeviceToHost, p->s_out));
+        RKL_CK(p, cudaEventRecord(p->ev_out[k], p->s_out));
+        if (s_last) s_last[i] = s;
+    }
+    RKL_CK(p, cudaStreamSynchronize(p->s_out));
+    RKL_CK(p, cudaStreamSynchronize(p->s_in));
+    RKL_CK(p, cudaStreamSynchronize(p->stream));
     return rkl_plan_check(p);
 }
 
