@@ -386,7 +386,19 @@ __global__ void __launch_bounds__(256) stats_kernel(const R* __restrict__ T, int
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (sizeof(R) == 4 && (n & 3) == 0 && (reinterpret_cast<uintptr_t>(T) & 15) == 0) {
         const float4* T4 = reinterpret_cast<const float4*>(T);
-        for (int64_t c = t0; c < n / 4; c += stride) {
+        const int64_t n4 = n / 4;
+        int64_t c = t0;
+        // four independent 16-byte loads in flight per thread
+        for (; c + 3 * stride < n4; c += 4 * stride) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = T4[c + u * stride];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                fold((R)v[u].x); fold((R)v[u].y); fold((R)v[u].z); fold((R)v[u].w);
+            }
+        }
+        for (; c < n4; c += stride) {
             const float4 v = T4[c];
             fold((R)v.x); fold((R)v.y); fold((R)v.z); fold((R)v.w);
         }
