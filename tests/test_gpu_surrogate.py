@@ -237,3 +237,66 @@ def test_tcgen05_backend_matches_warp_mma_and_oracle(rk):
         print(f"tcgen05 backward layer {l}: dW rel-L2 {rl2:.3e} cos {cos:.6f}")
         assert rl2 < 1e-1 and cos > 0.995, l
     rk._lib.rkl_sur_destroy(sur)
+
+
+def test_trained_surrogate_gains_over_no_network(rk):
+    """What training buys, on held-out RKL2 pairs of 32^3 patches (tangled
+    fields of seeds the training pool does not contain, dt / dt_expl in
+    [50, 150]): the relative L2 error of the
+    predicted end-of-super-step state against the plain RKL2 super-step,
+    for the trained network, the same network before training, and no
+    network at all (T unchanged).  Also times one forward pass against one
+    RKL2 super-step on the same patch; the figures are printed."""
+    import torch
+    from paper_1702_05487_gb300.surrogate import Surrogate, SurrogateConfig
+    sur = Surrogate(SurrogateConfig(n=32, pool=6, seed0=700))
+
+    # held-out fields: seeds the training pool does not use
+    test_pool = []
+    for k in range(3):
+        T, bb = workloads.tangled_box(32, 32, 32, 900 + k)
+        test_pool.append((torch.from_numpy(T.astype(np.float32)).cuda(),
+                          torch.from_numpy(bb.astype(np.float32)).cuda()))
+
+    def heldout(n, seed):
+        rng_state, pool = sur.rng, sur.pool
+        sur.rng, sur.pool = np.random.default_rng(seed), test_pool
+        rows = []
+        for _ in range(n):
+            T0, b, kappa0, ratio, dt, target = sur.draw()
+            if sur.cfg.head_scale <= 0.0:
+                sur.cfg.head_scale = float(target.double().pow(2).mean().sqrt()) * sur.dx[0]
+            dT = sur.predict(T0, b, kappa0, ratio)
+            Tt = (T0 + target).double()
+            nrm = float(Tt.norm())
+            rows.append((float((dT - target).double().norm()) / nrm, float(target.double().norm()) / nrm))
+        sur.rng, sur.pool = rng_state, pool
+        return np.array(rows)
+
+    before = heldout(12, 99)
+    sur.train(600)
+    after = heldout(12, 99)
+    e_net, e_none, e_untrained = np.median(after[:, 0]), np.median(after[:, 1]), np.median(before[:, 0])
+    # time of one forward pass and one super-step at dt = 100 dt_expl
+    T0, b = sur.pool[0]
+    plan = sur.plan(0.01)
+    dt = 100.0 * plan.dt_expl(T0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    T1 = T0.clone()
+    plan.super_step(dt, T1, b)
+    sur.predict(T0, b, 0.01, 100.0)
+    torch.cuda.synchronize()
+    ev[0].record(sur.stream)
+    for _ in range(5):
+        plan.super_step(dt, T1, b)
+    ev[1].record(sur.stream)
+    for _ in range(5):
+        rk._lib.rkl_sur_forward(sur.handle, sur.cfg.head_scale)
+    ev[2].record(sur.stream)
+    torch.cuda.synchronize()
+    print(f"held-out state error (median): trained {e_net:.2e}, untrained {e_untrained:.2e}, "
+          f"no network {e_none:.2e}; 32^3 RKL2 super-step {ev[0].elapsed_time(ev[1]) / 5:.3f} ms, "
+          f"forward {ev[1].elapsed_time(ev[2]) / 5:.3f} ms")
+    assert e_net < 0.5 * e_none
+    assert e_net < 0.5 * e_untrained
+    sur.close()
