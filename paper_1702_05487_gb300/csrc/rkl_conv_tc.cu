@@ -16,12 +16,20 @@
 // is then a plain K-major no-swizzle matrix -- core matrix i (rows y = i,
 // x = 0..7) starts at voxel (dx, i + dy) of the halo plane and the next one
 // is one halo row (10 voxels) further.  The weights sit in shared memory
-// once per persistent CTA as [9][Cin/8][3 Cout][8].  Thread 0 issues the
-// MMAs of an input plane and commits them to an mbarrier; while they run,
-// four warps (one TMEM lane quarter each) drain the output plane that the
-// previous input plane completed (bias, ReLU or mask, BF16 or FP32 store)
-// and clear the columns the next one starts.  Every wait is bounded and
-// reports ST_TIMEOUT.
+// once per persistent CTA as [9][Cin/8][3 Cout][8].  The CTA is a
+// pipeline of three roles that meet only at mbarriers: three loader warps
+// stream input planes into the ring with cp.async, keeping two planes in
+// flight per thread; once a plane's copies have landed each loader fences
+// them into the tensor cores' (async) proxy and arrives on the slot's
+// "full" barrier.  Thread 0 issues the MMAs of a plane once it is full and
+// commits them to the slot's "empty" barrier (the loaders refill the slot
+// after it) and to the "done" barrier of the output plane they complete.
+// Four drain warps (one TMEM lane quarter each) wait for that, drain the
+// plane (bias, ReLU or mask, BF16 or FP32 store), zero its columns for the
+// next work item and arrive on its "freed" barrier, which the MMA thread
+// waits for before it starts that plane of the next item.  No CTA-wide
+// barrier per plane, and no proxy fence on the MMA thread's path.  Every
+// wait is bounded and reports ST_TIMEOUT.
 #include <cstdint>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -37,15 +45,15 @@ using x2::cp16;
 using x2::cp_commit;
 using x2::cp_wait;
 using x2::mbar_init;
-using x2::mbar_inval;
-using x2::mbar_wait;
+using x2::mbar_try_wait;
 using x2::smem_u32;
 
 constexpr int QX = 8, QY = 16;                 // output block of a plane: M = 128
 constexpr int HX = QX + 2, HY = QY + 2;         // halo plane
 constexpr int HP = HX * HY;                     // 180 voxels
-constexpr int NSLOT = 5;                        // input planes q-3 .. q+1 (and q+2 in flight)
-constexpr int NTHR_TC = 256;                    // warps 4-7 = the 4 TMEM lane quarters
+constexpr int NSLOT = 5;                        // input-plane ring
+constexpr int NTHR_TC = 256;                    // warp 0 MMA, warps 1-3 loads, warps 4-7 TMEM lane quarters
+constexpr int NLOAD = 96;                       // loader threads
 constexpr int NZC_TC = 6;                       // output planes per work item
 constexpr int TMEM_COLS = 256;                  // 32 (NZC_TC + 2) columns
 
@@ -53,7 +61,10 @@ template <int CIN, int COUT>
 struct TcSmem {
     __nv_bfloat16 W[9][CIN / 8][3 * COUT][8];   // B operands: per (dy, dx) the dz = +1, 0, -1 blocks
     __nv_bfloat16 A[NSLOT][CIN / 8][HP][8];     // A operands, one halo plane per slot
-    unsigned long long bar[2];                  // MMA completion of alternate input planes
+    unsigned long long full[NSLOT];             // slot's input plane landed (loader cp.async arrivals)
+    unsigned long long empty[NSLOT];            // MMAs reading the slot completed
+    unsigned long long done[NZC_TC];            // output plane r of the current item accumulated
+    unsigned long long freed[NZC_TC];           // output plane r drained and its columns zeroed
     unsigned tmem;                              // TMEM base column from tcgen05.alloc
 };
 
@@ -143,11 +154,15 @@ __device__ __forceinline__ void tmem_zero16(unsigned taddr)
 
 __device__ __forceinline__ int wrapi_tc(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
+__device__ __forceinline__ void mbar_arrive(unsigned bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
 // MODE 0: ReLU, bf16 out; 1: linear, f32 out; 2: no bias, times the ReLU
 // mask (mask > 0), bf16 out.  Persistent: work item = (8 x 16 column block,
-// chunk of NZC_TC output planes).  Roles: all threads stream input planes;
-// thread 0 issues the MMAs; warps 4-7 drain and clear TMEM (warp w: lane
-// quarter w - 4).
+// chunk of NZC_TC output planes); the items of a CTA ascend, so only its
+// last one can be short.
 template <int CIN, int COUT, int MODE>
 __global__ void __launch_bounds__(NTHR_TC, 1)
 conv_tc_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ wt,
@@ -159,10 +174,10 @@ conv_tc_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __rest
     S& sm = *reinterpret_cast<S*>(smem_raw);
     constexpr int NCH = CIN / 8;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool drainer = warp >= 4;
-    const int q4 = warp - 4;
     const int ncolx = W / QX, ncols = ncolx * (H / QY);
     const int nitems = ncols * ((D + NZC_TC - 1) / NZC_TC);
+    // output plane r (-1 <= r <= nz of an item) owns columns COUT (r + 1) ...
+    auto col_of = [](int r) { return (unsigned)(COUT * (r + 1)); };
 
     // weights [27][COUT][CIN] (o = (dz+1) 9 + (dy+1) 3 + dx+1) -> [9][CIN/8][3 COUT][8]
     // with block j of the N dimension holding dz = 1 - j
@@ -173,10 +188,6 @@ conv_tc_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __rest
         cp16(smem_u32(&sm.W[e][ch][jn][0]), wt + ((int64_t)o * COUT + n) * CIN + ch * 8);
     }
     cp_commit();
-    float bs[COUT];
-#pragma unroll
-    for (int c = 0; c < COUT; ++c) bs[c] = (MODE != 2 && drainer) ? bias[c] : 0.f;
-
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&sm.tmem)),
                      "r"(TMEM_COLS)
@@ -184,146 +195,200 @@ conv_tc_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __rest
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(smem_u32(&sm.bar[0]), 1u);
-        mbar_init(smem_u32(&sm.bar[1]), 1u);
+        for (int i = 0; i < NSLOT; ++i) {
+            mbar_init(smem_u32(&sm.full[i]), NLOAD);
+            mbar_init(smem_u32(&sm.empty[i]), 1u);
+        }
+        for (int i = 0; i < NZC_TC; ++i) {
+            mbar_init(smem_u32(&sm.done[i]), 1u);
+            mbar_init(smem_u32(&sm.freed[i]), 128u);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
+    cp_wait<0>();                                // the weights
+    fence_proxy_async();
     fence_before();
     __syncthreads();
     fence_after();
     const unsigned tbase = sm.tmem;
-    const unsigned id3 = idesc<3 * COUT>(), id1 = idesc<COUT>();
-    const uint64_t bdesc0 = sdesc(smem_u32(&sm.W[0][0][0][0]), 3 * COUT * 16, 8 * 16);
-    const unsigned tlane = tbase + ((unsigned)(q4 * 32) << 16);     // drainers' lane quarter
+    // Bounded waits without a back-off sleep (try_wait itself suspends the
+    // thread until the phase completes or a hardware time limit passes; a
+    // sleeping waiter would wake late and leave the tensor pipe idle).  A
+    // thread whose wait gave up skips its later waits, so a broken pipeline
+    // ends after one bounded wait per thread.
     bool ok = true;
-    unsigned g = 0;                              // input planes committed by this CTA (phase)
+    auto wait = [&](unsigned long long& bar, unsigned parity) {
+        if (!ok) return;
+        for (int it = 0; it < (1 << 24); ++it)
+            if (mbar_try_wait(smem_u32(&bar), parity)) return;
+        ok = false;
+    };
 
-    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const int col = item % ncols, chunk = item / ncols;
-        const int x0 = (col % ncolx) * QX, y0 = (col / ncolx) * QY, z0 = chunk * NZC_TC;
-        const int nz = min(NZC_TC, D - z0);
-        // output plane r (z0 + r, -1 <= r <= nz) owns columns COUT (r + 1) ...
-        auto col_of = [&](int r) { return (unsigned)(COUT * (r + 1)); };
-        // input plane q (z0 + q, periodic, -1 <= q <= nz) into its ring slot
-        auto load = [&](int q) {
-            const int gz = wrapi_tc(z0 + q, D);
-            const int sl = (q + 2 * NSLOT) % NSLOT;
-            for (int t = tid; t < HP * NCH; t += NTHR_TC) {
-                const int hv = t / NCH, ch = t % NCH;
-                const int gy = wrapi_tc(y0 + hv / HX - 1, H), gx = wrapi_tc(x0 + hv % HX - 1, W);
-                cp16(smem_u32(&sm.A[sl][ch][hv][0]), in + (((int64_t)gz * H + gy) * W + gx) * CIN + ch * 8);
+    if (warp == 0) {
+        // ---------------- MMA issue (one thread) ----------------
+        if (lane == 0) {
+            const unsigned id3 = idesc<3 * COUT>(), id1 = idesc<COUT>();
+            const uint64_t bdesc0 = sdesc(smem_u32(&sm.W[0][0][0][0]), 3 * COUT * 16, 8 * 16);
+            unsigned n = 0, k = 0;               // input planes and items of this CTA so far
+            for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++k) {
+                const int z0 = (item / ncols) * NZC_TC, nz = min(NZC_TC, D - z0);
+                for (int q = -1; q <= nz; ++q, ++n) {
+                    const unsigned sl = n % NSLOT;
+                    wait(sm.full[sl], (n / NSLOT) & 1u);
+                    // output plane q + 1 is first reached by input plane q: wait
+                    // until it is zeroed (phase k: the drain warps' initial pass,
+                    // then the drain of each previous item)
+                    if (q + 1 < nz) wait(sm.freed[q + 1], k & 1u);
+                    fence_after();
+                    const uint64_t ab = sdesc(smem_u32(&sm.A[sl][0][0][0]), HP * 16, HX * 16);
+                    if (q == -1 || q == nz) {
+                        // edge planes reach one output plane: dz = -1 (q = -1 -> r = 0)
+                        // or dz = +1 (q = nz -> r = nz - 1)
+                        const int j = q == -1 ? 2 : 0;
+                        const unsigned dt = tbase + col_of(q == -1 ? 0 : nz - 1);
+#pragma unroll
+                        for (int e = 0; e < 9; ++e)
+#pragma unroll
+                            for (int kk = 0; kk < CIN / 16; ++kk) {
+                                const uint64_t a =
+                                    ab + (uint64_t)((((e / 3) * HX + e % 3) * 16 + 2 * kk * HP * 16) >> 4);
+                                const uint64_t b =
+                                    bdesc0 + (uint64_t)((((e * NCH + 2 * kk) * 3 * COUT) + j * COUT) * 16 >> 4);
+                                mma_f16(dt, a, b, id1, (q == -1 && (e | kk) == 0) ? 0u : 1u);
+                            }
+                    } else {
+                        const unsigned dt = tbase + col_of(q - 1);
+#pragma unroll
+                        for (int e = 0; e < 9; ++e)
+#pragma unroll
+                            for (int kk = 0; kk < CIN / 16; ++kk) {
+                                const uint64_t a =
+                                    ab + (uint64_t)((((e / 3) * HX + e % 3) * 16 + 2 * kk * HP * 16) >> 4);
+                                const uint64_t b = bdesc0 + (uint64_t)(((e * NCH + 2 * kk) * 3 * COUT) * 16 >> 4);
+                                mma_f16(dt, a, b, id3, 1u);
+                            }
+                    }
+                    mma_commit(smem_u32(&sm.empty[sl]));
+                    if (q >= 1) mma_commit(smem_u32(&sm.done[q - 1]));   // output plane q - 1 complete
+                }
+                // planes a short item does not have: the same one phase per item
+                // of "freed" waited and of "done" completed, so that no role
+                // gets two phases ahead of another on any barrier
+                for (int r = nz; r < NZC_TC; ++r) {
+                    wait(sm.freed[r], k & 1u);
+                    mbar_arrive(smem_u32(&sm.done[r]));
+                }
             }
-        };
+        }
+    } else if (warp < 4) {
+        // ---------------- loads (warps 1-3) ----------------
+        const int lt = tid - 32;
+        unsigned n = 0;
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+            const int col = item % ncols, chunk = item / ncols;
+            const int x0 = (col % ncolx) * QX, y0 = (col / ncolx) * QY, z0 = chunk * NZC_TC;
+            const int nz = min(NZC_TC, D - z0);
+            for (int q = -1; q <= nz; ++q, ++n) {
+                const unsigned sl = n % NSLOT;
+                // the slot's previous plane (n - NSLOT) has been multiplied
+                if (n >= NSLOT) wait(sm.empty[sl], (n / NSLOT - 1) & 1u);
+                const int gz = wrapi_tc(z0 + q, D);
+                for (int t = lt; t < HP * NCH; t += NLOAD) {
+                    const int hv = t / NCH, ch = t % NCH;
+                    const int gy = wrapi_tc(y0 + hv / HX - 1, H), gx = wrapi_tc(x0 + hv % HX - 1, W);
+                    cp16(smem_u32(&sm.A[sl][ch][hv][0]), in + (((int64_t)gz * H + gy) * W + gx) * CIN + ch * 8);
+                }
+                cp_commit();
+                // the previous plane's copies have landed: make them visible to
+                // the tensor cores' proxy and report the slot full
+                if (n >= 1) {
+                    cp_wait<1>();
+                    fence_proxy_async();
+                    mbar_arrive(smem_u32(&sm.full[(n - 1) % NSLOT]));
+                }
+            }
+        }
+        cp_wait<0>();
+        if (n >= 1) {
+            fence_proxy_async();
+            mbar_arrive(smem_u32(&sm.full[(n - 1) % NSLOT]));
+        }
+    } else {
+        // ---------------- drain (warps 4-7, TMEM lane quarter warp - 4) ----------------
+        const int q4 = warp - 4;
+        const unsigned tlane = tbase + ((unsigned)(q4 * 32) << 16);
+        float bs[COUT];
+#pragma unroll
+        for (int c = 0; c < COUT; ++c) bs[c] = MODE != 2 ? bias[c] : 0.f;
         auto clear = [&](int r) {
             if (COUT == 32) tmem_zero32(tlane + col_of(r));
             else tmem_zero16(tlane + col_of(r));
         };
-        // drain output plane r once the MMAs of input plane r + 1 (commit k) are done
-        auto drain = [&](int r, unsigned k) {
-            if (!mbar_wait(smem_u32(&sm.bar[k & 1u]), (k >> 1) & 1u)) ok = false;
-            fence_after();
-            float v[COUT];
-            if (COUT == 32) tmem_ld32(tlane + col_of(r), v);
-            else tmem_ld16(tlane + col_of(r), v);
-            const int m = q4 * 32 + lane;         // TMEM lane = GEMM row = voxel of the block
-            const int64_t gv = ((int64_t)(z0 + r) * H + (y0 + m / QX)) * W + (x0 + m % QX);
-            if (MODE == 1) {
-                float* o = static_cast<float*>(out) + gv * COUT;
+        // output planes 1 .. are accumulated from their first MMA on: zero them
+        // for the first item (plane 0 starts with an overwriting MMA)
+        for (int r = 0; r < NZC_TC; ++r) {
+            if (r >= 1) clear(r);
+            fence_before();
+            mbar_arrive(smem_u32(&sm.freed[r]));
+        }
+        unsigned k = 0;
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++k) {
+            const int col = item % ncols, chunk = item / ncols;
+            const int x0 = (col % ncolx) * QX, y0 = (col / ncolx) * QY, z0 = chunk * NZC_TC;
+            const int nz = min(NZC_TC, D - z0);
+            for (int r = 0; r < NZC_TC; ++r) {
+                wait(sm.done[r], k & 1u);
+                if (r < nz) {
+                    fence_after();
+                    float v[COUT];
+                    if (COUT == 32) tmem_ld32(tlane + col_of(r), v);
+                    else tmem_ld16(tlane + col_of(r), v);
+                    const int m = q4 * 32 + lane;         // TMEM lane = GEMM row = voxel of the block
+                    const int64_t gv = ((int64_t)(z0 + r) * H + (y0 + m / QX)) * W + (x0 + m % QX);
+                    if (MODE == 1) {
+                        float* o = static_cast<float*>(out) + gv * COUT;
 #pragma unroll
-                for (int c = 0; c < COUT; c += 4)
-                    *reinterpret_cast<float4*>(o + c) =
-                        make_float4(v[c] + bs[c], v[c + 1] + bs[c + 1], v[c + 2] + bs[c + 2], v[c + 3] + bs[c + 3]);
-            } else {
-                __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out) + gv * COUT;
+                        for (int c = 0; c < COUT; c += 4)
+                            *reinterpret_cast<float4*>(o + c) = make_float4(v[c] + bs[c], v[c + 1] + bs[c + 1],
+                                                                            v[c + 2] + bs[c + 2], v[c + 3] + bs[c + 3]);
+                    } else {
+                        __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out) + gv * COUT;
 #pragma unroll
-                for (int c = 0; c < COUT; c += 8) {
-                    float w[8];
+                        for (int c = 0; c < COUT; c += 8) {
+                            float w[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) w[i] = MODE == 0 ? fmaxf(v[c + i] + bs[c + i], 0.f) : v[c + i];
-                    if (MODE == 2) {
-                        const uint4 mk = *reinterpret_cast<const uint4*>(mask + gv * COUT + c);
-                        const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk);
+                            for (int i = 0; i < 8; ++i) w[i] = MODE == 0 ? fmaxf(v[c + i] + bs[c + i], 0.f) : v[c + i];
+                            if (MODE == 2) {
+                                const uint4 mk = *reinterpret_cast<const uint4*>(mask + gv * COUT + c);
+                                const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk);
 #pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            if (!(__bfloat162float(mb[i]) > 0.f)) w[i] = 0.f;
+                                for (int i = 0; i < 8; ++i)
+                                    if (!(__bfloat162float(mb[i]) > 0.f)) w[i] = 0.f;
+                            }
+                            uint4 pk;
+                            __nv_bfloat162* ph = reinterpret_cast<__nv_bfloat162*>(&pk);
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) ph[i] = __floats2bfloat162_rn(w[2 * i], w[2 * i + 1]);
+                            *reinterpret_cast<uint4*>(o + c) = pk;
+                        }
                     }
-                    uint4 pk;
-                    __nv_bfloat162* ph = reinterpret_cast<__nv_bfloat162*>(&pk);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) ph[i] = __floats2bfloat162_rn(w[2 * i], w[2 * i + 1]);
-                    *reinterpret_cast<uint4*>(o + c) = pk;
                 }
-            }
-        };
-
-        load(-1);
-        cp_commit();
-        load(0);
-        cp_commit();
-        // output plane 1 is first reached by input plane 0 (accumulating)
-        if (drainer && nz >= 2) clear(1);
-        for (int q = -1; q <= nz; ++q) {
-            cp_wait<1>();                        // input plane q (and the weights) has landed; q + 1 may be in flight
-            fence_proxy_async();                 // generic-proxy writes -> tensor-core reads
-            fence_before();
-            __syncthreads();                     // also: cleared columns and drained planes are done
-            if (tid == 0) {
-                fence_after();
-                const uint64_t ab = sdesc(smem_u32(&sm.A[(q + 2 * NSLOT) % NSLOT][0][0][0]), HP * 16, HX * 16);
-                if (q == -1 || q == nz) {
-                    // edge planes reach one output plane: dz = -1 (q = -1 -> r = 0) or dz = +1 (q = nz -> r = nz - 1)
-                    const int j = q == -1 ? 2 : 0;
-                    const unsigned dt = tbase + col_of(q == -1 ? 0 : nz - 1);
-#pragma unroll
-                    for (int e = 0; e < 9; ++e)
-#pragma unroll
-                        for (int kk = 0; kk < CIN / 16; ++kk) {
-                            const uint64_t a = ab + (uint64_t)((((e / 3) * HX + e % 3) * 16 + 2 * kk * HP * 16) >> 4);
-                            const uint64_t b =
-                                bdesc0 + (uint64_t)((((e * NCH + 2 * kk) * 3 * COUT) + j * COUT) * 16 >> 4);
-                            mma_f16(dt, a, b, id1, (q == -1 && (e | kk) == 0) ? 0u : 1u);
-                        }
-                } else {
-                    const unsigned dt = tbase + col_of(q - 1);
-#pragma unroll
-                    for (int e = 0; e < 9; ++e)
-#pragma unroll
-                        for (int kk = 0; kk < CIN / 16; ++kk) {
-                            const uint64_t a = ab + (uint64_t)((((e / 3) * HX + e % 3) * 16 + 2 * kk * HP * 16) >> 4);
-                            const uint64_t b = bdesc0 + (uint64_t)(((e * NCH + 2 * kk) * 3 * COUT) * 16 >> 4);
-                            mma_f16(dt, a, b, id3, 1u);
-                        }
-                }
-                mma_commit(smem_u32(&sm.bar[g & 1u]));
-            }
-            // input plane q + 2 into the slot of plane q - 3, whose MMAs
-            // completed before the drain of the previous iteration
-            if (q + 2 <= nz) load(q + 2);
-            cp_commit();
-            if (drainer) {
-                // output plane q - 1 is complete once input plane q's MMAs are;
-                // drain r = q - 2 (input q - 1 done) and clear the columns that
-                // input plane q + 1 starts (r = q + 2)
-                if (q >= 1 && q - 2 >= 0) drain(q - 2, g - 1);
-                if (q + 2 <= nz - 1 && q + 2 >= 2) clear(q + 2);
+                // no later MMA of this item writes plane r's columns (for r >= nz
+                // all of them are done), so they can be zeroed for the next item
+                if (r >= 1) clear(r);
                 fence_before();
+                mbar_arrive(smem_u32(&sm.freed[r]));
             }
-            ++g;
         }
-        // the last output plane, complete with input plane nz
-        if (drainer) {
-            drain(nz - 1, g - 1);
-            fence_before();
-        }
-        __syncthreads();                         // ring slots and TMEM columns free for the next item
-        fence_after();
     }
-    if (warp == 0)
+    // every MMA has completed: the drain warps waited for the last plane's
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0) {
+        __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tbase), "r"(TMEM_COLS)
                      : "memory");
-    if (tid == 0) {
-        mbar_inval(smem_u32(&sm.bar[0]));
-        mbar_inval(smem_u32(&sm.bar[1]));
     }
     if (!ok && status) atomicOr(status, ST_TIMEOUT);
 }
