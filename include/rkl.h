@@ -79,7 +79,8 @@ typedef struct rkl_phys {
                                 of Appendix C, MC(MC(up_L, down_L),
                                 MC(up_R, down_R)), at faces whose lower
                                 temperature is below limiter_floor (generic
-                                kernel only)                                  */
+                                kernel, and the one-cell tiled kernel for 3D
+                                FP32; the paired-cell kernels decline it)     */
     double limiter_floor;    /* +inf limits every face (Section 3.4: limiters
                                 only where T falls below a floor)            */
 } rkl_phys;

@@ -310,8 +310,60 @@ __device__ __forceinline__ float face_y_smem(const Smem& sm, const KGrid<float>&
                                      0.5f * (Bz[off(iy, ix)] + Bz[off(iy + 1, ix)]), p);
 }
 
+// Transverse gradient of a face from the four one-sided differences at its
+// two cells (L, R) along axis e: their average, or where the limiter is on
+// (Appendix C) the MC limit of the MC limits taken at L and at R.
+__device__ __forceinline__ float tgrad(float TL, float TR, float Lp, float Lm, float Rp, float Rm, float inv_dx,
+                                       float inv_4dx, bool limit)
+{
+    if (limit) return mc_limit(mc_limit(Lp - TL, TL - Lm), mc_limit(Rp - TR, TR - Rm)) * inv_dx;
+    return (Lp + Rp - Lm - Rm) * inv_4dx;
+}
+
+// Face flux along DIR (0 x, 1 y, 2 z) between local cell (ix, iy) of plane
+// tc and its +DIR neighbour, every value straight from the smem ring, with
+// MC-limited transverse gradients at faces whose lower temperature is below
+// the floor.  tm / tp: T slots of the planes below / above tc; bc / bp: b
+// slots of plane tc and of the plane above (z-faces take b there).
+template <bool SP, bool SAT, int DIR>
+__device__ __forceinline__ float face_lim(const Smem& sm, const KGrid<float>& g, const KPhys<float>& p, int tm,
+                                          int tc, int tp, int bc, int bp, int ix, int iy)
+{
+    const float* T = sm.T[tc];
+    const int jx = DIR == 0 ? ix + 1 : ix, jy = DIR == 1 ? iy + 1 : iy;
+    const float* TRp = DIR == 2 ? sm.T[tp] : T;          // plane of the R cell
+    const float TL = T[off(iy, ix)], TR = TRp[off(jy, jx)];
+    const bool limit = p.limiter && fminf(TL, TR) < p.lfloor;
+    const float gn = (TR - TL) * g.inv_dx[DIR];
+    float g1, g2;
+    if (DIR == 0) {
+        g1 = tgrad(TL, TR, T[off(iy + 1, ix)], T[off(iy - 1, ix)], T[off(iy + 1, jx)], T[off(iy - 1, jx)],
+                   g.inv_dx[1], g.inv_4dx[1], limit);
+        g2 = tgrad(TL, TR, sm.T[tp][off(iy, ix)], sm.T[tm][off(iy, ix)], sm.T[tp][off(iy, jx)],
+                   sm.T[tm][off(iy, jx)], g.inv_dx[2], g.inv_4dx[2], limit);
+    } else if (DIR == 1) {
+        g1 = tgrad(TL, TR, T[off(iy, ix + 1)], T[off(iy, ix - 1)], T[off(jy, ix + 1)], T[off(jy, ix - 1)],
+                   g.inv_dx[0], g.inv_4dx[0], limit);
+        g2 = tgrad(TL, TR, sm.T[tp][off(iy, ix)], sm.T[tm][off(iy, ix)], sm.T[tp][off(jy, ix)],
+                   sm.T[tm][off(jy, ix)], g.inv_dx[2], g.inv_4dx[2], limit);
+    } else {
+        g1 = tgrad(TL, TR, T[off(iy, ix + 1)], T[off(iy, ix - 1)], TRp[off(iy, ix + 1)], TRp[off(iy, ix - 1)],
+                   g.inv_dx[0], g.inv_4dx[0], limit);
+        g2 = tgrad(TL, TR, T[off(iy + 1, ix)], T[off(iy - 1, ix)], TRp[off(iy + 1, ix)], TRp[off(iy - 1, ix)],
+                   g.inv_dx[1], g.inv_4dx[1], limit);
+    }
+    const int br = DIR == 2 ? bp : bc;
+    float bf[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) bf[e] = 0.5f * (sm.B[bc][e][off(iy, ix)] + sm.B[br][e][off(jy, jx)]);
+    // normal component first, then the transverse ones in axis order
+    const int t1 = DIR == 0 ? 1 : 0, t2 = DIR == 2 ? 1 : 2;
+    return face_flux<float, SP, SAT>(TL, TR, gn, g1, g2, bf[DIR], bf[t1], bf[t2], p);
+}
+
 // MODE 0: out = M(Tin); 1: stage 1 (MY0out = M, out = Y0 + mt M); 2: stage j.
-template <bool SP, bool SAT, int MODE>
+// LIM: slope-limited transverse gradients, every face from shared memory.
+template <bool SP, bool SAT, int MODE, bool LIM>
 __global__ void __launch_bounds__(NTHREADS, 3)
 stage_fast_kernel(KGrid<float> g, KPhys<float> p, FastArgs a, KCoef<float> cf, unsigned* status)
 {
@@ -371,10 +423,15 @@ stage_fast_kernel(KGrid<float> g, KPhys<float> p, FastArgs a, KCoef<float> cf, u
     PlaneQ prv = read_plane(sm, tslot(-1), bslot(-1), ix, iy);
     PlaneQ cur = read_plane(sm, tslot(0), bslot(0), ix, iy);
     // z-face between planes z0 - 1 and z0
-    float Fz_lo = face_flux<float, SP, SAT>(
-        prv.To, cur.To, (cur.To - prv.To) * g.inv_dx[2], (prv.gxo + cur.gxo) * g.inv_4dx[0],
-        (prv.gyo + cur.gyo) * g.inv_4dx[1], 0.5f * (prv.bo[2] + cur.bo[2]), 0.5f * (prv.bo[0] + cur.bo[0]),
-        0.5f * (prv.bo[1] + cur.bo[1]), p);
+    float Fz_lo;
+    if (LIM) {
+        Fz_lo = face_lim<SP, SAT, 2>(sm, g, p, 0, tslot(-1), tslot(0), bslot(-1), bslot(0), ix, iy);
+    } else {
+        Fz_lo = face_flux<float, SP, SAT>(
+            prv.To, cur.To, (cur.To - prv.To) * g.inv_dx[2], (prv.gxo + cur.gxo) * g.inv_4dx[0],
+            (prv.gyo + cur.gyo) * g.inv_4dx[1], 0.5f * (prv.bo[2] + cur.bo[2]), 0.5f * (prv.bo[0] + cur.bo[0]),
+            0.5f * (prv.bo[1] + cur.bo[1]), p);
+    }
     float TmO = prv.To, TmR = prv.TR, TmU = prv.TU;
 
     const bool inside = (i0 + ix < nx) && (j0 + iy < ny);
@@ -388,31 +445,43 @@ stage_fast_kernel(KGrid<float> g, KPhys<float> p, FastArgs a, KCoef<float> cf, u
         PlaneQ nxt = read_plane(sm, tslot(q + 1), bslot(q + 1), ix, iy);
         const float gzo = nxt.To - TmO, gzR = nxt.TR - TmR, gzU = nxt.TU - TmU;
 
-        // +x face
-        float Fx = face_flux<float, SP, SAT>(
-            cur.To, cur.TR, (cur.TR - cur.To) * g.inv_dx[0], (cur.gyo + cur.gyR) * g.inv_4dx[1],
-            (gzo + gzR) * g.inv_4dx[2], 0.5f * (cur.bo[0] + cur.bR[0]), 0.5f * (cur.bo[1] + cur.bR[1]),
-            0.5f * (cur.bo[2] + cur.bR[2]), p);
-        // +y face
-        float Fy = face_flux<float, SP, SAT>(
-            cur.To, cur.TU, (cur.TU - cur.To) * g.inv_dx[1], (cur.gxo + cur.gxU) * g.inv_4dx[0],
-            (gzo + gzU) * g.inv_4dx[2], 0.5f * (cur.bo[1] + cur.bU[1]), 0.5f * (cur.bo[0] + cur.bU[0]),
-            0.5f * (cur.bo[2] + cur.bU[2]), p);
-        // +z face
-        float Fz = face_flux<float, SP, SAT>(
-            cur.To, nxt.To, (nxt.To - cur.To) * g.inv_dx[2], (cur.gxo + nxt.gxo) * g.inv_4dx[0],
-            (cur.gyo + nxt.gyo) * g.inv_4dx[1], 0.5f * (cur.bo[2] + nxt.bo[2]), 0.5f * (cur.bo[0] + nxt.bo[0]),
-            0.5f * (cur.bo[1] + nxt.bo[1]), p);
+        float Fx, Fy, Fz;
+        if (LIM) {
+            const int tm = tslot(q - 1), tc = tslot(q), tp = tslot(q + 1), bc = bslot(q), bp = bslot(q + 1);
+            Fx = face_lim<SP, SAT, 0>(sm, g, p, tm, tc, tp, bc, bp, ix, iy);
+            Fy = face_lim<SP, SAT, 1>(sm, g, p, tm, tc, tp, bc, bp, ix, iy);
+            Fz = face_lim<SP, SAT, 2>(sm, g, p, tm, tc, tp, bc, bp, ix, iy);
+        } else {
+            // +x face
+            Fx = face_flux<float, SP, SAT>(
+                cur.To, cur.TR, (cur.TR - cur.To) * g.inv_dx[0], (cur.gyo + cur.gyR) * g.inv_4dx[1],
+                (gzo + gzR) * g.inv_4dx[2], 0.5f * (cur.bo[0] + cur.bR[0]), 0.5f * (cur.bo[1] + cur.bR[1]),
+                0.5f * (cur.bo[2] + cur.bR[2]), p);
+            // +y face
+            Fy = face_flux<float, SP, SAT>(
+                cur.To, cur.TU, (cur.TU - cur.To) * g.inv_dx[1], (cur.gxo + cur.gxU) * g.inv_4dx[0],
+                (gzo + gzU) * g.inv_4dx[2], 0.5f * (cur.bo[1] + cur.bU[1]), 0.5f * (cur.bo[0] + cur.bU[0]),
+                0.5f * (cur.bo[2] + cur.bU[2]), p);
+            // +z face
+            Fz = face_flux<float, SP, SAT>(
+                cur.To, nxt.To, (nxt.To - cur.To) * g.inv_dx[2], (cur.gxo + nxt.gxo) * g.inv_4dx[0],
+                (cur.gyo + nxt.gyo) * g.inv_4dx[1], 0.5f * (cur.bo[2] + nxt.bo[2]), 0.5f * (cur.bo[0] + nxt.bo[0]),
+                0.5f * (cur.bo[1] + nxt.bo[1]), p);
+        }
 
         const int par = q & 1;
         // faces on the tile's low boundary: y-face below row 0 (warp 0),
         // x-face left of column 0 (warp 1, one row per lane)
         if (iy == 0) {
-            sm.Fy[par][0][ix] = face_y_smem<SP, SAT>(sm, g, p, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q),
-                                                     ix, -1);
+            sm.Fy[par][0][ix] =
+                LIM ? face_lim<SP, SAT, 1>(sm, g, p, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), bslot(q + 1), ix,
+                                          -1)
+                    : face_y_smem<SP, SAT>(sm, g, p, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), ix, -1);
         } else if (iy == 1 && ix < TY) {
-            sm.Fx[par][ix][0] = face_x_smem<SP, SAT>(sm, g, p, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q),
-                                                     -1, ix);
+            sm.Fx[par][ix][0] =
+                LIM ? face_lim<SP, SAT, 0>(sm, g, p, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), bslot(q + 1), -1,
+                                          ix)
+                    : face_x_smem<SP, SAT>(sm, g, p, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), -1, ix);
         }
         float y0v = 0.f, yjm2v = 0.f, my0v = 0.f;
         if (MODE == 2) {
@@ -454,37 +523,45 @@ stage_fast_kernel(KGrid<float> g, KPhys<float> p, FastArgs a, KCoef<float> cf, u
     cp_wait<0>();
 }
 
-template <bool SP, bool SAT, int MODE>
+template <bool SP, bool SAT, int MODE, bool LIM>
 cudaError_t launch3(const KGrid<float>& g, const KPhys<float>& p, const FastArgs& a, const KCoef<float>& cf,
                     unsigned* status, cudaStream_t st)
 {
     static bool attr_set = false;
     const int smem = (int)sizeof(Smem);
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(stage_fast_kernel<SP, SAT, MODE>,
+        cudaError_t e = cudaFuncSetAttribute(stage_fast_kernel<SP, SAT, MODE, LIM>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + NZC - 1) / NZC);
-    stage_fast_kernel<SP, SAT, MODE><<<grid, NTHREADS, smem, st>>>(g, p, a, cf, status);
+    stage_fast_kernel<SP, SAT, MODE, LIM><<<grid, NTHREADS, smem, st>>>(g, p, a, cf, status);
     return cudaGetLastError();
 }
 
+template <bool SP, bool SAT, bool LIM>
+cudaError_t launch_lim(int mode, const KGrid<float>& g, const KPhys<float>& p, const FastArgs& a,
+                       const KCoef<float>& cf, unsigned* status, cudaStream_t st)
+{
+    if (mode == 0) return launch3<SP, SAT, 0, LIM>(g, p, a, cf, status, st);
+    if (mode == 1) return launch3<SP, SAT, 1, LIM>(g, p, a, cf, status, st);
+    return launch3<SP, SAT, 2, LIM>(g, p, a, cf, status, st);
+}
+
 template <bool SP, bool SAT>
-cudaError_t launch_mode(int mode, const KGrid<float>& g, const KPhys<float>& p, const FastArgs& a,
+cudaError_t launch_mode(bool limiter, int mode, const KGrid<float>& g, const KPhys<float>& p, const FastArgs& a,
                         const KCoef<float>& cf, unsigned* status, cudaStream_t st)
 {
-    if (mode == 0) return launch3<SP, SAT, 0>(g, p, a, cf, status, st);
-    if (mode == 1) return launch3<SP, SAT, 1>(g, p, a, cf, status, st);
-    return launch3<SP, SAT, 2>(g, p, a, cf, status, st);
+    if (limiter) return launch_lim<SP, SAT, true>(mode, g, p, a, cf, status, st);
+    return launch_lim<SP, SAT, false>(mode, g, p, a, cf, status, st);
 }
 
 }  // namespace
 
 bool fast_stage_supported(const LaunchCfg& c, const KGrid<float>& g)
 {
-    return c.dtype == 0 && c.ndim == 3 && !c.limiter && g.n[0] >= 1 && g.n[1] >= 1 && g.n[2] >= 1;
+    return c.dtype == 0 && c.ndim == 3 && g.n[0] >= 1 && g.n[1] >= 1 && g.n[2] >= 1;
 }
 
 cudaError_t launch_stage_fast(const LaunchCfg& c, const KGrid<float>& g, const KPhys<float>& p,
@@ -501,11 +578,11 @@ cudaError_t launch_stage_fast(const LaunchCfg& c, const KGrid<float>& g, const K
     a.coef_tab = static_cast<const float*>(io.coef_tab);
     a.j = io.j;
     if (c.spitzer) {
-        if (c.saturate) return launch_mode<true, true>(io.mode, g, p, a, coef, status, st);
-        return launch_mode<true, false>(io.mode, g, p, a, coef, status, st);
+        if (c.saturate) return launch_mode<true, true>(c.limiter, io.mode, g, p, a, coef, status, st);
+        return launch_mode<true, false>(c.limiter, io.mode, g, p, a, coef, status, st);
     }
-    if (c.saturate) return launch_mode<false, true>(io.mode, g, p, a, coef, status, st);
-    return launch_mode<false, false>(io.mode, g, p, a, coef, status, st);
+    if (c.saturate) return launch_mode<false, true>(c.limiter, io.mode, g, p, a, coef, status, st);
+    return launch_mode<false, false>(c.limiter, io.mode, g, p, a, coef, status, st);
 }
 
 }  // namespace rkl

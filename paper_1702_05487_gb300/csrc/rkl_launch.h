@@ -27,7 +27,7 @@ struct LaunchCfg {
     int ndim;
     int spitzer;
     int saturate;
-    int limiter;            // MC-limited transverse gradients: generic kernels only
+    int limiter;            // MC-limited transverse gradients: generic and tiled kernels
 };
 
 // Generic kernels: one thread per cell, any dtype / ndim / boundary.

@@ -41,7 +41,7 @@ def _cases():
         ("2d_f64_dirichlet", (41, 29), dict(kappa_par0=0.05, bc="dirichlet", bc_value=1.0), "f64"),
         ("2d_f32", (45, 67), spitz, "f32"),
         ("1d_f32", (300,), dict(kappa_par0=0.3, kappa_perp_ratio=1.0), "f32"),
-        # MC-limited transverse gradients (Appendix C; generic kernel)
+        # MC-limited transverse gradients (Appendix C; generic and tiled kernels)
         ("3d_limiter_mc", (20, 22, 24), dict(spitz, limiter="mc"), "f32"),
         ("3d_limiter_sat", (12, 16, 20), dict(kappa_model="spitzer", kappa_par0=0.01, saturate=True, phi=0.3,
                                                limiter="mc"), "f32"),
@@ -135,7 +135,7 @@ def _variant_cases():
     out = []
     for c in _cases():
         out.append(c + (0,))
-        if c[3] == "f32" and len(c[1]) == 3 and "limiter" not in c[2]:
+        if c[3] == "f32" and len(c[1]) == 3:
             out.append(c + (1,))        # the generic kernel on the same 3D FP32 case
             out.append(c + (2,))        # the tiled one-cell-per-thread kernel
     # grids with nx % 4 == 0 (the paired-cell kernel) and Dirichlet partial tiles
@@ -147,6 +147,11 @@ def _variant_cases():
         out.append(("3d_x4_sat", (18, 26, 68), sat, "f32", v))
         out.append(("3d_x4_sat_upwind", (10, 9, 132), dict(sat, phi=0.05, sat_upwind=True), "f32", v))
         out.append(("3d_x4_const", (33, 17, 44), dict(kappa_par0=0.02, kappa_perp_ratio=0.1), "f32", v))
+    # MC limiter on the tiled kernel: Dirichlet ghosts, a floor inside the
+    # temperature range (both branches per face), several 32 x 8 tiles
+    lim = dict(spitz, bc="dirichlet", bc_value=0.95, limiter="mc", limiter_floor=1.0)
+    for v in (0, 1, 2):
+        out.append(("3d_limiter_floor_dirichlet", (14, 18, 70), lim, "f32", v))
     # two-stage kernel: several 60 x 7 tiles with ragged edges in x, y and z
     out.append(("3d_pair_spitzer", (45, 30, 128), spitz, "f32", 5))
     out.append(("3d_pair_small", (5, 4, 8), spitz, "f32", 5))
