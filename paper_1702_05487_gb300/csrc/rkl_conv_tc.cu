@@ -61,7 +61,7 @@ template <int CIN, int COUT>
 struct TcSmem {
     __nv_bfloat16 W[9][CIN / 8][3 * COUT][8];   // B operands: per (dy, dx) the dz = +1, 0, -1 blocks
     __nv_bfloat16 A[NSLOT][CIN / 8][HP][8];     // A operands, one halo plane per slot
-    unsigned long long full[NSLOT];             // slot's input plane landed (loader cp.async arrivals)
+    unsigned long long full[NSLOT];             // slot's input plane landed and fenced (one arrival per loader)
     unsigned long long empty[NSLOT];            // MMAs reading the slot completed
     unsigned long long done[NZC_TC];            // output plane r of the current item accumulated
     unsigned long long freed[NZC_TC];           // output plane r drained and its columns zeroed
