@@ -300,3 +300,36 @@ def test_trained_surrogate_gains_over_no_network(rk):
     assert e_net < 0.5 * e_none
     assert e_net < 0.5 * e_untrained
     sur.close()
+
+
+@pytest.mark.parametrize("shape", [(64, 64, 64), (100, 64, 96)])
+def test_tcgen05_persistent_ctas_with_several_items(rk, shape):
+    """Grids with more work items (8 x 16 column blocks x 6-plane chunks)
+    than resident CTAs, so that CTAs run several items in a row (ending with
+    a short last chunk) and the pipeline's barriers go through many phases:
+    the tcgen05 forward and backward-data passes against the warp-level
+    mma.sync ones, layer by layer through the whole network, and the
+    increment's exact conservation."""
+    import torch
+    sur, params, T, b, Td, bd, dx = _setup(rk, shape=shape)
+    kappa0, ratio, hs = 0.01, 100.0, 2e-3
+    rk._lib.rkl_sur_features(sur, Td, bd, kappa0, True, ratio)
+    rng = np.random.default_rng(9)
+    target = torch_dev(rng.normal(scale=1e-3, size=shape))
+    out, grads = {}, {}
+    for backend in (0, 1):
+        rk._lib.rkl_sur_set_backend(sur, backend)
+        dT = torch.empty_like(Td)
+        rk._lib.rkl_sur_forward(sur, hs, dT)
+        rk._lib.rkl_sur_backward(sur, target)
+        rk._lib.rkl_sur_check(sur)
+        out[backend] = host(dT)
+        grads[backend] = [rk._lib.rkl_sur_get_grads(sur, l)[0] for l in range(6)]
+    rl2, cos = _stats(out[1], out[0])
+    print(f"{shape}: tcgen05 vs mma.sync forward rel-L2 {rl2:.3e}, cosine {cos:.6f}")
+    assert rl2 < 1e-2 and cos > 0.9999
+    assert abs(out[1].sum()) <= 1e-5 * np.abs(out[1]).sum()
+    for l in range(6):
+        rl2, cos = _stats(grads[1][l], grads[0][l])
+        assert rl2 < 2e-2 and cos > 0.9998, (l, rl2, cos)
+    rk._lib.rkl_sur_destroy(sur)
