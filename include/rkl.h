@@ -395,7 +395,7 @@ rkl_status rkl_ensemble_selftest_timeout(rkl_ensemble *ens, int *status_out);
 
 /* ------------------------------------------------------------------------
  * Learned surrogate of one super-step (no counterpart in the paper; the
- * RKL2 super-step above is its fallback and the judge of its error).
+ * RKL2 super-step above is its fallback and the reference for its error).
  * Network: 6 periodic 3x3x3 convolutions, channels 6 -> 32 -> 32 -> 32 ->
  * 32 -> 32 -> 3, ReLU between layers, BF16 weights and activations with
  * FP32 accumulation on tensor cores.  Inputs per cell: T - 1, b_x, b_y,
