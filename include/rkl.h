@@ -260,7 +260,10 @@ rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
  * j + 1 per pass over the grid, 60 x 7 tiles; periodic only; allocates a
  * fourth stage buffer), 6 = the paired-cell kernel with its plane bundles
  * copied by the TMA engine (cp.async.bulk rows with mbarrier completion;
- * periodic grids with nx >= 72, else as 3).  RKL_ERR_UNSUPPORTED if the kernel
+ * periodic grids with nx >= 72, else as 3), 7 = the paired-cell kernel with
+ * the Y0 / Y_{j-2} / M(Y0) bundles of stages j >= 2 copied by the TMA engine
+ * from tensor maps (cp.async.bulk.tensor, one issuing thread; as 3 where the
+ * driver offers no tensor-map encoder).  RKL_ERR_UNSUPPORTED if the kernel
  * does not apply to the grid.  nzchunk = planes per CTA of the paired-cell
  * kernels (0: chosen from the grid and the SM count, at least 3.5 waves of
  * CTAs where the grid has that many and a last wave that is nearly full); a

@@ -59,9 +59,13 @@ cudaError_t launch_stage_fast(const LaunchCfg& c, const KGrid<float>& g, const K
 // completion) instead of per-thread 16-byte cp.async.
 bool x2_stage_supported(const LaunchCfg& c, const KGrid<float>& g);
 bool x2_bulk_supported(const LaunchCfg& c, const KGrid<float>& g);
+// With ytma the Y0 / Y_{j-2} / M(Y0) bundles of stages j >= 2 are copied by
+// the TMA engine from tensor maps (cp.async.bulk.tensor, one thread, mbarrier
+// completion) instead of per-thread 16-byte copies.
+bool x2_ytma_supported(const LaunchCfg& c, const KGrid<float>& g);
 cudaError_t launch_stage_x2(const LaunchCfg& c, const KGrid<float>& g, const KPhys<float>& p, const StageIO& io,
                             const KCoef<float>& coef, unsigned* status, int nzchunk, int occupancy,
-                            cudaStream_t st, bool bulk = false);
+                            cudaStream_t st, bool bulk = false, bool ytma = false);
 
 // Two-stage paired-cell FP32 3D kernel: stages j (io, coefficients at
 // io.coef_tab[4 j]) and j + 1 (written to Yj1) in one pass, 60 x 7 tiles of

@@ -3,6 +3,8 @@
 // The tile body and the kernel template are in rkl_x2_tile.cuh.
 #include <algorithm>
 
+#include <cudaTypedefs.h>
+
 #include "rkl_x2_tile.cuh"
 
 namespace rkl {
@@ -11,11 +13,45 @@ namespace {
 
 template <int OCC, bool BULK>
 cudaError_t launch_phys(const LaunchCfg& c, int mode, const KGrid<float>& g, const KPhys<float>& p,
-                        const x2::FastArgs& a, const KCoef<float>& cf, unsigned* status, int nzchunk, cudaStream_t st)
+                        const x2::FastArgs& a, const KCoef<float>& cf, unsigned* status, int nzchunk, cudaStream_t st,
+                        const x2::YMaps* ym = nullptr)
 {
-    if (c.saturate) return launch_x2_sat(c.spitzer, OCC, BULK, mode, g, p, a, cf, status, nzchunk, st);
-    if (c.spitzer) return launch_mode<true, false, OCC, BULK>(mode, g, p, a, cf, status, nzchunk, st);
-    return launch_mode<false, false, OCC, BULK>(mode, g, p, a, cf, status, nzchunk, st);
+    if (c.saturate) return launch_x2_sat(c.spitzer, OCC, BULK, mode, g, p, a, cf, status, nzchunk, st, ym);
+    if (c.spitzer) return launch_mode<true, false, OCC, BULK>(mode, g, p, a, cf, status, nzchunk, st, ym);
+    return launch_mode<false, false, OCC, BULK>(mode, g, p, a, cf, status, nzchunk, st, ym);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); nullptr if the driver does not offer it.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
+}
+
+// Tensor map of one grid-sized FP32 array: dims (nx, ny, nz), boxes of one
+// tile's rows of one plane (TX x TY x 1); rows 16-byte multiples (nx % 4 == 0).
+bool encode_ymap(CUtensorMap* m, const void* base, const KGrid<float>& g)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || !base) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.n[0] * 4u, (cuuint64_t)g.n[0] * (cuuint64_t)g.n[1] * 4u};
+    const cuuint32_t box[3] = {(cuuint32_t)x2::TX, (cuuint32_t)x2::TY, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -28,6 +64,11 @@ bool x2_stage_supported(const LaunchCfg& c, const KGrid<float>& g)
 bool x2_bulk_supported(const LaunchCfg& c, const KGrid<float>& g)
 {
     return x2_stage_supported(c, g) && g.bc == 0 && g.n[0] >= x2::SXS;
+}
+
+bool x2_ytma_supported(const LaunchCfg& c, const KGrid<float>& g)
+{
+    return x2_stage_supported(c, g) && tensor_map_encoder() != nullptr;
 }
 
 // Planes per CTA when none is given: the chunk length in [16, 48] that
@@ -73,13 +114,20 @@ x2::FastArgs x2_args(const StageIO& io)
 
 cudaError_t launch_stage_x2(const LaunchCfg& c, const KGrid<float>& g, const KPhys<float>& p, const StageIO& io,
                             const KCoef<float>& coef, unsigned* status, int nzchunk, int occupancy, cudaStream_t st,
-                            bool bulk)
+                            bool bulk, bool ytma)
 {
     const x2::FastArgs a = x2_args(io);
     if (nzchunk == 0) nzchunk = auto_nzchunk(g, occupancy);
     else if (nzchunk < 0) nzchunk = 0;
     if (occupancy == 3) return launch_phys<3, false>(c, io.mode, g, p, a, coef, status, nzchunk, st);
     if (bulk && x2_bulk_supported(c, g)) return launch_phys<2, true>(c, io.mode, g, p, a, coef, status, nzchunk, st);
+    if (ytma && io.mode == 2 && x2_ytma_supported(c, g)) {
+        x2::YMaps ym;
+        if (!encode_ymap(&ym.m[0], io.Y0, g) || !encode_ymap(&ym.m[1], io.Yjm2, g) ||
+            !encode_ymap(&ym.m[2], io.MY0, g))
+            return cudaErrorInvalidValue;
+        return launch_phys<2, false>(c, io.mode, g, p, a, coef, status, nzchunk, st, &ym);
+    }
     return launch_phys<2, false>(c, io.mode, g, p, a, coef, status, nzchunk, st);
 }
 
@@ -107,7 +155,7 @@ __global__ void __launch_bounds__(x2::NTHREADS, x2::kCtasPerSm)
 ensemble_x2_kernel(const x2::EnsProb* __restrict__ probs, const x2::EnsSeg* __restrict__ segs, int nseg,
                    int total, int* work, unsigned* done, unsigned* status, int* abort_flag, long long spin_limit)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     x2::Smem& sm = *reinterpret_cast<x2::Smem*>(smem_raw);
     __shared__ int s_go, s_p, s_j, s_tile;
     for (;;) {

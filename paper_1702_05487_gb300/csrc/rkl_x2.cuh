@@ -2,6 +2,8 @@
 // kernel: tile geometry, kernel arguments and the shared-memory bundle ring.
 #pragma once
 
+#include <cuda.h>
+
 #include "rkl_device.cuh"
 
 namespace rkl {
@@ -39,10 +41,17 @@ struct SmemT {
     static constexpr int NT = 3 + PD, NB = 2 + PD, NY = 2 + PD;
     float T[NT][PLANE];             // Y_{j-1} planes q-1, q, q+1 and those in flight
     float B[NB][3][PLANE];          // b planes q, q+1 and those in flight
-    float Y[NY][3][TY * TX];        // Y0, Y_{j-2}, M(Y0) of plane q and those in flight
+    alignas(128) float Y[NY][3][TY * TX];   // Y0, Y_{j-2}, M(Y0) of plane q and those in flight
     float Fy[2][TY + 1][TX];        // y-face fluxes (row 0: the tile's lower boundary)
     float FxLo[2][TY];              // x-faces on the tile's left boundary
     alignas(8) unsigned long long bar[PD + 2];    // bundle barriers of the bulk-copy path
+    alignas(8) unsigned long long ybar[4];        // Y bundles copied by tensor maps (plane q: ybar[q & 3])
+};
+
+// Tensor maps of Y0, Y_{j-2} and M(Y0) (3D FP32, boxes of TX x TY x 1) for
+// the variant whose Y bundles the TMA engine copies (cp.async.bulk.tensor).
+struct YMaps {
+    CUtensorMap m[3];
 };
 constexpr int kPD = 2;              // prefetch distance of the default build
 using Smem = SmemT<kPD>;

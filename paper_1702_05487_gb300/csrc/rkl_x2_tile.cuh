@@ -298,10 +298,22 @@ __device__ __forceinline__ float low_xface(const SM& sm, const KGrid<float>& g, 
 // --------------------------------------------------------------------------
 // one tile: columns [i0, i0 + 64), rows [j0, j0 + 8), planes [z0, z0 + nzc)
 
-template <bool SP, bool SAT, int MODE, int PD, bool BULK = false>
+// TMA tensor copy of one box into shared memory, completing on an mbarrier
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map, int x, int y, int z, unsigned bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+// YT: the Y0 / Y_{j-2} / M(Y0) bundle of each plane is one tensor copy per
+// array issued by a single thread (ym: tensor maps in kernel-parameter space)
+// instead of per-thread 16-byte copies; plane q completes on ybar[q & 3].
+template <bool SP, bool SAT, int MODE, int PD, bool BULK = false, bool YT = false>
 __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g, const KPhys<float>& p,
                                         const x2::FastArgs& a, KCoef<float> cf, unsigned* status, int i0, int j0,
-                                        int z0, int nzc)
+                                        int z0, int nzc, const x2::YMaps* ym = nullptr)
 {
     using namespace x2;
     const int tid = threadIdx.x;
@@ -315,7 +327,8 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         cf.mu = t[0]; cf.nu = t[1]; cf.mt = t[2]; cf.gt = t[3];
     }
 
-    constexpr int kTk = BULK ? 1 : kSlots;
+    constexpr bool kYT = YT && MODE == 2 && !BULK;
+    constexpr int kTk = BULK ? 1 : (kYT ? kSlotY : kSlots);
     Task tk[kTk];
     RowTask rt{};
     if constexpr (BULK) {
@@ -327,7 +340,15 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         __syncthreads();
     } else {
 #pragma unroll
-        for (int s = 0; s < kSlots; ++s) tk[s] = make_task<MODE>(sm, g, a, s, tid, i0, j0);
+        for (int s = 0; s < kTk; ++s) tk[s] = make_task<MODE>(sm, g, a, s, tid, i0, j0);
+        if constexpr (kYT) {
+            if (tid == 0) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) mbar_init(smem_u32(&sm.ybar[i]), 1u);
+                asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+            }
+            __syncthreads();
+        }
     }
     // bundle q completes phase (q + 1) / (PD + 2) of barrier (q + 1) % (PD + 2)
     auto bar_of = [&](int q) { return smem_u32(&sm.bar[(q + 1) % (PD + 2)]); };
@@ -363,14 +384,25 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         } else if (plain) {
             // periodic: only the valid flag is set, so dst + off - 1 is the address
 #pragma unroll
-            for (int s = 0; s < kSlots; ++s) {
+            for (int s = 0; s < kTk; ++s) {
                 const unsigned off = (s == 0 ? ts : (s < kSlotY ? bs : ys)) - TK_VALID;
                 const bool on = (tk[s].dst & TK_VALID) && (s < kSlotY || withY);
                 if (on) cp16(tk[s].dst + off, tk[s].src + po.t);
             }
         } else {
 #pragma unroll
-            for (int s = 0; s < kSlots; ++s) issue(tk[s], s, po, s == 0 ? ts : (s < kSlotY ? bs : ys), withY, g.bcv);
+            for (int s = 0; s < kTk; ++s) issue(tk[s], s, po, s == 0 ? ts : (s < kSlotY ? bs : ys), withY, g.bcv);
+        }
+        if constexpr (kYT) {
+            // planes with Y lie inside the grid (0 <= z0 + q < nz): no wrap
+            if (withY && tid == 0) {
+                const unsigned bar = smem_u32(&sm.ybar[q & 3]);
+                mbar_expect_tx(bar, 3u * TY * TX * 4u);
+                const unsigned dst = smem_u32(&sm.Y[0][0][0]) + ys;
+#pragma unroll
+                for (int arr = 0; arr < 3; ++arr)
+                    tma_load_3d(dst + (unsigned)(arr * TY * TX * 4), &ym->m[arr], i0, j0, z0 + q, bar);
+            }
         }
     };
 
@@ -449,6 +481,16 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
     auto step = [&](int q, QZ& cur, QZ& nxt) {
         if constexpr (BULK) wait_bundle(q + 1);     // bundle q + 1 has landed
         else cp_wait<PD - 1>();
+        if constexpr (kYT) {
+            // plane q's Y bundle (read after the barrier); a polling wait,
+            // bounded, that records a timeout and lets the tile finish
+            if (tid == 0) {
+                const unsigned bar = smem_u32(&sm.ybar[q & 3]);
+                bool ok = false;
+                for (int it = 0; it < (1 << 24) && !ok; ++it) ok = mbar_try_wait(bar, (unsigned)((q >> 2) & 1));
+                if (!ok) atomicOr(status, ST_TIMEOUT);
+            }
+        }
         __syncthreads();
         // the slots of bundle q + PD + 1 held planes no thread reads any more
         if (q + PD + 1 <= nzc) load(q + PD + 1, q + PD + 1 < nzc);
@@ -525,6 +567,12 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
             for (int i = 0; i < PD + 2; ++i) mbar_inval(smem_u32(&sm.bar[i]));
         }
     }
+    if constexpr (kYT) {
+        if (tid == 0) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) mbar_inval(smem_u32(&sm.ybar[i]));
+        }
+    }
     if (MODE != 0) {
         const bool bad_nf = nfacc.x != 0.f || nfacc.y != 0.f;
         const bool bad_np = SP && !(mnacc > 0.f);
@@ -541,18 +589,19 @@ namespace {
 // BULK: bundles copied by the TMA engine (periodic grids with nx >= 72).
 constexpr int ctas_per_sm(int occ) { return occ == 2 ? x2::kCtasPerSm : 6; }
 
-template <bool SP, bool SAT, int MODE, int OCC, bool BULK>
+template <bool SP, bool SAT, int MODE, int OCC, bool BULK, bool YT = false>
 __global__ void __launch_bounds__(x2::NTHREADS, ctas_per_sm(OCC))
-stage_x2_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf, unsigned* status, int nzchunk)
+stage_x2_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf, unsigned* status, int nzchunk,
+                const __grid_constant__ x2::YMaps ym)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];     // tensor copies land 128-byte aligned
     constexpr int PD = OCC == 2 ? x2::kPD : 1;     // 3 CTAs per SM leave room for one plane in flight
     x2::SmemT<PD>& sm = *reinterpret_cast<x2::SmemT<PD>*>(smem_raw);
     if (nzchunk > 0) {
         // one tile column, one chunk of nzchunk planes per CTA
         const int z0 = blockIdx.z * nzchunk;
-        tile_x2<SP, SAT, MODE, PD, BULK>(sm, g, p, a, cf, status, blockIdx.x * x2::TX, blockIdx.y * x2::TY, z0,
-                                         min(nzchunk, g.n[2] - z0));
+        tile_x2<SP, SAT, MODE, PD, BULK, YT>(sm, g, p, a, cf, status, blockIdx.x * x2::TX, blockIdx.y * x2::TY,
+                                             z0, min(nzchunk, g.n[2] - z0), &ym);
         return;
     }
     // Balanced schedule: the column-planes (tile column, plane) in column-major
@@ -568,8 +617,8 @@ stage_x2_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf,
         const int64_t col = u / nz;
         const int z0 = (int)(u - col * nz);
         const int nzc = (int)min((int64_t)(nz - z0), u1 - u);
-        tile_x2<SP, SAT, MODE, PD, BULK>(sm, g, p, a, cf, status, (int)(col % ntx) * x2::TX,
-                                         (int)(col / ntx) * x2::TY, z0, nzc);
+        tile_x2<SP, SAT, MODE, PD, BULK, YT>(sm, g, p, a, cf, status, (int)(col % ntx) * x2::TX,
+                                             (int)(col / ntx) * x2::TY, z0, nzc, &ym);
         u += nzc;
     }
 }
@@ -586,15 +635,15 @@ int sm_count()
     return n;
 }
 
-template <bool SP, bool SAT, int MODE, int OCC, bool BULK>
+template <bool SP, bool SAT, int MODE, int OCC, bool BULK, bool YT = false>
 cudaError_t launch3(const KGrid<float>& g, const KPhys<float>& p, const x2::FastArgs& a, const KCoef<float>& cf,
-                    unsigned* status, int nzchunk, cudaStream_t st)
+                    unsigned* status, int nzchunk, cudaStream_t st, const x2::YMaps& ym)
 {
     constexpr int kCtasPerSm = ctas_per_sm(OCC);
     const int smem = (int)sizeof(x2::SmemT<OCC == 2 ? x2::kPD : 1>);
     static bool attr_set = false;       // the attribute is per function, set once
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(stage_x2_kernel<SP, SAT, MODE, OCC, BULK>,
+        cudaError_t e = cudaFuncSetAttribute(stage_x2_kernel<SP, SAT, MODE, OCC, BULK, YT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -607,17 +656,25 @@ cudaError_t launch3(const KGrid<float>& g, const KPhys<float>& p, const x2::Fast
         grid = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)kCtasPerSm * sm_count(), U / 8)), 1, 1);
         nzchunk = 0;
     }
-    stage_x2_kernel<SP, SAT, MODE, OCC, BULK><<<grid, x2::NTHREADS, smem, st>>>(g, p, a, cf, status, nzchunk);
+    stage_x2_kernel<SP, SAT, MODE, OCC, BULK, YT><<<grid, x2::NTHREADS, smem, st>>>(g, p, a, cf, status, nzchunk,
+                                                                               ym);
     return cudaGetLastError();
 }
 
+// ym: tensor maps of the Y arrays for the stages j >= 2 of the default
+// build (OCC 2, no bulk copies), or nullptr for per-thread Y copies.
 template <bool SP, bool SAT, int OCC, bool BULK>
 cudaError_t launch_mode(int mode, const KGrid<float>& g, const KPhys<float>& p, const x2::FastArgs& a,
-                        const KCoef<float>& cf, unsigned* status, int nzchunk, cudaStream_t st)
+                        const KCoef<float>& cf, unsigned* status, int nzchunk, cudaStream_t st,
+                        const x2::YMaps* ym = nullptr)
 {
-    if (mode == 0) return launch3<SP, SAT, 0, OCC, BULK>(g, p, a, cf, status, nzchunk, st);
-    if (mode == 1) return launch3<SP, SAT, 1, OCC, BULK>(g, p, a, cf, status, nzchunk, st);
-    return launch3<SP, SAT, 2, OCC, BULK>(g, p, a, cf, status, nzchunk, st);
+    static const x2::YMaps none{};
+    if (mode == 0) return launch3<SP, SAT, 0, OCC, BULK>(g, p, a, cf, status, nzchunk, st, none);
+    if (mode == 1) return launch3<SP, SAT, 1, OCC, BULK>(g, p, a, cf, status, nzchunk, st, none);
+    if constexpr (OCC == 2 && !BULK) {
+        if (ym) return launch3<SP, SAT, 2, OCC, BULK, true>(g, p, a, cf, status, nzchunk, st, *ym);
+    }
+    return launch3<SP, SAT, 2, OCC, BULK>(g, p, a, cf, status, nzchunk, st, none);
 }
 
 }  // namespace
@@ -625,6 +682,6 @@ cudaError_t launch_mode(int mode, const KGrid<float>& g, const KPhys<float>& p, 
 // The saturated-flux launches (rkl_x2_sat.cu).
 cudaError_t launch_x2_sat(bool spitzer, int occ, bool bulk, int mode, const KGrid<float>& g, const KPhys<float>& p,
                           const x2::FastArgs& a, const KCoef<float>& cf, unsigned* status, int nzchunk,
-                          cudaStream_t st);
+                          cudaStream_t st, const x2::YMaps* ym);
 
 }  // namespace rkl

@@ -141,7 +141,7 @@ def _variant_cases():
     # grids with nx % 4 == 0 (the paired-cell kernel) and Dirichlet partial tiles
     spitz = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
     sat = dict(kappa_model="spitzer", kappa_par0=0.01, saturate=True, phi=0.3)
-    for v in (2, 3, 4, 5, 6):
+    for v in (2, 3, 4, 5, 6, 7):
         if v not in (5, 6):     # the two-stage kernel and bulk copies are periodic only
             out.append(("3d_x4_dirichlet", (21, 19, 36), dict(spitz, bc="dirichlet", bc_value=0.9), "f32", v))
         out.append(("3d_x4_sat", (18, 26, 68), sat, "f32", v))
