@@ -285,8 +285,9 @@ rkl_status rkl_plan_set_method(rkl_plan *plan, int method, double sts_nu);
 /*
  * Autotuner: times one super-step of length dt (s from dt / dt_expl(T))
  * with every kernel variant and z-chunk that applies to the grid (generic;
- * tiled; paired-cell at 5 and 6 CTAs per SM, balanced or with 8, 16, 32, 64
- * planes per CTA) on a scratch copy of T (T is not changed), keeps the fastest with
+ * tiled; paired-cell at 5 and 6 CTAs per SM, automatic, balanced or with 16,
+ * 32, 64 planes per CTA; two-stage; bulk and tensor-map copies) on a
+ * scratch copy of T (T is not changed), keeps the fastest with
  * rkl_plan_set_variant and returns it.  Allocates and frees one grid-sized
  * scratch array.  Synchronises.
  */

@@ -876,6 +876,7 @@ rkl_status rkl_plan_autotune(rkl_plan* p, double dt, const void* T, const void* 
         for (int nz : {16, 32, 64}) cands.push_back({5, nz});
     if (p->x2ok && p->gf.bc == 0 && p->gf.n[0] >= 72)
         for (int nz : {0, 32}) cands.push_back({6, nz});
+        if (x2_ytma_supported(p->cfg, p->gf)) cands.push_back({7, 0});
     void* scratch = nullptr;
     RKL_CK(p, cudaMalloc(&scratch, (size_t)p->ncell * p->esize));
     cudaEvent_t a = nullptr, e = nullptr;
