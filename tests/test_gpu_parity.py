@@ -273,6 +273,26 @@ def test_run_host_matches_device_path(rk, orc):
     assert np.array_equal(Th, host(Td).astype(np.float32))
 
 
+def test_run_host_batch_edge_cases(rk):
+    """No jobs is a no-op; a null host buffer is an argument error raised
+    before any copy."""
+    import ctypes
+    shape = (8, 8, 16)
+    params = dict(kappa_model="spitzer", kappa_par0=0.01)
+    plan = rk.Plan(shape, "f32", params=params)
+    assert plan.run_host_batch(1e-3, 1, [], []) == []
+    T = np.ones(shape, dtype=np.float32)
+    b = np.zeros((3,) + shape, dtype=np.float32)
+    b[0] = 1.0
+    lib = rk._lib.load()
+    Tp = (ctypes.c_void_p * 2)(T.ctypes.data, None)
+    bp = (ctypes.c_void_p * 2)(b.ctypes.data, b.ctypes.data)
+    st = lib.rkl_run_host_batch(plan.handle, 1e-3, 1, 2, Tp, bp, None)
+    assert st == rk._lib.RKL_ERR_INVALID_ARG
+    assert np.all(T == 1.0)
+    assert plan.check() == 0
+
+
 @pytest.mark.parametrize("n_jobs", [1, 2, 5])
 def test_run_host_batch_matches_serial_and_oracle(rk, orc, n_jobs):
     """Jobs streamed with overlapping copies give, bit for bit, what one
