@@ -67,48 +67,114 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clock / throttle sampling during the timed region.
+
+    nvidia-smi writes to a pseudo-terminal, so that its C library flushes
+    every row as it is printed (a pipe may hold them until exit), and
+    every row carries nvidia-smi's own timestamp: the rows kept are those
+    stamped between the end of __enter__ and the start of __exit__.
+    Entering waits briefly for the first row so that sampling is under way
+    when the timed region starts.  If no row falls in the window (a region
+    shorter than the sampling period) the row closest to its end is kept and
+    the summary says so."""
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
+        self.lines = []
+        self.rows = []
+        self.nearest = False
+        self.window_ms = 0.0
+
+    def _read(self):
+        buf = b""
+        while True:
+            try:
+                chunk = os.read(self.master, 4096)
+            except OSError:          # EIO once the child has closed its side
+                break
+            if not chunk:
+                break
+            buf += chunk
+            *done, buf = buf.split(b"\n")
+            self.lines.extend(x.decode(errors="replace") for x in done)
+
+    @staticmethod
+    def _stamp(text):
+        import datetime
+        try:
+            return datetime.datetime.strptime(text.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
 
     def __enter__(self):
+        import threading
+        import pty
+        try:
+            self.master, slave = pty.openpty()
+        except OSError:              # no pseudo-terminals here: a pipe, rows may arrive late
+            self.master, slave = os.pipe()
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.PERIOD_MS)], stdin=subprocess.DEVNULL, stdout=slave, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            os.close(self.master)
+            return self
+        finally:
+            os.close(slave)
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+        t_end = time.monotonic() + 2.0
+        while not self.lines and time.monotonic() < t_end and self.proc.poll() is None:
+            time.sleep(0.005)
+        self.t0 = time.time()
         return self
 
     def __exit__(self, *a):
-        self.rows = []
         if self.proc is None:
             return
+        t1 = time.time()
+        self.window_ms = 1e3 * (t1 - self.t0)
+        time.sleep(2e-3 * self.PERIOD_MS)          # the row that closes the window
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-            out = ""
-        for line in out.splitlines():
+            self.proc.wait(timeout=5)
+        self.reader.join(timeout=5)
+        os.close(self.master)
+        parsed = []
+        for line in self.lines:
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                self.rows.append(parts)
+            t = self._stamp(parts[0]) if len(parts) >= 10 else None
+            if t is not None:
+                parsed.append((t, parts[1:]))
+        self.rows = [r for t, r in parsed if self.t0 <= t <= t1]
+        if not self.rows and parsed:
+            self.rows = [min(parsed, key=lambda tr: abs(tr[0] - t1))[1]]
+            self.nearest = True
 
     def summary(self):
-        if not getattr(self, "rows", None):
+        if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        # row: index, clocks.sm, clocks.max.sm, power.draw, active mask, then the four reasons
         sm = [float(r[1]) for r in self.rows if r[1].replace(".", "", 1).isdigit()]
         mx = [float(r[2]) for r in self.rows if r[2].replace(".", "", 1).isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({n for r in self.rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+        reasons = sorted({n for r in self.rows for n, v in zip(self.REASONS, r[5:9]) if v.lower() == "active"})
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+               "reasons": reasons, "samples": len(self.rows), "period_ms": self.PERIOD_MS,
+               "window_ms": round(self.window_ms, 1)}
+        if self.nearest:
+            out["note"] = "region shorter than the sampling period: the nearest sample"
+        return out
 
 
 def dist_env():
@@ -136,12 +202,13 @@ def make_inputs(name="tangled256"):
     return workloads.ring(100)
 
 
-def cpu_oracle_sample(W, target_seconds: float = 12.0):
+def cpu_oracle_sample(W, target_seconds: float = 12.0, size: int | None = None):
     """Time the FP64 oracle on a bounded sample of the workload: for a 3D
     grid one super-step of s stages on a (nz_w, ny, nx) window of it
     (periodic in z), nz_w doubled until the run takes about a quarter of
     target_seconds; for a 2D grid whole super-steps of the full grid,
-    repeated likewise.  Returns (dict, seconds of the last timed run)."""
+    repeated likewise.  A given size (nz_w, or the repeat count) skips the
+    search.  Returns (dict, seconds of the last timed run, size)."""
     import oracle
     from oracle import Problem
     P = Problem(W.T.shape, **W.params)
@@ -150,7 +217,7 @@ def cpu_oracle_sample(W, target_seconds: float = 12.0):
     threads = oracle.set_threads(0)
     if W.T.ndim == 3:
         nz_full, ny, nx = W.T.shape
-        nz = 4
+        nz = min(nz_full, size) if size else 4
         while True:
             Tw = np.ascontiguousarray(W.T[:nz])
             bw = np.ascontiguousarray(W.b[:, :nz])
@@ -158,28 +225,28 @@ def cpu_oracle_sample(W, target_seconds: float = 12.0):
             t0 = time.perf_counter()
             oracle.super_step(Pw, Tw, bw, dt, s)
             el = time.perf_counter() - t0
-            if el >= target_seconds / 4 or nz >= nz_full:
+            if size or el >= target_seconds / 4 or nz >= nz_full:
                 break
             nz = min(nz_full, nz * 2)
         cells = Tw.size * s
         sample = (f"one {s}-stage super-step of a {nz}x{ny}x{nx} window of the {W.name} workload "
                   f"(periodic in z), FP64, {el:.1f} s wall")
     else:
-        reps = 1
+        reps = size or 1
         while True:
             T = W.T.copy()
             t0 = time.perf_counter()
             for _ in range(reps):
                 T, _ = oracle.super_step(P, T, W.b, dt, s)
             el = time.perf_counter() - t0
-            if el >= target_seconds / 4:
+            if size or el >= target_seconds / 4:
                 break
             reps *= 2
         cells = W.T.size * s * reps
         sample = (f"{reps} {s}-stage super-steps of the whole {'x'.join(map(str, W.T.shape))} {W.name} grid, "
                   f"FP64, {el:.1f} s wall")
     return {"value": cells / el / 1e9, "unit": "Gcell-stage/s", "cores": threads, "kind": "oracle",
-            "sample": sample}, el
+            "sample": sample}, el, (nz if W.T.ndim == 3 else reps)
 
 
 def run_reference(args):
@@ -189,8 +256,12 @@ def run_reference(args):
     W = make_inputs()
     res = None
     times = []
+    # the sample size is chosen in the first warm-up step (about a minute in
+    # all), then every step runs that same sample
+    size = None
     for k in range(args.warmup + args.steps):
-        r, el = cpu_oracle_sample(W, target_seconds=max(2.0, 60.0 / max(1, args.steps + args.warmup)))
+        r, el, size = cpu_oracle_sample(W, target_seconds=max(0.5, 60.0 / max(1, args.steps + args.warmup)),
+                                        size=size)
         if k >= args.warmup:
             times.append(el)
             res = r
@@ -335,7 +406,7 @@ def run_ours(args):
         traffic = MEASURED_TRAFFIC["bytes_per_launch"]
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu, _ = cpu_oracle_sample(W)
+        cpu, _, _ = cpu_oracle_sample(W)
     s_last = s_used[-1] if s_used else rk.rkl_num_stages(W.ratio)
     line = {
         "metric": "Gcell-stage/s per RKL2 stage", "value": value, "unit": "Gcell-stage/s",
@@ -602,7 +673,7 @@ def run_surrogate(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
