@@ -57,13 +57,23 @@ __device__ __forceinline__ float2 face2(float2 TL, float2 TR, float2 gn, float2 
 // not the average) and Ts = T_L + T_R, the flux of Eq. qN is
 //   F = -kappa_par(Ts / 2) / 4 * (Bn (B . g) + 4 (kappa_perp / kappa_par) gn),
 // so the halves of the face averages and the whole prefactor become one
-// constant per launch.  Without saturation face2s returns F / fscale and the
-// divergence absorbs fscale; with saturation the blend needs |F|, so it
-// returns F itself and fscale = 1.
+// constant per launch, and face2s returns F / fscale (the divergence absorbs
+// fscale).
+//
+// Saturation (Eq. qsat) blends F with q = q0 (Ts / 2)^1.5 as F q / (q + |F|).
+// Write F = nk Ts^2.5 V_n (Spitzer; nk Ts^0 for a constant kappa) with
+// V = (X, Y1, Y2) the bracket above for the three flux components.  When q
+// is taken at the face temperature, Ts^1.5 cancels between q and |F|:
+//   F_sat / nk = Ts^2.5 X / (1 + s Ts |V|)              (Spitzer)
+//   F_sat / nk = Ts^1.5 X / (Ts^1.5 + s |V|)            (constant kappa)
+// with s = -nk / (q0 2^-1.5), so the blend costs |V| and one division and
+// no separate q.  The upwind choice of q (the donor cell's temperature)
+// does not cancel; that form returns F itself and fscale = 1.
 struct FaceK {
     float nk;         // -kappa_par0 / 4 (x 2^-2.5 under Spitzer: (Ts / 2)^2.5)
     float kp4;        // 4 kappa_perp / kappa_par
     float fscale;     // true flux = fscale x returned value
+    float sat;        // s above (saturation at the face temperature)
 };
 
 template <bool SP, bool SAT>
@@ -72,7 +82,8 @@ __device__ __forceinline__ FaceK face_consts(const KPhys<float>& p)
     FaceK k;
     k.nk = -0.25f * p.kappa0 * (SP ? 0.17677669529663688f : 1.f);    // 2^-2.5
     k.kp4 = 4.f * p.kperp;
-    k.fscale = SAT ? 1.f : k.nk;
+    k.fscale = (SAT && p.upwind) ? 1.f : k.nk;
+    k.sat = SAT ? -k.nk / (p.q0 * 0.35355339059327373f) : 0.f;       // 2^-1.5
     return k;
 }
 
@@ -88,20 +99,31 @@ __device__ __forceinline__ float2 face2s(float2 TL, float2 TR, float2 gn, float2
         return X;
     }
     const float2 sTs = sqrt2(Ts);
-    const float2 nk = SP ? mul2(mul2(bc2(k.nk), mul2(Ts, Ts)), sTs) : bc2(k.nk);
-    float2 Fn = mul2(nk, X);
-    const float2 F1 = mul2(nk, fma2(B1, bdg, mul2(bc2(k.kp4), g1)));
-    const float2 F2 = mul2(nk, fma2(B2, bdg, mul2(bc2(k.kp4), g2)));
-    const float2 Fmag = sqrt2(fma2(Fn, Fn, fma2(F1, F1, mul2(F2, F2))));
-    float2 q;
-    if (p.upwind) {
-        // c_iso^3 from the donor cell of the normal flux
-        const float2 Tq = make_float2(Fn.x >= 0.f ? TL.x : TR.x, Fn.y >= 0.f ? TL.y : TR.y);
-        q = mul2(mul2(bc2(p.q0), Tq), sqrt2(Tq));
-    } else {
-        // (Ts / 2)^1.5 = 2^-1.5 Ts sqrt(Ts), the square root shared with kappa
-        q = mul2(mul2(bc2(p.q0 * 0.35355339059327373f), Ts), sTs);
+    // |V|^2, one transverse component at a time
+    float2 V2 = mul2(X, X);
+    const float2 Y1 = fma2(B1, bdg, mul2(bc2(k.kp4), g1));
+    V2 = fma2(Y1, Y1, V2);
+    const float2 Y2 = fma2(B2, bdg, mul2(bc2(k.kp4), g2));
+    V2 = fma2(Y2, Y2, V2);
+    if (!p.upwind) {
+        const float2 Vm = sqrt2(V2);
+        float2 num, den;
+        if (SP) {
+            num = mul2(mul2(mul2(Ts, Ts), sTs), X);
+            den = fma2(bc2(k.sat), mul2(Ts, Vm), bc2(1.f));
+        } else {
+            const float2 T15 = mul2(Ts, sTs);
+            num = mul2(T15, X);
+            den = fma2(bc2(k.sat), Vm, T15);
+        }
+        return make_float2(ddiv<float>(num.x, den.x), ddiv<float>(num.y, den.y));
     }
+    // upwind: F itself, blended with c_iso^3 from the donor cell of the normal flux
+    const float2 nk = SP ? mul2(mul2(bc2(k.nk), mul2(Ts, Ts)), sTs) : bc2(k.nk);
+    const float2 Fn = mul2(nk, X);
+    const float2 Fmag = mul2(make_float2(fabsf(nk.x), fabsf(nk.y)), sqrt2(V2));
+    const float2 Tq = make_float2(Fn.x >= 0.f ? TL.x : TR.x, Fn.y >= 0.f ? TL.y : TR.y);
+    const float2 q = mul2(mul2(bc2(p.q0), Tq), sqrt2(Tq));
     const float2 den = add2(q, Fmag);
     return make_float2(ddiv<float>(q.x, den.x) * Fn.x, ddiv<float>(q.y, den.y) * Fn.y);
 }

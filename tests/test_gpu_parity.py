@@ -36,6 +36,9 @@ def _cases():
                                             phi=0.3), "f32"),
         ("3d_saturated_upwind", (20, 18, 35), dict(kappa_model="spitzer", kappa_par0=0.01,
                                                    saturate=True, phi=0.05, sat_upwind=True), "f32"),
+        # constant kappa with saturation (the paired-cell kernel: nx % 4 == 0)
+        ("3d_saturated_const", (16, 20, 48), dict(kappa_par0=0.02, kappa_perp_ratio=0.1, saturate=True,
+                                                  phi=0.003), "f32"),
         ("3d_dirichlet", (19, 21, 34), dict(spitz, bc="dirichlet", bc_value=0.9), "f32"),
         ("3d_f64", (13, 15, 17), spitz, "f64"),
         ("2d_f64_dirichlet", (41, 29), dict(kappa_par0=0.05, bc="dirichlet", bc_value=1.0), "f64"),
