@@ -79,8 +79,9 @@ typedef struct rkl_phys {
                                 of Appendix C, MC(MC(up_L, down_L),
                                 MC(up_R, down_R)), at faces whose lower
                                 temperature is below limiter_floor (generic
-                                kernel, and the one-cell tiled kernel for 3D
-                                FP32; the paired-cell kernels decline it)     */
+                                kernel and the one-cell tiled kernel; the
+                                paired-cell kernel for 3D FP32 with the floor
+                                at +inf only)                                 */
     double limiter_floor;    /* +inf limits every face (Section 3.4: limiters
                                 only where T falls below a floor)            */
 } rkl_phys;
@@ -263,8 +264,11 @@ rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
  * periodic grids with nx >= 72, else as 3), 7 = the paired-cell kernel with
  * the Y0 / Y_{j-2} / M(Y0) bundles of stages j >= 2 copied by the TMA engine
  * from tensor maps (cp.async.bulk.tensor, one issuing thread; as 3 where the
- * driver offers no tensor-map encoder).  RKL_ERR_UNSUPPORTED if the kernel
- * does not apply to the grid.  nzchunk = planes per CTA of the paired-cell
+ * driver offers no tensor-map encoder).  With the MC limiter at every face
+ * (limiter_floor = +inf) variants 3, 4, 6 and 7 all launch the paired-cell
+ * kernel's limited build (16 resident warps per SM, per-thread copies);
+ * with a finite floor the paired-cell variants do not apply.
+ * RKL_ERR_UNSUPPORTED if the kernel does not apply to the grid.  nzchunk = planes per CTA of the paired-cell
  * kernels (0: chosen from the grid and the SM count, at least 3.5 waves of
  * CTAs where the grid has that many and a last wave that is nearly full); a
  * negative value selects the balanced schedule instead: one launch of 5 (or

@@ -578,7 +578,8 @@ rkl_status rkl_plan_create(const rkl_grid* grid, const rkl_phys* phys, void* cud
     p->esize = g.dtype == RKL_F64 ? 8 : 4;
     p->ncell = ncell;
     p->cfg = LaunchCfg{g.dtype, g.ndim, ph.kappa_model == RKL_KAPPA_SPITZER, ph.saturate != 0,
-                       ph.limiter == RKL_LIMITER_MC};
+                       ph.limiter == RKL_LIMITER_MC,
+                       ph.limiter == RKL_LIMITER_MC && std::isinf(ph.limiter_floor) && ph.limiter_floor > 0};
     auto fill = [&](auto& kg, auto& kp) {
         using R = std::remove_reference_t<decltype(kg.bcv)>;
         for (int d = 0; d < 3; ++d) {
@@ -867,16 +868,18 @@ rkl_status rkl_plan_autotune(rkl_plan* p, double dt, const void* T, const void* 
     struct Cand { int v, nz; };
     std::vector<Cand> cands = {{1, 0}};
     if (p->fast) cands.push_back({2, 0});
+    // a limiter plan has one paired-cell build (variants 3-7 all launch it)
+    const bool lim = p->cfg.limiter != 0;
     if (p->x2ok)
         for (int nz : {0, -1, 16, 32, 64}) {
             cands.push_back({3, nz});
-            cands.push_back({4, nz});
+            if (!lim) cands.push_back({4, nz});
         }
     if (p->x2ok && p->pairok)
         for (int nz : {16, 32, 64}) cands.push_back({5, nz});
-    if (p->x2ok && p->gf.bc == 0 && p->gf.n[0] >= 72)
+    if (p->x2ok && !lim && p->gf.bc == 0 && p->gf.n[0] >= 72)
         for (int nz : {0, 32}) cands.push_back({6, nz});
-        if (x2_ytma_supported(p->cfg, p->gf)) cands.push_back({7, 0});
+    if (p->x2ok && !lim && x2_ytma_supported(p->cfg, p->gf)) cands.push_back({7, 0});
     void* scratch = nullptr;
     RKL_CK(p, cudaMalloc(&scratch, (size_t)p->ncell * p->esize));
     cudaEvent_t a = nullptr, e = nullptr;

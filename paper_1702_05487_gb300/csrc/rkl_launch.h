@@ -27,7 +27,8 @@ struct LaunchCfg {
     int ndim;
     int spitzer;
     int saturate;
-    int limiter;            // MC-limited transverse gradients: generic and tiled kernels
+    int limiter;            // MC-limited transverse gradients (generic, tiled and paired-cell kernels)
+    int lim_all;            // the limiter at every face (floor +inf): the paired-cell kernel's only form
 };
 
 // Generic kernels: one thread per cell, any dtype / ndim / boundary.
@@ -57,6 +58,8 @@ cudaError_t launch_stage_fast(const LaunchCfg& c, const KGrid<float>& g, const K
 // With bulk (and a periodic grid with nx >= 72) the plane bundles are
 // copied by the TMA engine (cp.async.bulk, one row per copy, mbarrier
 // completion) instead of per-thread 16-byte cp.async.
+// A limiter plan (floor +inf only) always takes the MC-limited build (four
+// CTAs per SM, per-thread copies), whatever occupancy, bulk and ytma say.
 bool x2_stage_supported(const LaunchCfg& c, const KGrid<float>& g);
 bool x2_bulk_supported(const LaunchCfg& c, const KGrid<float>& g);
 // With ytma the Y0 / Y_{j-2} / M(Y0) bundles of stages j >= 2 are copied by

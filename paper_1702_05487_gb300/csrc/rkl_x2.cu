@@ -58,7 +58,7 @@ bool encode_ymap(CUtensorMap* m, const void* base, const KGrid<float>& g)
 
 bool x2_stage_supported(const LaunchCfg& c, const KGrid<float>& g)
 {
-    return c.dtype == 0 && c.ndim == 3 && !c.limiter && (g.n[0] % 4) == 0;
+    return c.dtype == 0 && c.ndim == 3 && (!c.limiter || c.lim_all) && (g.n[0] % 4) == 0;
 }
 
 bool x2_bulk_supported(const LaunchCfg& c, const KGrid<float>& g)
@@ -117,6 +117,12 @@ cudaError_t launch_stage_x2(const LaunchCfg& c, const KGrid<float>& g, const KPh
                             bool bulk, bool ytma)
 {
     const x2::FastArgs a = x2_args(io);
+    if (c.limiter) {
+        // the MC-limited build, whatever the variant asked for
+        if (nzchunk == 0) nzchunk = auto_nzchunk(g, 4);
+        else if (nzchunk < 0) nzchunk = 0;
+        return launch_x2_lim(c.spitzer, c.saturate, io.mode, g, p, a, coef, status, nzchunk, st);
+    }
     if (nzchunk == 0) nzchunk = auto_nzchunk(g, occupancy);
     else if (nzchunk < 0) nzchunk = 0;
     if (occupancy == 3) return launch_phys<3, false>(c, io.mode, g, p, a, coef, status, nzchunk, st);

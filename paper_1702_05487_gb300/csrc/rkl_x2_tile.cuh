@@ -16,6 +16,13 @@
 //
 // The per-tile body (tile_x2) is also the work item of the persistent
 // ensemble kernel (rkl_ensemble.cu).
+//
+// LIM: MC-limited transverse gradients at every face (Appendix C, the
+// limiter floor at +inf).  The per-cell quantities that the unlimited form
+// carries as centred differences T+ - T- become the cells' limited slopes
+// MC(T+ - T0, T0 - T-), and a face takes MC of its two cells' slopes / dx
+// instead of their sum / (4 dx): the same four one-sided differences per
+// transverse direction, each cell's pair limited once per plane.
 #pragma once
 
 #include <algorithm>
@@ -31,6 +38,30 @@ namespace x2 {
 // shared memory and copies
 
 __device__ __forceinline__ int off(int r, int c) { return (r + 1) * SXS + c + 4; }
+
+// Per-cell transverse slope along one axis from the cell (T0) and its two
+// neighbours: the centred difference T+ - T- (unscaled), or with LIM the
+// limited slope MC(T+ - T0, T0 - T-).
+template <bool LIM>
+__device__ __forceinline__ float2 cslope(float2 Tp, float2 T0, float2 Tm)
+{
+    if (!LIM) return sub2(Tp, Tm);
+    const float2 up = sub2(Tp, T0), dn = sub2(T0, Tm);
+    return make_float2(mc_limit<float>(up.x, dn.x), mc_limit<float>(up.y, dn.y));
+}
+template <bool LIM>
+__device__ __forceinline__ float cslope1(float Tp, float T0, float Tm)
+{
+    return LIM ? mc_limit<float>(Tp - T0, T0 - Tm) : Tp - Tm;
+}
+// Transverse gradient at a face from its two cells' slopes: their sum
+// times 1 / (4 dx) (i4), or with LIM their MC limit times 1 / dx (i1).
+template <bool LIM>
+__device__ __forceinline__ float2 fgrad(float2 sL, float2 sR, float2 i4, float2 i1)
+{
+    if (!LIM) return mul2(add2(sL, sR), i4);
+    return mul2(make_float2(mc_limit<float>(sL.x, sR.x), mc_limit<float>(sL.y, sR.y)), i1);
+}
 
 // Copy tasks fixed per thread for the whole tile, grouped by ring so that a
 // thread's slot s always feeds the same ring (its slot offset is known at
@@ -194,25 +225,25 @@ __device__ __forceinline__ void issue(const Task& k, int s, const PlaneOff& po, 
 
 // Quantities carried from one plane to the next (needed by the z-face and
 // the z-differences): T of the pair, of column 2l+2 and one row up, the
-// pair's centred x/y differences (unscaled) and b.
+// pair's x/y slopes (cslope) and b.
 struct QZ {
     float2 To;        // T at columns (2l, 2l+1)
     float Tr;         // T at column 2l+2
     float2 TU;        // T one row up
-    float2 gxo, gyo;  // centred differences at the pair
+    float2 gxo, gyo;  // x / y slopes at the pair
     float2 bo[3];     // b at the pair
 };
 
 // Quantities of the current plane needed only by its x- and y-faces
 // (read at the start of the plane's step, not carried).
 struct QXY {
-    float2 gyR;       // centred y-differences at (2l+1, 2l+2)
-    float2 gxU;       // centred x-differences one row up
+    float2 gyR;       // y slopes at (2l+1, 2l+2)
+    float2 gxU;       // x slopes one row up
     float bR[3];      // b at column 2l+2
     float2 bU[3];     // b one row up
 };
 
-template <class SM>
+template <bool LIM, class SM>
 __device__ __forceinline__ QZ read_qz(const SM& sm, int ts, int bs, int c, int r)
 {
     const float* T = sm.T[ts];
@@ -225,14 +256,14 @@ __device__ __forceinline__ QZ read_qz(const SM& sm, int ts, int bs, int c, int r
     q.To = Tc;
     q.Tr = Trr.x;
     q.TU = Tu;
-    q.gxo = sub2(make_float2(Tc.y, Trr.x), make_float2(Tl.y, Tc.x));
-    q.gyo = sub2(Tu, Td);
+    q.gxo = cslope<LIM>(make_float2(Tc.y, Trr.x), Tc, make_float2(Tl.y, Tc.x));
+    q.gyo = cslope<LIM>(Tu, Tc, Td);
 #pragma unroll
     for (int e = 0; e < 3; ++e) q.bo[e] = lds2(&sm.B[bs][e][off(r, c)]);
     return q;
 }
 
-template <class SM>
+template <bool LIM, class SM>
 __device__ __forceinline__ QXY read_qxy(const SM& sm, int ts, int bs, int c, int r, const QZ& z)
 {
     const float* T = sm.T[ts];
@@ -241,8 +272,8 @@ __device__ __forceinline__ QXY read_qxy(const SM& sm, int ts, int bs, int c, int
     const float2 Tur = lds2(&T[off(r + 1, c + 2)]);
     const float2 Tdr = lds2(&T[off(r - 1, c + 2)]);
     const float2 Tul = lds2(&T[off(r + 1, c - 2)]);
-    q.gyR = sub2(make_float2(z.TU.y, Tur.x), make_float2(Td.y, Tdr.x));
-    q.gxU = sub2(make_float2(z.TU.y, Tur.x), make_float2(Tul.y, z.TU.x));
+    q.gyR = cslope<LIM>(make_float2(z.TU.y, Tur.x), make_float2(z.To.y, z.Tr), make_float2(Td.y, Tdr.x));
+    q.gxU = cslope<LIM>(make_float2(z.TU.y, Tur.x), z.TU, make_float2(Tul.y, z.TU.x));
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
         const float* B = sm.B[bs][e];
@@ -255,7 +286,7 @@ __device__ __forceinline__ QXY read_qxy(const SM& sm, int ts, int bs, int c, int
 // Boundary faces of the tile, straight from smem: the y-face pair between
 // row -1 and row 0 at columns (c, c+1), and the x-face between columns -1
 // and 0 at row r.
-template <bool SP, bool SAT, class SM>
+template <bool SP, bool SAT, bool LIM, class SM>
 __device__ __forceinline__ float2 low_yface2(const SM& sm, const KGrid<float>& g, const KPhys<float>& p,
                                              const FaceK& fk, int tm, int tc, int tp, int bs, int c)
 {
@@ -263,33 +294,36 @@ __device__ __forceinline__ float2 low_yface2(const SM& sm, const KGrid<float>& g
     const float2 TL = lds2(&T[off(-1, c)]), TR = lds2(&T[off(0, c)]);
     const float2 Ll = lds2(&T[off(-1, c - 2)]), Lr = lds2(&T[off(-1, c + 2)]);
     const float2 Rl = lds2(&T[off(0, c - 2)]), Rr = lds2(&T[off(0, c + 2)]);
-    const float2 gxL = sub2(make_float2(TL.y, Lr.x), make_float2(Ll.y, TL.x));
-    const float2 gxR = sub2(make_float2(TR.y, Rr.x), make_float2(Rl.y, TR.x));
-    const float2 gzL = sub2(lds2(&sm.T[tp][off(-1, c)]), lds2(&sm.T[tm][off(-1, c)]));
-    const float2 gzR = sub2(lds2(&sm.T[tp][off(0, c)]), lds2(&sm.T[tm][off(0, c)]));
+    const float2 gxL = cslope<LIM>(make_float2(TL.y, Lr.x), TL, make_float2(Ll.y, TL.x));
+    const float2 gxR = cslope<LIM>(make_float2(TR.y, Rr.x), TR, make_float2(Rl.y, TR.x));
+    const float2 gzL = cslope<LIM>(lds2(&sm.T[tp][off(-1, c)]), TL, lds2(&sm.T[tm][off(-1, c)]));
+    const float2 gzR = cslope<LIM>(lds2(&sm.T[tp][off(0, c)]), TR, lds2(&sm.T[tm][off(0, c)]));
     float2 b[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) b[e] = add2(lds2(&sm.B[bs][e][off(-1, c)]), lds2(&sm.B[bs][e][off(0, c)]));
-    return face2s<SP, SAT>(TL, TR, mul2(sub2(TR, TL), bc2(g.inv_dx[1])), mul2(add2(gxL, gxR), bc2(g.inv_4dx[0])),
-                           mul2(add2(gzL, gzR), bc2(g.inv_4dx[2])), b[1], b[0], b[2], fk, p);
+    return face2s<SP, SAT>(TL, TR, mul2(sub2(TR, TL), bc2(g.inv_dx[1])),
+                           fgrad<LIM>(gxL, gxR, bc2(g.inv_4dx[0]), bc2(g.inv_dx[0])),
+                           fgrad<LIM>(gzL, gzR, bc2(g.inv_4dx[2]), bc2(g.inv_dx[2])), b[1], b[0], b[2], fk, p);
 }
 
-template <bool SP, bool SAT, class SM>
+template <bool SP, bool SAT, bool LIM, class SM>
 __device__ __forceinline__ float low_xface(const SM& sm, const KGrid<float>& g, const KPhys<float>& p,
                                            const FaceK& fk, int tm, int tc, int tp, int bs, int r)
 {
     const float* T = sm.T[tc];
     const float TL = T[off(r, -1)], TR = T[off(r, 0)];
-    const float gyL = T[off(r + 1, -1)] - T[off(r - 1, -1)];
-    const float gyR = T[off(r + 1, 0)] - T[off(r - 1, 0)];
-    const float gzL = sm.T[tp][off(r, -1)] - sm.T[tm][off(r, -1)];
-    const float gzR = sm.T[tp][off(r, 0)] - sm.T[tm][off(r, 0)];
+    const float gyL = cslope1<LIM>(T[off(r + 1, -1)], TL, T[off(r - 1, -1)]);
+    const float gyR = cslope1<LIM>(T[off(r + 1, 0)], TR, T[off(r - 1, 0)]);
+    const float gzL = cslope1<LIM>(sm.T[tp][off(r, -1)], TL, sm.T[tm][off(r, -1)]);
+    const float gzR = cslope1<LIM>(sm.T[tp][off(r, 0)], TR, sm.T[tm][off(r, 0)]);
+    const float gy = LIM ? mc_limit<float>(gyL, gyR) * g.inv_dx[1] : (gyL + gyR) * g.inv_4dx[1];
+    const float gz = LIM ? mc_limit<float>(gzL, gzR) * g.inv_dx[2] : (gzL + gzR) * g.inv_4dx[2];
     float b[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) b[e] = sm.B[bs][e][off(r, -1)] + sm.B[bs][e][off(r, 0)];
     // the packed form on a duplicated scalar costs what the scalar form does
-    return face2s<SP, SAT>(bc2(TL), bc2(TR), bc2((TR - TL) * g.inv_dx[0]), bc2((gyL + gyR) * g.inv_4dx[1]),
-                           bc2((gzL + gzR) * g.inv_4dx[2]), bc2(b[0]), bc2(b[1]), bc2(b[2]), fk, p)
+    return face2s<SP, SAT>(bc2(TL), bc2(TR), bc2((TR - TL) * g.inv_dx[0]), bc2(gy), bc2(gz), bc2(b[0]), bc2(b[1]),
+                           bc2(b[2]), fk, p)
         .x;
 }
 
@@ -310,7 +344,7 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map
 // YT: the Y0 / Y_{j-2} / M(Y0) bundle of each plane is one tensor copy per
 // array issued by a single thread (ym: tensor maps in kernel-parameter space)
 // instead of per-thread 16-byte copies; plane q completes on ybar[q & 3].
-template <bool SP, bool SAT, int MODE, int PD, bool BULK = false, bool YT = false>
+template <bool SP, bool SAT, int MODE, int PD, bool BULK = false, bool YT = false, bool LIM = false>
 __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g, const KPhys<float>& p,
                                         const x2::FastArgs& a, KCoef<float> cf, unsigned* status, int i0, int j0,
                                         int z0, int nzc, const x2::YMaps* ym = nullptr)
@@ -429,11 +463,11 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
     const float2 cmx = bc2(-fk.fscale * g.inv_dx[0]), cmy = bc2(-fk.fscale * g.inv_dx[1]);
     const float2 cmz = bc2(-fk.fscale * g.inv_dx[2]);
 
-    QZ A = read_qz(sm, tslot(-1), bslot(-1), c, r);
-    QZ B = read_qz(sm, tslot(0), bslot(0), c, r);
-    float2 Fz_lo = face2s<SP, SAT>(A.To, B.To, mul2(sub2(B.To, A.To), idz2), mul2(add2(A.gxo, B.gxo), i4x),
-                                   mul2(add2(A.gyo, B.gyo), i4y), add2(A.bo[2], B.bo[2]), add2(A.bo[0], B.bo[0]),
-                                   add2(A.bo[1], B.bo[1]), fk, p);
+    QZ A = read_qz<LIM>(sm, tslot(-1), bslot(-1), c, r);
+    QZ B = read_qz<LIM>(sm, tslot(0), bslot(0), c, r);
+    float2 Fz_lo = face2s<SP, SAT>(A.To, B.To, mul2(sub2(B.To, A.To), idz2), fgrad<LIM>(A.gxo, B.gxo, i4x, idx2),
+                                   fgrad<LIM>(A.gyo, B.gyo, i4y, idy2), add2(A.bo[2], B.bo[2]),
+                                   add2(A.bo[0], B.bo[0]), add2(A.bo[1], B.bo[1]), fk, p);
     float2 TmO = A.To, TmU = A.TU;
     float TmR = A.Tr;
 
@@ -498,27 +532,29 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         if (q > 0) finish(q - 1);
 
         const float2 TmRp = make_float2(TmO.y, TmR);
-        const QXY cx = read_qxy(sm, tslot(q), bslot(q), c, r, cur);
-        nxt = read_qz(sm, tslot(q + 1), bslot(q + 1), c, r);
-        const float2 gzo = sub2(nxt.To, TmO);
-        const float2 TRn = make_float2(nxt.To.y, nxt.Tr);
-        const float2 gzR = sub2(TRn, TmRp);
-        const float2 gzU = sub2(nxt.TU, TmU);
+        const QXY cx = read_qxy<LIM>(sm, tslot(q), bslot(q), c, r, cur);
+        nxt = read_qz<LIM>(sm, tslot(q + 1), bslot(q + 1), c, r);
         const float2 TR = make_float2(cur.To.y, cur.Tr);
+        const float2 gzo = cslope<LIM>(nxt.To, cur.To, TmO);
+        const float2 TRn = make_float2(nxt.To.y, nxt.Tr);
+        const float2 gzR = cslope<LIM>(TRn, TR, TmRp);
+        const float2 gzU = cslope<LIM>(nxt.TU, cur.TU, TmU);
 
         // +x faces of the pair
         const float2 Fx = face2s<SP, SAT>(
-            cur.To, TR, mul2(sub2(TR, cur.To), idx2), mul2(add2(cur.gyo, cx.gyR), i4y), mul2(add2(gzo, gzR), i4z),
+            cur.To, TR, mul2(sub2(TR, cur.To), idx2), fgrad<LIM>(cur.gyo, cx.gyR, i4y, idy2),
+            fgrad<LIM>(gzo, gzR, i4z, idz2),
             add2(cur.bo[0], make_float2(cur.bo[0].y, cx.bR[0])), add2(cur.bo[1], make_float2(cur.bo[1].y, cx.bR[1])),
             add2(cur.bo[2], make_float2(cur.bo[2].y, cx.bR[2])), fk, p);
         // +y faces
         const float2 Fy = face2s<SP, SAT>(cur.To, cur.TU, mul2(sub2(cur.TU, cur.To), idy2),
-                                          mul2(add2(cur.gxo, cx.gxU), i4x), mul2(add2(gzo, gzU), i4z),
+                                          fgrad<LIM>(cur.gxo, cx.gxU, i4x, idx2), fgrad<LIM>(gzo, gzU, i4z, idz2),
                                           add2(cur.bo[1], cx.bU[1]), add2(cur.bo[0], cx.bU[0]),
                                           add2(cur.bo[2], cx.bU[2]), fk, p);
         // +z faces
         const float2 Fz = face2s<SP, SAT>(cur.To, nxt.To, mul2(sub2(nxt.To, cur.To), idz2),
-                                          mul2(add2(cur.gxo, nxt.gxo), i4x), mul2(add2(cur.gyo, nxt.gyo), i4y),
+                                          fgrad<LIM>(cur.gxo, nxt.gxo, i4x, idx2),
+                                          fgrad<LIM>(cur.gyo, nxt.gyo, i4y, idy2),
                                           add2(cur.bo[2], nxt.bo[2]), add2(cur.bo[0], nxt.bo[0]),
                                           add2(cur.bo[1], nxt.bo[1]), fk, p);
 
@@ -528,9 +564,10 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         const int wy = q & (TY - 1), wx = (q + TY / 2) & (TY - 1);
         if (r == wy) {
             *reinterpret_cast<float2*>(&sm.Fy[par][0][c]) =
-                low_yface2<SP, SAT>(sm, g, p, fk, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), c);
+                low_yface2<SP, SAT, LIM>(sm, g, p, fk, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), c);
         } else if (r == wx && lane < TY) {
-            sm.FxLo[par][lane] = low_xface<SP, SAT>(sm, g, p, fk, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), lane);
+            sm.FxLo[par][lane] =
+                low_xface<SP, SAT, LIM>(sm, g, p, fk, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), lane);
         }
         if (MODE == 2) {
             const int ys = yslot(q);
@@ -585,9 +622,11 @@ namespace {
 
 // OCC selects the build: 2 the default (x2::kCtasPerSm CTAs per SM, two
 // planes in flight), 3 six CTAs per SM at up to 80 registers with one plane
-// in flight.
+// in flight, 4 the MC-limited faces (LIM; two planes in flight, four CTAs
+// per SM for the registers the limited slopes take).
 // BULK: bundles copied by the TMA engine (periodic grids with nx >= 72).
-constexpr int ctas_per_sm(int occ) { return occ == 2 ? x2::kCtasPerSm : 6; }
+constexpr int ctas_per_sm(int occ) { return occ == 2 ? x2::kCtasPerSm : (occ == 4 ? 4 : 6); }
+constexpr int occ_pd(int occ) { return occ == 3 ? 1 : x2::kPD; }
 
 template <bool SP, bool SAT, int MODE, int OCC, bool BULK, bool YT = false>
 __global__ void __launch_bounds__(x2::NTHREADS, ctas_per_sm(OCC))
@@ -595,13 +634,14 @@ stage_x2_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf,
                 const __grid_constant__ x2::YMaps ym)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];     // tensor copies land 128-byte aligned
-    constexpr int PD = OCC == 2 ? x2::kPD : 1;     // 3 CTAs per SM leave room for one plane in flight
+    constexpr int PD = occ_pd(OCC);
+    constexpr bool LIM = OCC == 4;
     x2::SmemT<PD>& sm = *reinterpret_cast<x2::SmemT<PD>*>(smem_raw);
     if (nzchunk > 0) {
         // one tile column, one chunk of nzchunk planes per CTA
         const int z0 = blockIdx.z * nzchunk;
-        tile_x2<SP, SAT, MODE, PD, BULK, YT>(sm, g, p, a, cf, status, blockIdx.x * x2::TX, blockIdx.y * x2::TY,
-                                             z0, min(nzchunk, g.n[2] - z0), &ym);
+        tile_x2<SP, SAT, MODE, PD, BULK, YT, LIM>(sm, g, p, a, cf, status, blockIdx.x * x2::TX,
+                                                  blockIdx.y * x2::TY, z0, min(nzchunk, g.n[2] - z0), &ym);
         return;
     }
     // Balanced schedule: the column-planes (tile column, plane) in column-major
@@ -617,8 +657,8 @@ stage_x2_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf,
         const int64_t col = u / nz;
         const int z0 = (int)(u - col * nz);
         const int nzc = (int)min((int64_t)(nz - z0), u1 - u);
-        tile_x2<SP, SAT, MODE, PD, BULK, YT>(sm, g, p, a, cf, status, (int)(col % ntx) * x2::TX,
-                                             (int)(col / ntx) * x2::TY, z0, nzc, &ym);
+        tile_x2<SP, SAT, MODE, PD, BULK, YT, LIM>(sm, g, p, a, cf, status, (int)(col % ntx) * x2::TX,
+                                                  (int)(col / ntx) * x2::TY, z0, nzc, &ym);
         u += nzc;
     }
 }
@@ -640,7 +680,7 @@ cudaError_t launch3(const KGrid<float>& g, const KPhys<float>& p, const x2::Fast
                     unsigned* status, int nzchunk, cudaStream_t st, const x2::YMaps& ym)
 {
     constexpr int kCtasPerSm = ctas_per_sm(OCC);
-    const int smem = (int)sizeof(x2::SmemT<OCC == 2 ? x2::kPD : 1>);
+    const int smem = (int)sizeof(x2::SmemT<occ_pd(OCC)>);
     static bool attr_set = false;       // the attribute is per function, set once
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(stage_x2_kernel<SP, SAT, MODE, OCC, BULK, YT>,
@@ -678,6 +718,11 @@ cudaError_t launch_mode(int mode, const KGrid<float>& g, const KPhys<float>& p, 
 }
 
 }  // namespace
+
+// The MC-limited launches (rkl_x2_lim.cu).
+cudaError_t launch_x2_lim(bool spitzer, bool saturate, int mode, const KGrid<float>& g, const KPhys<float>& p,
+                          const x2::FastArgs& a, const KCoef<float>& cf, unsigned* status, int nzchunk,
+                          cudaStream_t st);
 
 // The saturated-flux launches (rkl_x2_sat.cu).
 cudaError_t launch_x2_sat(bool spitzer, int occ, bool bulk, int mode, const KGrid<float>& g, const KPhys<float>& p,

@@ -8,12 +8,14 @@ configuration the benchmark times (rkl_super_step with cached graphs).
   window's own wrap cannot reach the centre); then all 10 super-steps with
   FP64 energy conservation.
 * 3D saturated blob, FP32, 512^3: the same sampled check of the first
-  super-step, then all 20 super-steps with FP64 energy conservation."""
+  super-step, then all 20 super-steps with FP64 energy conservation.
+* The 256^3 tangled field with MC-limited transverse gradients at every
+  face (the paired-cell kernel's limited build): the same checks."""
 import numpy as np
 import pytest
 
 import workloads
-from gpu_util import F32_STATE_MAX, host, rounded, torch_dev, window
+from gpu_util import F32_LIMITER_MAX, F32_STATE_MAX, host, rounded, torch_dev, window
 from oracle import Problem
 
 pytestmark = pytest.mark.gpu
@@ -46,7 +48,7 @@ def test_ring_fp64_full_run(rk, orc):
     assert plan.check() == 0
 
 
-def _sampled_first_step(rk, orc, W, dtype, cells, variant=0):
+def _sampled_first_step(rk, orc, W, dtype, cells, variant=0, tol=F32_STATE_MAX):
     import torch
     P = Problem(W.T.shape, **W.params)
     T = rounded(W.T, dtype)
@@ -69,7 +71,7 @@ def _sampled_first_step(rk, orc, W, dtype, cells, variant=0):
         Tw1, _ = orc.super_step(Pw, Tw, bw, dt, s)
         ref = Tw1[half, half, half]
         errs.append(abs(T1[tuple(c)] - ref) / np.max(np.abs(T)))
-    assert max(errs) < F32_STATE_MAX, errs
+    assert max(errs) < tol, errs
     return plan, Td, bd, dt, e0, P
 
 
@@ -100,4 +102,20 @@ def test_blob_512_saturated_sampled_and_conservation(rk, orc):
         s, eb, ea = plan.super_step(dt, Td, bd, energies=True)
         assert abs(ea - eb) <= 1e-6 * abs(eb)
     assert abs(plan.energy(Td) - e0) <= 1e-5 * abs(e0)
+    assert plan.check() == 0
+
+
+def test_tangled_256_limiter_sampled_and_conservation(rk, orc):
+    """The 256^3 workload of the limiter benchmark (floor +inf): sampled
+    cells of the first super-step against the oracle on windows, then the
+    remaining super-steps with FP64 energy conservation."""
+    import dataclasses
+    W = workloads.tangled(256, seed=2)
+    W = dataclasses.replace(W, params=dict(W.params, limiter="mc"))
+    rng = np.random.default_rng(3)
+    cells = [tuple(int(v) for v in rng.integers(0, 256, 3)) for _ in range(3)] + [(0, 0, 0), (32, 3, 63)]
+    plan, Td, bd, dt, e0, P = _sampled_first_step(rk, orc, W, "f32", cells, 0, F32_LIMITER_MAX)
+    for _ in range(3):
+        s, eb, ea = plan.super_step(dt, Td, bd, energies=True)
+        assert abs(ea - eb) <= 1e-6 * abs(eb)
     assert plan.check() == 0

@@ -155,6 +155,15 @@ def _variant_cases():
     lim = dict(spitz, bc="dirichlet", bc_value=0.95, limiter="mc", limiter_floor=1.0)
     for v in (0, 1, 2):
         out.append(("3d_limiter_floor_dirichlet", (14, 18, 70), lim, "f32", v))
+    # MC limiter at every face on the paired-cell kernel (variant 0 and the
+    # paired-cell variants all launch its limited build): Dirichlet ghosts,
+    # two tile columns with a ragged one, several 64 x 4 tiles, saturation
+    lim_all = dict(spitz, bc="dirichlet", bc_value=0.95, limiter="mc")
+    for v in (0, 3, 7):
+        out.append(("3d_limiter_all_dirichlet", (14, 18, 68), lim_all, "f32", v))
+    out.append(("3d_limiter_all_periodic", (21, 13, 132), dict(spitz, limiter="mc"), "f32", 4))
+    out.append(("3d_limiter_all_sat_const", (9, 10, 40), dict(kappa_par0=0.02, kappa_perp_ratio=0.1, saturate=True,
+                                                             phi=0.003, limiter="mc"), "f32", 0))
     # two-stage kernel: several 60 x 7 tiles with ragged edges in x, y and z
     out.append(("3d_pair_spitzer", (45, 30, 128), spitz, "f32", 5))
     out.append(("3d_pair_small", (5, 4, 8), spitz, "f32", 5))
@@ -362,3 +371,27 @@ def test_invalid_arguments_and_device_status(rk):
     plan.stage(1, 2, 1e-3, b, T3, M0, None, None, Y)
     assert plan.check() == rk._lib.RKL_ERR_NONFINITE
     assert plan.check() == 0
+
+
+def test_limiter_plan_kernel_routing(rk, orc):
+    """A limiter plan with the floor at +inf runs the paired-cell kernel's
+    limited build under variant 0 and every paired-cell variant (so their
+    results are bit-identical), the tiled kernel under variant 2; with a
+    finite floor the paired-cell variants do not apply."""
+    params = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4, limiter="mc")
+    shape = (12, 9, 72)
+    outs = {}
+    for v in (0, 3, 4, 6, 7, 2):
+        P, plan, T, b, Td, bd = _setup(rk, "routing", shape, params, "f32", v)
+        dt = 100.0 * orc.dt_expl(P, T)
+        plan.super_step(dt, Td, bd)
+        assert plan.check() == 0
+        outs[v] = host(Td)
+    for v in (3, 4, 6, 7):
+        assert np.array_equal(outs[v], outs[0]), v
+    # the tiled kernel's rounding differs, its result agrees within FP32
+    assert rel_l2(outs[2], outs[0]) < 1e-6
+    P, plan, T, b, Td, bd = _setup(rk, "routing", shape, dict(params, limiter_floor=1.0), "f32", 0)
+    for v in (3, 4, 6, 7):
+        with pytest.raises(rk.RklError):
+            plan.set_variant(v)
