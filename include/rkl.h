@@ -266,7 +266,7 @@ rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
  * from tensor maps (cp.async.bulk.tensor, one issuing thread; as 3 where the
  * driver offers no tensor-map encoder).  With the MC limiter at every face
  * (limiter_floor = +inf) variants 3, 4, 6 and 7 all launch the paired-cell
- * kernel's limited build (16 resident warps per SM, per-thread copies);
+ * kernel's limited build (20 resident warps per SM, per-thread copies);
  * with a finite floor the paired-cell variants do not apply.
  * RKL_ERR_UNSUPPORTED if the kernel does not apply to the grid.  nzchunk = planes per CTA of the paired-cell
  * kernels (0: chosen from the grid and the SM count, at least 3.5 waves of

@@ -115,6 +115,14 @@ __device__ __forceinline__ R mc_limit(R a, R b)
     m = fmin(m, R(2) * fabs(b));
     return a > R(0) ? m : -m;
 }
+// FP32: the same value without branches (2 min(|a|, |b|) = min(2|a|, 2|b|)
+// exactly; the sign of a when a b > 0).
+template <>
+__device__ __forceinline__ float mc_limit<float>(float a, float b)
+{
+    const float m = fminf(0.5f * fabsf(a + b), 2.f * fminf(fabsf(a), fabsf(b)));
+    return a * b > 0.f ? copysignf(m, a) : 0.f;
+}
 
 // Wrap or clamp an index that is at most a few cells outside [0, n).
 __device__ __forceinline__ int wrap(int i, int n)

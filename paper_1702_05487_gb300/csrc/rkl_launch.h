@@ -58,7 +58,7 @@ cudaError_t launch_stage_fast(const LaunchCfg& c, const KGrid<float>& g, const K
 // With bulk (and a periodic grid with nx >= 72) the plane bundles are
 // copied by the TMA engine (cp.async.bulk, one row per copy, mbarrier
 // completion) instead of per-thread 16-byte cp.async.
-// A limiter plan (floor +inf only) always takes the MC-limited build (four
+// A limiter plan (floor +inf only) always takes the MC-limited build (five
 // CTAs per SM, per-thread copies), whatever occupancy, bulk and ytma say.
 bool x2_stage_supported(const LaunchCfg& c, const KGrid<float>& g);
 bool x2_bulk_supported(const LaunchCfg& c, const KGrid<float>& g);

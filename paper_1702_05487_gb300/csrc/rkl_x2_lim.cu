@@ -1,6 +1,6 @@
 // Paired-cell stage kernel with MC-limited transverse gradients at every
 // face (Appendix C with the limiter floor at +inf): the instantiations of
-// the LIM build (four CTAs per SM), in a translation unit of their own so
+// the LIM build (five CTAs per SM), in a translation unit of their own so
 // that they compile in parallel with the others.
 #include "rkl_x2_tile.cuh"
 
