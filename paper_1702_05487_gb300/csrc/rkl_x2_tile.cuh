@@ -22,7 +22,10 @@
 // carries as centred differences T+ - T- become the cells' limited slopes
 // MC(T+ - T0, T0 - T-), and a face takes MC of its two cells' slopes / dx
 // instead of their sum / (4 dx): the same four one-sided differences per
-// transverse direction, each cell's pair limited once per plane.
+// transverse direction.  A cell's slope is limited once per plane where the
+// thread owns the cell (and again where a neighbouring face needs a cell of
+// the next row or column); the kernel carries halves of the slopes
+// (mc_half), which changes no rounding.
 #pragma once
 
 #include <algorithm>
@@ -39,28 +42,38 @@ namespace x2 {
 
 __device__ __forceinline__ int off(int r, int c) { return (r + 1) * SXS + c + 4; }
 
+// Half the MC limit: MC(a, b) / 2 = sign(a) min(|a + b| / 4, |a|, |b|) if
+// a b > 0, else 0.  Both factors 2 of MC are powers of two, so they move
+// into the callers' constants without changing a rounding.
+__device__ __forceinline__ float mc_half(float a, float b)
+{
+    const float m = fminf(0.25f * fabsf(a + b), fminf(fabsf(a), fabsf(b)));
+    return a * b > 0.f ? copysignf(m, a) : 0.f;
+}
+
 // Per-cell transverse slope along one axis from the cell (T0) and its two
-// neighbours: the centred difference T+ - T- (unscaled), or with LIM the
-// limited slope MC(T+ - T0, T0 - T-).
+// neighbours: the centred difference T+ - T- (unscaled), or with LIM half
+// the limited slope, MC(T+ - T0, T0 - T-) / 2.
 template <bool LIM>
 __device__ __forceinline__ float2 cslope(float2 Tp, float2 T0, float2 Tm)
 {
     if (!LIM) return sub2(Tp, Tm);
     const float2 up = sub2(Tp, T0), dn = sub2(T0, Tm);
-    return make_float2(mc_limit<float>(up.x, dn.x), mc_limit<float>(up.y, dn.y));
+    return make_float2(mc_half(up.x, dn.x), mc_half(up.y, dn.y));
 }
 template <bool LIM>
 __device__ __forceinline__ float cslope1(float Tp, float T0, float Tm)
 {
-    return LIM ? mc_limit<float>(Tp - T0, T0 - Tm) : Tp - Tm;
+    return LIM ? mc_half(Tp - T0, T0 - Tm) : Tp - Tm;
 }
 // Transverse gradient at a face from its two cells' slopes: their sum
-// times 1 / (4 dx) (i4), or with LIM their MC limit times 1 / dx (i1).
+// times 1 / (4 dx) (i4), or with LIM MC of the two limited slopes / dx =
+// 4 mc_half of the halves / dx (i1 = 4 / dx).
 template <bool LIM>
 __device__ __forceinline__ float2 fgrad(float2 sL, float2 sR, float2 i4, float2 i1)
 {
     if (!LIM) return mul2(add2(sL, sR), i4);
-    return mul2(make_float2(mc_limit<float>(sL.x, sR.x), mc_limit<float>(sL.y, sR.y)), i1);
+    return mul2(make_float2(mc_half(sL.x, sR.x), mc_half(sL.y, sR.y)), i1);
 }
 
 // Copy tasks fixed per thread for the whole tile, grouped by ring so that a
@@ -272,7 +285,10 @@ __device__ __forceinline__ QXY read_qxy(const SM& sm, int ts, int bs, int c, int
     const float2 Tur = lds2(&T[off(r + 1, c + 2)]);
     const float2 Tdr = lds2(&T[off(r - 1, c + 2)]);
     const float2 Tul = lds2(&T[off(r + 1, c - 2)]);
-    q.gyR = cslope<LIM>(make_float2(z.TU.y, Tur.x), make_float2(z.To.y, z.Tr), make_float2(Td.y, Tdr.x));
+    if (LIM)    // column 2l+1's limited slope is the pair's own
+        q.gyR = make_float2(z.gyo.y, cslope1<LIM>(Tur.x, z.Tr, Tdr.x));
+    else
+        q.gyR = cslope<LIM>(make_float2(z.TU.y, Tur.x), make_float2(z.To.y, z.Tr), make_float2(Td.y, Tdr.x));
     q.gxU = cslope<LIM>(make_float2(z.TU.y, Tur.x), z.TU, make_float2(Tul.y, z.TU.x));
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
@@ -302,8 +318,8 @@ __device__ __forceinline__ float2 low_yface2(const SM& sm, const KGrid<float>& g
 #pragma unroll
     for (int e = 0; e < 3; ++e) b[e] = add2(lds2(&sm.B[bs][e][off(-1, c)]), lds2(&sm.B[bs][e][off(0, c)]));
     return face2s<SP, SAT>(TL, TR, mul2(sub2(TR, TL), bc2(g.inv_dx[1])),
-                           fgrad<LIM>(gxL, gxR, bc2(g.inv_4dx[0]), bc2(g.inv_dx[0])),
-                           fgrad<LIM>(gzL, gzR, bc2(g.inv_4dx[2]), bc2(g.inv_dx[2])), b[1], b[0], b[2], fk, p);
+                           fgrad<LIM>(gxL, gxR, bc2(g.inv_4dx[0]), bc2(4.f * g.inv_dx[0])),
+                           fgrad<LIM>(gzL, gzR, bc2(g.inv_4dx[2]), bc2(4.f * g.inv_dx[2])), b[1], b[0], b[2], fk, p);
 }
 
 template <bool SP, bool SAT, bool LIM, class SM>
@@ -316,8 +332,8 @@ __device__ __forceinline__ float low_xface(const SM& sm, const KGrid<float>& g, 
     const float gyR = cslope1<LIM>(T[off(r + 1, 0)], TR, T[off(r - 1, 0)]);
     const float gzL = cslope1<LIM>(sm.T[tp][off(r, -1)], TL, sm.T[tm][off(r, -1)]);
     const float gzR = cslope1<LIM>(sm.T[tp][off(r, 0)], TR, sm.T[tm][off(r, 0)]);
-    const float gy = LIM ? mc_limit<float>(gyL, gyR) * g.inv_dx[1] : (gyL + gyR) * g.inv_4dx[1];
-    const float gz = LIM ? mc_limit<float>(gzL, gzR) * g.inv_dx[2] : (gzL + gzR) * g.inv_4dx[2];
+    const float gy = LIM ? mc_half(gyL, gyR) * (4.f * g.inv_dx[1]) : (gyL + gyR) * g.inv_4dx[1];
+    const float gz = LIM ? mc_half(gzL, gzR) * (4.f * g.inv_dx[2]) : (gzL + gzR) * g.inv_4dx[2];
     float b[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) b[e] = sm.B[bs][e][off(r, -1)] + sm.B[bs][e][off(r, 0)];
@@ -458,6 +474,8 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
 
     const float2 idx2 = bc2(g.inv_dx[0]), idy2 = bc2(g.inv_dx[1]), idz2 = bc2(g.inv_dx[2]);
     const float2 i4x = bc2(g.inv_4dx[0]), i4y = bc2(g.inv_4dx[1]), i4z = bc2(g.inv_4dx[2]);
+    // with LIM, limited face gradients take 4 / dx (fgrad)
+    const float2 ilx = bc2(4.f * g.inv_dx[0]), ily = bc2(4.f * g.inv_dx[1]), ilz = bc2(4.f * g.inv_dx[2]);
     // fluxes in face2s units; cm = -fscale / dx turns their differences into M
     const FaceK fk = face_consts<SP, SAT>(p);
     const float2 cmx = bc2(-fk.fscale * g.inv_dx[0]), cmy = bc2(-fk.fscale * g.inv_dx[1]);
@@ -465,8 +483,8 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
 
     QZ A = read_qz<LIM>(sm, tslot(-1), bslot(-1), c, r);
     QZ B = read_qz<LIM>(sm, tslot(0), bslot(0), c, r);
-    float2 Fz_lo = face2s<SP, SAT>(A.To, B.To, mul2(sub2(B.To, A.To), idz2), fgrad<LIM>(A.gxo, B.gxo, i4x, idx2),
-                                   fgrad<LIM>(A.gyo, B.gyo, i4y, idy2), add2(A.bo[2], B.bo[2]),
+    float2 Fz_lo = face2s<SP, SAT>(A.To, B.To, mul2(sub2(B.To, A.To), idz2), fgrad<LIM>(A.gxo, B.gxo, i4x, ilx),
+                                   fgrad<LIM>(A.gyo, B.gyo, i4y, ily), add2(A.bo[2], B.bo[2]),
                                    add2(A.bo[0], B.bo[0]), add2(A.bo[1], B.bo[1]), fk, p);
     float2 TmO = A.To, TmU = A.TU;
     float TmR = A.Tr;
@@ -537,24 +555,24 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         const float2 TR = make_float2(cur.To.y, cur.Tr);
         const float2 gzo = cslope<LIM>(nxt.To, cur.To, TmO);
         const float2 TRn = make_float2(nxt.To.y, nxt.Tr);
-        const float2 gzR = cslope<LIM>(TRn, TR, TmRp);
+        const float2 gzR = LIM ? make_float2(gzo.y, cslope1<LIM>(TRn.y, TR.y, TmRp.y)) : cslope<LIM>(TRn, TR, TmRp);
         const float2 gzU = cslope<LIM>(nxt.TU, cur.TU, TmU);
 
         // +x faces of the pair
         const float2 Fx = face2s<SP, SAT>(
-            cur.To, TR, mul2(sub2(TR, cur.To), idx2), fgrad<LIM>(cur.gyo, cx.gyR, i4y, idy2),
-            fgrad<LIM>(gzo, gzR, i4z, idz2),
+            cur.To, TR, mul2(sub2(TR, cur.To), idx2), fgrad<LIM>(cur.gyo, cx.gyR, i4y, ily),
+            fgrad<LIM>(gzo, gzR, i4z, ilz),
             add2(cur.bo[0], make_float2(cur.bo[0].y, cx.bR[0])), add2(cur.bo[1], make_float2(cur.bo[1].y, cx.bR[1])),
             add2(cur.bo[2], make_float2(cur.bo[2].y, cx.bR[2])), fk, p);
         // +y faces
         const float2 Fy = face2s<SP, SAT>(cur.To, cur.TU, mul2(sub2(cur.TU, cur.To), idy2),
-                                          fgrad<LIM>(cur.gxo, cx.gxU, i4x, idx2), fgrad<LIM>(gzo, gzU, i4z, idz2),
+                                          fgrad<LIM>(cur.gxo, cx.gxU, i4x, ilx), fgrad<LIM>(gzo, gzU, i4z, ilz),
                                           add2(cur.bo[1], cx.bU[1]), add2(cur.bo[0], cx.bU[0]),
                                           add2(cur.bo[2], cx.bU[2]), fk, p);
         // +z faces
         const float2 Fz = face2s<SP, SAT>(cur.To, nxt.To, mul2(sub2(nxt.To, cur.To), idz2),
-                                          fgrad<LIM>(cur.gxo, nxt.gxo, i4x, idx2),
-                                          fgrad<LIM>(cur.gyo, nxt.gyo, i4y, idy2),
+                                          fgrad<LIM>(cur.gxo, nxt.gxo, i4x, ilx),
+                                          fgrad<LIM>(cur.gyo, nxt.gyo, i4y, ily),
                                           add2(cur.bo[2], nxt.bo[2]), add2(cur.bo[0], nxt.bo[0]),
                                           add2(cur.bo[1], nxt.bo[1]), fk, p);
 
