@@ -42,7 +42,7 @@ WORKLOAD = "tangled256_spitzer_rkl2"
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, summarised in
 # profiles/stage_x2_tangled256.md), valid only while the stage kernel's
 # sources hash to source_hash (sha256 of STAGE_KERNEL_SOURCES, 16 hex).
-MEASURED_TRAFFIC = {"source_hash": "5f0eea0001977a9e", "bytes_per_launch": 542298624}
+MEASURED_TRAFFIC = {"source_hash": "87aa6e6bc24b5060", "bytes_per_launch": 541682944}
 
 
 # the sources of the default stage kernel (stage_x2_kernel)
