@@ -225,6 +225,32 @@ def test_tiled_kernels_match_generic(rk, orc, shape, nzchunk):
         assert norm_max(res[v], res[1]) < F32_STATE_MAX, v
 
 
+@pytest.mark.parametrize("shape,nzchunk", [((7, 9, 4), 0), ((40, 3, 68), 0), ((1, 33, 64), 0), ((37, 24, 128), 5),
+                                           ((9, 40, 8), 2), ((3, 8, 200), 1), ((37, 24, 128), -1),
+                                           ((21, 16, 68), -1)])
+def test_limited_paired_cell_shapes_and_schedules(rk, orc, shape, nzchunk):
+    """The paired-cell kernel's MC-limited build on tile-aligned, ragged and
+    degenerate shapes, with several z-chunk lengths and the balanced
+    schedule (nzchunk -1), against the oracle and the generic kernel."""
+    params = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4, limiter="mc")
+    res = {}
+    for v in (1, 3):
+        P, plan, T, b, Td, bd = _setup(rk, "x", shape, params, "f32", v)
+        if v == 3:
+            plan.set_variant(v, nzchunk)
+        dt = 40 * orc.dt_expl(P, T)
+        for _ in range(2):
+            plan.super_step(dt, Td, bd)
+        assert plan.check() == 0
+        res[v] = host(Td)
+    Tref = T
+    for _ in range(2):
+        Tref, _ = orc.super_step(P, Tref, b, dt)
+    for v in (1, 3):
+        assert rel_l2(res[v], Tref) < F32_STATE_REL_L2, v
+        assert norm_max(res[v], Tref) < F32_LIMITER_MAX, v
+
+
 def test_autotune_keeps_input_and_parity(rk, orc):
     """The autotuner times every kernel on a scratch copy, leaves T alone,
     and the kernel it picks still matches the oracle."""
