@@ -249,6 +249,24 @@ def cpu_oracle_sample(W, target_seconds: float = 12.0, size: int | None = None):
             "sample": sample}, el, (nz if W.T.ndim == 3 else reps)
 
 
+def cpu_baseline_all_and_one(W):
+    """The oracle on all host cores (the cpu_baseline value) and, on a
+    smaller window, on one thread; with the host's architecture and CPU
+    count."""
+    import platform
+    import oracle
+    cpu, _, _ = cpu_oracle_sample(W)
+    n_all = cpu["cores"]
+    oracle.set_threads(1)
+    try:
+        one, _, _ = cpu_oracle_sample(W, target_seconds=8.0)
+    finally:
+        oracle.set_threads(n_all)
+    cpu["single_thread"] = {"value": one["value"], "sample": one["sample"]}
+    cpu["host"] = f"{platform.machine()}, {os.cpu_count()} logical CPUs"
+    return cpu
+
+
 def run_reference(args):
     world, rank, local = dist_env()
     if rank != 0:
@@ -406,7 +424,7 @@ def run_ours(args):
         traffic = MEASURED_TRAFFIC["bytes_per_launch"]
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu, _, _ = cpu_oracle_sample(W)
+        cpu = cpu_baseline_all_and_one(W)
     s_last = s_used[-1] if s_used else rk.rkl_num_stages(W.ratio)
     line = {
         "metric": "Gcell-stage/s per RKL2 stage", "value": value, "unit": "Gcell-stage/s",
