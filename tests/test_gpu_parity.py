@@ -268,6 +268,24 @@ def test_autotune_keeps_input_and_parity(rk, orc):
     assert rel_l2(host(Td), Tref) < F32_STATE_REL_L2
 
 
+def test_autotune_limiter_plan(rk, orc):
+    """A limiter plan (floor +inf) autotunes over the generic, tiled and
+    limited paired-cell kernels only, and the pick matches the oracle."""
+    import torch
+    shape = (20, 16, 64)
+    params = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4, limiter="mc")
+    P, plan, T, b, Td, bd = _setup(rk, "x", shape, params, "f32")
+    dt = 50 * orc.dt_expl(P, T)
+    T_before = Td.clone()
+    v, nz, ms = plan.autotune(dt, Td, bd)
+    assert torch.equal(Td, T_before)
+    assert v in (1, 2, 3) and ms > 0
+    plan.super_step(dt, Td, bd)
+    Tref, _ = orc.super_step(P, T, b, dt)
+    assert rel_l2(host(Td), Tref) < F32_STATE_REL_L2
+    assert norm_max(host(Td), Tref) < F32_LIMITER_MAX
+
+
 def test_dt_expl_and_energy(rk, orc):
     shape = (24, 20, 36)
     params = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
