@@ -699,7 +699,8 @@ def main():
                     help="stage kernel: 0 auto, 1 generic, 2 tiled, 3/4 paired-cell at 5/6 CTAs per SM, 5 two-stage, 6 bulk copies, 7 tensor-map Y copies")
     ap.add_argument("--nzchunk", type=int, default=0, help="planes per CTA (0 automatic, < 0 balanced runs)")
     ap.add_argument("--limiter", default="none", choices=["none", "mc"],
-                    help="transverse gradients: plain averages, or MC-limited at every face (Appendix C)")
+                    help="transverse gradients: plain averages, or MC-limited at every face (Appendix C; "
+                         "the paired-cell kernel's limited build, --variant 2 the tiled kernel)")
     ap.add_argument("--workload", default="tangled256",
                     choices=list(WORKLOADS) + ["ensemble64", "surrogate128", "split256"])
     ap.add_argument("--pairs", type=int, default=20000, help="training pairs of the surrogate workload")
