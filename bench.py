@@ -39,9 +39,9 @@ BYTES_PER_CELL_STAGE = 32          # Y_{j-1}, Y_{j-2}, Y_0, M(Y_0), bx, by, bz r
 WORKLOAD = "tangled256_spitzer_rkl2"
 
 # DRAM traffic of one stage launch (j >= 2) of the 256^3 workload from one
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, summarised in
-# profiles/stage_x2_tangled256.md), valid only while the stage kernel's
-# sources hash to source_hash (sha256 of STAGE_KERNEL_SOURCES, 16 hex).
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of the stage
+# kernel), valid only while the stage kernel's sources hash to source_hash
+# (sha256 of STAGE_KERNEL_SOURCES, 16 hex).
 MEASURED_TRAFFIC = {"source_hash": "87aa6e6bc24b5060", "bytes_per_launch": 541682944}
 
 
@@ -80,7 +80,7 @@ class ClockSampler:
     QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-    PERIOD_MS = 50
+    PERIOD_MS = 10
     REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, gpu_index: int):
@@ -192,6 +192,17 @@ WORKLOADS = {
 }
 
 
+def workload_config(W, world: int, name: str = "tangled256") -> dict:
+    """The workload as both arms report it (no kernel or sample details)."""
+    ncell = int(W.T.size)
+    return {"workload": WORKLOAD if name == "tangled256" else W.name, "shape": list(W.T.shape),
+            "cells": ncell, "dt_over_dtexpl": W.ratio,
+            "step": "one RKL2 super-step (dt_expl pass + s stages)",
+            "l2": ("inputs larger than L2: 8 grid arrays per stage" if ncell * 32 > 129e6
+                   else "working set fits in L2"),
+            "parallelism": f"replicas{world}" if world > 1 else "single"}
+
+
 def make_inputs(name="tangled256"):
     import workloads
     gen = WORKLOADS[name][0]
@@ -287,7 +298,7 @@ def run_reference(args):
             "unit": "Gcell-stage/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": N_GRID, "dt_over_dtexpl": RATIO},
+            "config": workload_config(W, world),
             "cpu_baseline": res,
             "e2e": {"value": res["value"], "unit": "Gcell-stage/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -365,9 +376,11 @@ def run_ours(args):
         ev0.record(stream)
         stages = 0
         launches = 0
+        s_timed = []
         for _ in range(args.steps):
             s = plan.super_step(dt, T, b)
             stages += s
+            s_timed.append(s)
             launches += stage_launches_per_step(args.variant, s)
         ev1.record(stream)
         barrier()
@@ -425,19 +438,15 @@ def run_ours(args):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_all_and_one(W)
-    s_last = s_used[-1] if s_used else rk.rkl_num_stages(W.ratio)
     line = {
         "metric": "Gcell-stage/s per RKL2 stage", "value": value, "unit": "Gcell-stage/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.workload == "tangled256" else W.name, "shape": list(W.T.shape),
-                   "cells": ncell, "s": s_last,
-                   "dt_over_dtexpl": W.ratio, "step": "one RKL2 super-step (dt_expl pass + s stages)",
-                   "l2": ("inputs larger than L2: 8 grid arrays per stage" if ncell * 32 > 129e6
-                          else "working set fits in L2"),
-                   "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "kernel_variant": args.variant, "nzchunk": args.nzchunk, "limiter": args.limiter},
+        "config": workload_config(W, world, args.workload),
+        "run": {"s": stages / max(1, args.steps), "s_range": [min(s_timed), max(s_timed)],
+                "s_note": "mean stage count of the timed super-steps (T cools at fixed dt, so s may drop)",
+                "kernel_variant": args.variant, "nzchunk": args.nzchunk, "limiter": args.limiter},
         "roofline": {"bound": "hbm", "kernel": "rkl2 stage", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_cs * ncell,

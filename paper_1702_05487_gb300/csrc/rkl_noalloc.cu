@@ -154,6 +154,7 @@ extern "C" rkl_status rkl_dt_expl_energy_noalloc(const rkl_grid* grid, const rkl
     int64_t n = 1;
     for (int d = 0; d < 3; ++d) {
         if (g.n[d] < 1) return err(RKL_ERR_INVALID_ARG, "bad n");
+        if (d >= g.ndim && g.n[d] != 1) return err(RKL_ERR_INVALID_ARG, "inactive axis must have n = 1");
         if (d < g.ndim && !(g.dx[d] > 0.0 && std::isfinite(g.dx[d])))
             return err(RKL_ERR_INVALID_ARG, "dx must be finite and > 0");
         if (g.n[d] > kNoAllocMaxCells) return err(RKL_ERR_INVALID_ARG, "grid larger than the no-allocation limit");

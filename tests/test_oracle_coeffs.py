@@ -137,3 +137,24 @@ def test_effective_cfl_asymptote(orc):
     for s in (50, 100, 400):
         ratio = (s * s + s - 2) / 4.0
         assert ratio / 2 / (s * s / 8.0) == pytest.approx(1.0, rel=3.0 / s)
+
+
+@pytest.mark.parametrize("s", [2, 9, 20, 28, 40])
+def test_stage_perturbations_grow_most_on_undamped_modes(orc, s):
+    """The FP32 error model of the GPU tests propagates a perturbation of
+    stage k by the homogeneous recurrence of Eq. rkl2scheme at z = tau lambda
+    = 0.  On an eigenmode with z in the real stability interval
+    [-(s^2+s-2)/2, 0] the recurrence is e_j = (mu_j + mu~_j z) e_{j-1} +
+    nu_j e_{j-2}: its reach |e_s| never exceeds the z = 0 value A_k(s)."""
+    import numpy as np
+    from gpu_util import stage_amplification
+    mu, nu, mut, _ = orc.coeffs(s)
+    A = stage_amplification(orc, s)
+    zs = -np.linspace(0.0, (s * s + s - 2) / 2.0, 801)
+    for k in range(1, s + 1):
+        e = np.zeros((s + 1, zs.size))
+        e[k] = 1.0
+        for j in range(k + 1, s + 1):
+            e[j] = (mu[j] + mut[j] * zs) * e[j - 1] + nu[j] * e[j - 2]
+        assert np.max(np.abs(e[s])) <= A[k - 1] * (1 + 1e-12), k
+    assert A[-1] == 1.0

@@ -68,3 +68,59 @@ def test_noalloc_rejects_grids_beyond_its_scratch(rk):
     with pytest.raises(rk.RklError) as ei:
         _lib.rkl_dt_expl_energy_noalloc(g, p, T)
     assert "cp" in str(ei.value)
+    # a 2D grid whose unused third axis claims more than one cell would make
+    # the reduction read past the end of T: rejected like rkl_plan_create does
+    g = make_grid((2, 4))
+    g.n[2] = 3
+    with pytest.raises(rk.RklError) as ei:
+        _lib.rkl_dt_expl_energy_noalloc(g, make_phys(), T)
+    assert ei.value.status == _lib.RKL_ERR_INVALID_ARG
+    assert "inactive axis" in str(ei.value)
+
+
+def test_noalloc_reports_nonfinite_under_any_kappa(rk):
+    """Unlike rkl_dt_expl under constant kappa (which never reads T), this
+    entry point reads every cell and reports NaN / Inf as an error."""
+    import torch
+    from paper_1702_05487_gb300 import _lib, make_grid, make_phys
+    T = torch.ones((6, 5, 7), device="cuda")
+    T[3, 2, 6] = float("nan")
+    for kappa in ("const", "spitzer"):
+        with pytest.raises(rk.RklError) as ei:
+            _lib.rkl_dt_expl_energy_noalloc(make_grid((6, 5, 7)), make_phys(kappa_model=kappa), T)
+        assert ei.value.status == _lib.RKL_ERR_NONFINITE
+    T[3, 2, 6] = 1.0
+    dt, e = _lib.rkl_dt_expl_energy_noalloc(make_grid((6, 5, 7)), make_phys(), T)
+    assert e == pytest.approx(1.0)          # 210 cells of T = 1, each of volume 1/210
+
+
+def test_noalloc_at_its_largest_grid_against_the_oracle(rk, orc):
+    """A 512^3 FP32 grid, 2^27 cells, fills every partial slot of the
+    scratch.  The hottest and the coldest cell sit in the last block, so
+    dt_expl depends on the top slot; the result must match the FP64 oracle's
+    Eq. dt_exp and energy, and a small grid reduced right after must not see
+    the large one's partials."""
+    import torch
+    from oracle import Problem
+    from paper_1702_05487_gb300 import _lib, make_grid, make_phys
+    n = 512
+    rng = np.random.default_rng(27)
+    T = (0.8 + 0.4 * rng.random(n ** 3, dtype=np.float32)).reshape(n, n, n)
+    T[-1, -1, -1] = np.float32(1.75)
+    T[-1, -1, -3] = np.float32(0.5)
+    params = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
+    P = Problem(T.shape, dx=(1.0 / n,) * 3, **params)
+    T64 = T.astype(np.float64)
+    want_dt, want_e = orc.dt_expl(P, T64), orc.energy(P, T64)
+    del T64
+    Td = torch.from_numpy(T).cuda()
+    stream = torch.cuda.current_stream().cuda_stream
+    dt, e = _lib.rkl_dt_expl_energy_noalloc(make_grid(T.shape), make_phys(**params), Td, stream)
+    assert dt == pytest.approx(want_dt, rel=1e-14)
+    assert e == pytest.approx(want_e, rel=1e-12)
+    del Td
+    Ts = torch.full((3, 4, 5), 2.0, device="cuda")
+    dt2, e2 = _lib.rkl_dt_expl_energy_noalloc(make_grid((3, 4, 5)), make_phys(**params), Ts, stream)
+    Ps = Problem((3, 4, 5), dx=(1 / 5, 1 / 4, 1 / 3), **params)
+    assert dt2 == pytest.approx(orc.dt_expl(Ps, np.full((3, 4, 5), 2.0)), rel=1e-14)
+    assert e2 == pytest.approx(orc.energy(Ps, np.full((3, 4, 5), 2.0)), rel=1e-14)
