@@ -455,6 +455,32 @@ rkl_status rkl_sur_adam(rkl_surrogate *sur, double lr, double beta1, double beta
 rkl_status rkl_sur_train_step(rkl_surrogate *sur, double head_scale, const void *target, double lr,
                               double *loss);
 /*
+ * One layer of the network on caller-owned device buffers, with the
+ * surrogate's current BF16 weights of that layer and its patch size
+ * (voxel v = (z H + y) W + x, channels last; asynchronous on the stream).
+ * These are the kernels rkl_sur_forward / rkl_sur_backward run, exposed one
+ * at a time so that each can be checked on its own (all three are periodic
+ * 3x3x3 cross-correlations, offset o = 9 (dz+1) + 3 (dy+1) + (dx+1)):
+ *   forward:       in bf16 [V][cin] -> out bf16 [V][cout] = ReLU(bias +
+ *                  sum_o sum_ci w[o][co][ci] in[v + o][ci]), or for the
+ *                  last layer f32 [V][16] without the ReLU;
+ *   backward_data: layer >= 1; dz bf16 [V][cout], mask bf16 [V][cin] ->
+ *                  out bf16 [V][cin] = (sum_o sum_co w[o][co][ci]
+ *                  dz[v - o][co]) where mask > 0, else 0;
+ *   weight_grad:   dz bf16 [V][cout], x bf16 [V][cin] -> the layer's
+ *                  gradients (read with rkl_sur_get_grads): dW[o][co][ci] =
+ *                  sum_v dz[v][co] x[v + o][ci], db[co] = sum_v dz[v][co],
+ *                  summed in a fixed order (the same result every run).
+ * The forward and backward-data passes use the backend of
+ * rkl_sur_set_backend; the weight gradient is the warp-level kernel.
+ * (cin, cout) of a layer: rkl_sur_layer_shape.
+ */
+rkl_status rkl_sur_layer_forward(rkl_surrogate *sur, int layer, const void *in, void *out);
+rkl_status rkl_sur_layer_backward_data(rkl_surrogate *sur, int layer, const void *dz, const void *mask,
+                                       void *out);
+rkl_status rkl_sur_layer_weight_grad(rkl_surrogate *sur, int layer, const void *dz, const void *x);
+
+/*
  * One super-step of length dt with the surrogate: predicts dT, computes the
  * trapezoidal-rule residual rho = ||dT - (dt/2)(M(T) + M(T + dT))|| / ||dT||
  * (two applications of M), accepts T + dT if rho <= threshold, otherwise
@@ -474,10 +500,14 @@ rkl_status rkl_sur_super_step(rkl_surrogate *sur, rkl_plan *plan, double dt, voi
  * host code that hands the library a fixed memory budget up front, or a
  * time-step loop that must not stall on an allocation.
  *
- * Computes exactly what rkl_dt_expl (Eq. dt_exp) and rkl_energy (sum T dV,
- * FP64) return for the device array T of the given grid, without a plan,
- * on cuda_stream (void* cudaStream_t), and synchronises that stream.
- * Writes *dt_out and *energy_out (host).
+ * Computes the same dt_expl as rkl_dt_expl and the same FP64 energy
+ * (sum T dV) as rkl_energy for the device array T of the given grid,
+ * without a plan, on cuda_stream (void* cudaStream_t), and synchronises
+ * that stream.  Writes *dt_out and *energy_out (host).  One difference:
+ * this entry point always reads every cell of T and fails with
+ * RKL_ERR_NONFINITE if any holds NaN or Inf, whatever the kappa model
+ * (rkl_dt_expl does not read T under constant kappa, and rkl_energy sums
+ * NaN without an error).
  *
  * Scratch: a fixed array inside the library (about 1.5 MB, held on every
  * GPU that loads the library until the process exits), enough for grids of
@@ -488,7 +518,8 @@ rkl_status rkl_sur_super_step(rkl_surrogate *sur, rkl_plan *plan, double dt, voi
  * current), so make that first call before any stream capture.  All calls
  * share the one array: calls whose GPU work overlaps (unordered streams)
  * race on it.  Each call overwrites every scratch entry it reads.
- * Errors: RKL_ERR_INVALID_ARG (bad grid/phys or too many cells),
+ * Errors: RKL_ERR_INVALID_ARG (bad grid/phys, an axis d >= ndim with
+ * n[d] != 1, or too many cells),
  * RKL_ERR_NONFINITE (T holds NaN/Inf), RKL_ERR_NONPOSITIVE_T (T <= 0 under
  * Spitzer kappa), RKL_ERR_CUDA; the message is in rkl_last_error(NULL).
  */

@@ -14,7 +14,12 @@ plain numpy in FP64 (arrays are channels-first [C][z][y][x]):
 * ``conv3d_grad_input`` - its adjoint with respect to the input,
 * ``conv3d_grad_weight``- its gradient with respect to weights and bias,
 * ``forward`` / ``backward`` - the network, MSE loss on dT, chain rule,
-* ``adam``              - one Adam update (Kingma & Ba 2015).
+* ``adam``              - one Adam update (Kingma & Ba 2015),
+* ``round_bf16``        - the nearest BF16 value (8 significant bits, ties to
+  even): with ``store=round_bf16`` the forward and backward passes round
+  every value at the points where the network keeps it in BF16 (inputs,
+  weights, hidden activations, back-propagated gradients), so that the
+  cost of BF16 storage itself can be measured in FP64.
 
 Only the test suite loads it; it shares nothing with the CUDA library.
 """
@@ -58,6 +63,24 @@ def conv3d_grad_weight(gy, x):
     return gw, gy.sum(axis=(1, 2, 3))
 
 
+def round_bf16(a):
+    """Round FP64 values to the nearest BF16 value (1 sign, 8 exponent and 7
+    stored fraction bits: the FP64 significand cut to its top 7 fraction
+    bits, round to nearest, ties to even), returned as FP64.  Valid for
+    values inside BF16's normal range and zero."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    bits = a.view(np.uint64)
+    drop = np.uint64(52 - 7)
+    lsb = (bits >> drop) & np.uint64(1)
+    half = (np.uint64(1) << (drop - np.uint64(1))) - np.uint64(1)
+    out = (bits + half + lsb) & ~((np.uint64(1) << drop) - np.uint64(1))
+    return out.view(np.float64)
+
+
+def _identity(a):
+    return a
+
+
 def features(T, b, kappa0, spitzer, ratio):
     """Network input channels [6][z][y][x]: T - 1, b_x, b_y, b_z,
     log10(kappa_par(T) / 0.01), (dt / dt_expl) / 100."""
@@ -82,36 +105,41 @@ def flux_divergence_adjoint(gdT, tau, dx):
     return gG
 
 
-def forward(params, x, tau, dx):
-    """params: list of (w, b) per layer; x: [6, D, H, W].  Returns (dT, cache)."""
-    acts = [x]
+def forward(params, x, tau, dx, store=None):
+    """params: list of (w, b) per layer; x: [6, D, H, W].  Returns (dT, cache).
+    store (default: none) is applied to the input, the weights and every
+    hidden activation, the values a BF16 network keeps in BF16."""
+    store = store or _identity
+    h = store(x)
+    acts = [h]
     pre = []
-    h = x
     for li, (w, b) in enumerate(params):
-        z = conv3d(h, w, b)
+        z = conv3d(h, store(w), b)
         pre.append(z)
-        h = np.maximum(z, 0.0) if li < len(params) - 1 else z
+        h = store(np.maximum(z, 0.0)) if li < len(params) - 1 else z
         acts.append(h)
     dT = flux_divergence(h, tau, dx)
     return dT, (acts, pre)
 
 
-def loss_and_grad(params, x, target, tau, dx):
-    """MSE loss 0.5 * mean((dT - target)^2) and its gradients per layer."""
-    dT, (acts, pre) = forward(params, x, tau, dx)
+def loss_and_grad(params, x, target, tau, dx, store=None):
+    """MSE loss 0.5 * mean((dT - target)^2) and its gradients per layer.
+    store as in forward, also applied to the gradients propagated back to
+    each layer's output (after the ReLU mask)."""
+    store = store or _identity
+    dT, (acts, pre) = forward(params, x, tau, dx, store)
     n = dT.size
     r = dT - target
     loss = 0.5 * float(np.sum(r * r)) / n
-    g = flux_divergence_adjoint(r / n, tau, dx)
+    g = store(flux_divergence_adjoint(r / n, tau, dx))
     grads = [None] * len(params)
     for li in range(len(params) - 1, -1, -1):
         w, b = params[li]
-        if li < len(params) - 1:
-            g = g * (pre[li] > 0.0)
         gw, gb = conv3d_grad_weight(g, acts[li])
         grads[li] = (gw, gb)
         if li > 0:
-            g = conv3d_grad_input(g, w)
+            # through layer li to the output of layer li - 1, then its ReLU
+            g = store(conv3d_grad_input(g, store(w)) * (pre[li - 1] > 0.0))
     return loss, grads, dT
 
 

@@ -109,6 +109,9 @@ SIGNATURES = {
     "rkl_sur_train_step": (ctypes.c_int, [_vp, ctypes.c_double, _vp, ctypes.c_double, _dp]),
     "rkl_sur_super_step": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, ctypes.c_double, ctypes.c_double,
                                           _ip, _dp, _ip]),
+    "rkl_sur_layer_forward": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "rkl_sur_layer_backward_data": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+    "rkl_sur_layer_weight_grad": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
 }
 
 _lib = None
@@ -415,6 +418,21 @@ def rkl_sur_get_grads(sur, layer):
     b = np.zeros(co, dtype=np.float32)
     _scheck(load().rkl_sur_get_grads(sur, int(layer), _ptr(w), _ptr(b)), sur)
     return w, b
+
+
+def rkl_sur_layer_forward(sur, layer, x, out):
+    """One layer's forward convolution on device tensors (bf16 [V][cin] in)."""
+    _scheck(load().rkl_sur_layer_forward(sur, int(layer), _ptr(x), _ptr(out)), sur)
+
+
+def rkl_sur_layer_backward_data(sur, layer, dz, mask, out):
+    """One layer's backward-data convolution, masked by mask > 0."""
+    _scheck(load().rkl_sur_layer_backward_data(sur, int(layer), _ptr(dz), _ptr(mask), _ptr(out)), sur)
+
+
+def rkl_sur_layer_weight_grad(sur, layer, dz, x):
+    """One layer's weight and bias gradients (read them with rkl_sur_get_grads)."""
+    _scheck(load().rkl_sur_layer_weight_grad(sur, int(layer), _ptr(dz), _ptr(x)), sur)
 
 
 def rkl_sur_features(sur, T, b, kappa_par0, spitzer, ratio):

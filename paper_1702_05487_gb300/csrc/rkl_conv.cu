@@ -189,10 +189,12 @@ conv_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restric
 // offsets from them.  The work of a tile is split into units (offset o,
 // 8-channel ci block nt), each a COUT x 8 block of dW; warp w owns units
 // w, w + 16, ... and accumulates them over all its tiles in registers,
-// then adds them to dW atomically.
+// then stores them to the CTA's own slice of part ([gridDim.x][27][COUT]
+// [CIN]); sum_partials adds the slices to dW in CTA order, so the result
+// does not depend on which CTA finishes first.
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(NTHR, 1)
-wgrad_kernel(const __nv_bfloat16* __restrict__ dz, const __nv_bfloat16* __restrict__ x, float* __restrict__ dW,
+wgrad_kernel(const __nv_bfloat16* __restrict__ dz, const __nv_bfloat16* __restrict__ x, float* __restrict__ part,
              int D, int H, int W)
 {
     constexpr int SZ = COUT + 8, SXC = CIN + 8;
@@ -279,9 +281,8 @@ wgrad_kernel(const __nv_bfloat16* __restrict__ dz, const __nv_bfloat16* __restri
             for (int h = 0; h < 2; ++h) {
                 const int co = mt * 16 + (lane >> 2) + 8 * h;
                 const int ci = nt * 8 + 2 * (lane & 3);
-                float* dst = dW + ((int64_t)o * COUT + co) * CIN + ci;
-                atomicAdd(dst, acc[i][mt][2 * h]);
-                atomicAdd(dst + 1, acc[i][mt][2 * h + 1]);
+                float* dst = part + (int64_t)blockIdx.x * (27 * COUT * CIN) + ((int64_t)o * COUT + co) * CIN + ci;
+                *reinterpret_cast<float2*>(dst) = make_float2(acc[i][mt][2 * h], acc[i][mt][2 * h + 1]);
             }
     }
 }
@@ -401,9 +402,10 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
     }
 }
 
-// bias gradient: db[c] = sum_v dz[v][c]
+// bias gradient: block b stores its sum of dz[v][c] over its voxels to
+// part[b][c]; sum_partials adds the blocks' sums to db in block order.
 template <int C>
-__global__ void bgrad_kernel(const __nv_bfloat16* __restrict__ dz, float* db, int64_t V)
+__global__ void __launch_bounds__(256) bgrad_kernel(const __nv_bfloat16* __restrict__ dz, float* part, int64_t V)
 {
     float s[C];
 #pragma unroll
@@ -411,12 +413,30 @@ __global__ void bgrad_kernel(const __nv_bfloat16* __restrict__ dz, float* db, in
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x)
 #pragma unroll
         for (int c = 0; c < C; ++c) s[c] += __bfloat162float(dz[v * C + c]);
+    __shared__ float sh[8][C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         float t = s[c];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&db[c], t);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][c] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < C) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += sh[w][threadIdx.x];
+        part[(int64_t)blockIdx.x * C + threadIdx.x] = t;
+    }
+}
+
+// out[i] += sum over b = 0 .. nparts - 1 of part[b][i], in that order.
+__global__ void sum_partials_kernel(const float* __restrict__ part, int nparts, int n, float* __restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float t = 0.f;
+        for (int b = 0; b < nparts; ++b) t += part[(int64_t)b * n + i];
+        out[i] += t;
     }
 }
 
@@ -504,7 +524,8 @@ cudaError_t adam(float* p, const float* g, float* m, float* v, int n, float lr, 
 }
 
 template <int CIN, int COUT>
-static cudaError_t wgrad_t(const void* dz, const void* x, float* dW, int D, int H, int W, cudaStream_t st)
+static cudaError_t wgrad_t(const void* dz, const void* x, float* dW, float* part, int D, int H, int W,
+                           cudaStream_t st)
 {
     constexpr int SZ = COUT + 8, SXC = CIN + 8;
     const int smem = (TV * SZ + HV * SXC) * 2;
@@ -514,32 +535,49 @@ static cudaError_t wgrad_t(const void* dz, const void* x, float* dW, int D, int 
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int ntiles = (D / TZ) * (H / TY) * (W / TX);
+    const int sms = wgrad_max_ctas();
     const int grid = ntiles < sms ? ntiles : sms;
     wgrad_kernel<CIN, COUT><<<grid, NTHR, smem, st>>>(static_cast<const __nv_bfloat16*>(dz),
-                                                     static_cast<const __nv_bfloat16*>(x), dW, D, H, W);
+                                                     static_cast<const __nv_bfloat16*>(x), part, D, H, W);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sum_partials_kernel<<<grid_for(27 * COUT * CIN), 256, 0, st>>>(part, grid, 27 * COUT * CIN, dW);
     return cudaGetLastError();
 }
 
-cudaError_t conv_wgrad(int cin, int cout, const void* dz, const void* x, float* dW, int D, int H, int W, int nsplit,
+int wgrad_max_ctas()
+{
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+    }
+    return sms;
+}
+
+size_t wgrad_workspace_floats() { return (size_t)wgrad_max_ctas() * 27 * 32 * 32; }
+
+cudaError_t conv_wgrad(int cin, int cout, const void* dz, const void* x, float* dW, float* part, int D, int H, int W,
                        cudaStream_t st)
 {
     if (D % TZ || H % TY || W % TX) return cudaErrorInvalidValue;
-    (void)nsplit;
-    if (cin == 16 && cout == 32) return wgrad_t<16, 32>(dz, x, dW, D, H, W, st);
-    if (cin == 32 && cout == 32) return wgrad_t<32, 32>(dz, x, dW, D, H, W, st);
-    if (cin == 32 && cout == 16) return wgrad_t<32, 16>(dz, x, dW, D, H, W, st);
+    if (cin == 16 && cout == 32) return wgrad_t<16, 32>(dz, x, dW, part, D, H, W, st);
+    if (cin == 32 && cout == 32) return wgrad_t<32, 32>(dz, x, dW, part, D, H, W, st);
+    if (cin == 32 && cout == 16) return wgrad_t<32, 16>(dz, x, dW, part, D, H, W, st);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t conv_bgrad(int c, const void* dz, float* db, int64_t V, cudaStream_t st)
+cudaError_t conv_bgrad(int c, const void* dz, float* db, float* part, int64_t V, cudaStream_t st)
 {
-    if (c == 32) bgrad_kernel<32><<<304, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(dz), db, V);
-    else if (c == 16) bgrad_kernel<16><<<304, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(dz), db, V);
+    if (c == 32) bgrad_kernel<32><<<kBgradBlocks, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(dz), part, V);
+    else if (c == 16) bgrad_kernel<16><<<kBgradBlocks, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(dz), part, V);
     else return cudaErrorInvalidValue;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sum_partials_kernel<<<1, 32, 0, st>>>(part, kBgradBlocks, c, db);
     return cudaGetLastError();
 }
 

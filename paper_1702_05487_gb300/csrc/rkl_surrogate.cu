@@ -8,6 +8,7 @@
 // super-step with the surrogate checks the prediction with one residual of
 // the trapezoidal rule built from two M evaluations and falls back to the
 // plain RKL2 super-step when the check fails.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -92,6 +93,7 @@ struct rkl_surrogate {
     float* r = nullptr;            // f32 [V]
     void* dG = nullptr;            // bf16 [V][16]
     void* dZ[2] = {};              // bf16 [V][32]
+    float* gpart = nullptr;        // per-CTA partial weight / bias gradients (fixed-order sums)
     float* Yp = nullptr;
     float* M0 = nullptr;
     float* Mp = nullptr;
@@ -158,15 +160,15 @@ rkl_status backward_impl(rkl_surrogate* s, const float* target, double* loss)
     }
     // head
     const void* dz = s->dG;
-    SUR_CK(s, conv::conv_wgrad(32, 16, dz, s->A[4], s->gw[5], D, H, W, 8, s->stream));
-    SUR_CK(s, conv::conv_bgrad(16, dz, s->gb[5], s->V, s->stream));
+    SUR_CK(s, conv::conv_wgrad(32, 16, dz, s->A[4], s->gw[5], s->gpart, D, H, W, s->stream));
+    SUR_CK(s, conv::conv_bgrad(16, dz, s->gb[5], s->gpart, s->V, s->stream));
     SUR_CK(s, conv_fwd(s, 16, 32, 2, dz, s->wb[5], nullptr, s->A[4], s->dZ[0]));
     int cur = 0;
     for (int l = kLayers - 2; l >= 0; --l) {
         dz = s->dZ[cur];
         const void* x = l > 0 ? s->A[l - 1] : s->X0;
-        SUR_CK(s, conv::conv_wgrad(kCin[l], 32, dz, x, s->gw[l], D, H, W, 8, s->stream));
-        SUR_CK(s, conv::conv_bgrad(32, dz, s->gb[l], s->V, s->stream));
+        SUR_CK(s, conv::conv_wgrad(kCin[l], 32, dz, x, s->gw[l], s->gpart, D, H, W, s->stream));
+        SUR_CK(s, conv::conv_bgrad(32, dz, s->gb[l], s->gpart, s->V, s->stream));
         if (l > 0) {
             SUR_CK(s, conv_fwd(s, 32, 32, 2, dz, s->wb[l], nullptr, s->A[l - 1], s->dZ[1 - cur]));
             cur = 1 - cur;
@@ -250,6 +252,8 @@ rkl_status rkl_sur_create(int D, int H, int W, const double* dx, void* cuda_stre
     if ((c = cudaMalloc(&s->M0, (size_t)V * 4)) != cudaSuccess) return bail(c, "M0");
     if ((c = cudaMalloc(&s->Mp, (size_t)V * 4)) != cudaSuccess) return bail(c, "Mp");
     if ((c = cudaMalloc(&s->d_part, sizeof(double) * 2 * kPartials)) != cudaSuccess) return bail(c, "partials");
+    const size_t gpart = std::max(conv::wgrad_workspace_floats(), (size_t)conv::kBgradBlocks * 32);
+    if ((c = cudaMalloc(&s->gpart, sizeof(float) * gpart)) != cudaSuccess) return bail(c, "gradient partials");
     if ((c = cudaMalloc(&s->d_tcst, sizeof(unsigned))) != cudaSuccess) return bail(c, "status");
     if ((c = cudaMemsetAsync(s->d_tcst, 0, sizeof(unsigned), s->stream)) != cudaSuccess) return bail(c, "status");
     if ((c = cudaMallocHost(&s->h_part, sizeof(double) * 2 * kPartials)) != cudaSuccess) return bail(c, "partials");
@@ -275,6 +279,7 @@ rkl_status rkl_sur_destroy(rkl_surrogate* s)
     cudaFree(s->dZ[0]); cudaFree(s->dZ[1]);
     cudaFree(s->Yp); cudaFree(s->M0); cudaFree(s->Mp);
     cudaFree(s->d_part);
+    cudaFree(s->gpart);
     cudaFree(s->d_tcst);
     if (s->h_part) cudaFreeHost(s->h_part);
     delete s;
@@ -382,6 +387,32 @@ rkl_status rkl_sur_train_step(rkl_surrogate* s, double head_scale, const void* t
     st = backward_impl(s, static_cast<const float*>(target), loss);
     if (st != RKL_OK) return st;
     return rkl_sur_adam(s, lr, 0.9, 0.999, 1e-8);
+}
+
+rkl_status rkl_sur_layer_forward(rkl_surrogate* s, int layer, const void* in, void* out)
+{
+    if (!s || layer < 0 || layer >= kLayers || !in || !out) return RKL_ERR_INVALID_ARG;
+    const int mode = layer == kLayers - 1 ? 1 : 0;
+    SUR_CK(s, conv_fwd(s, kCin[layer], kCout[layer], mode, in, s->wf[layer], s->b[layer], nullptr, out));
+    return RKL_OK;
+}
+
+rkl_status rkl_sur_layer_backward_data(rkl_surrogate* s, int layer, const void* dz, const void* mask, void* out)
+{
+    if (!s || layer < 1 || layer >= kLayers || !dz || !mask || !out) return RKL_ERR_INVALID_ARG;
+    SUR_CK(s, conv_fwd(s, kCout[layer], kCin[layer], 2, dz, s->wb[layer], nullptr, mask, out));
+    return RKL_OK;
+}
+
+rkl_status rkl_sur_layer_weight_grad(rkl_surrogate* s, int layer, const void* dz, const void* x)
+{
+    if (!s || layer < 0 || layer >= kLayers || !dz || !x) return RKL_ERR_INVALID_ARG;
+    SUR_CK(s, cudaMemsetAsync(s->gw[layer], 0, sizeof(float) * wcount(layer), s->stream));
+    SUR_CK(s, cudaMemsetAsync(s->gb[layer], 0, sizeof(float) * kCout[layer], s->stream));
+    SUR_CK(s, conv::conv_wgrad(kCin[layer], kCout[layer], dz, x, s->gw[layer], s->gpart, s->D, s->H, s->W,
+                               s->stream));
+    SUR_CK(s, conv::conv_bgrad(kCout[layer], dz, s->gb[layer], s->gpart, s->V, s->stream));
+    return RKL_OK;
 }
 
 rkl_status rkl_sur_super_step(rkl_surrogate* s, rkl_plan* plan, double dt, void* T, const void* b,

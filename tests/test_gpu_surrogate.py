@@ -3,13 +3,22 @@ forward increments, loss, every layer's weight and bias gradients, one
 Adam step; exact conservation of the flux-form head; the accept and
 fallback branches of the surrogate super-step.
 
-BF16 weights and activations (8-bit mantissa, relative rounding 2^-9 per
-stored value, accumulated over six layers forward and five BF16 gradient
-layers backward, then differenced by the flux-form divergence) bound the
-agreement with FP64: the increment within 5e-2 relative L2 and cosine
-0.998 (measured 1.8e-2, 0.99985), weight and bias gradients within 1e-1
-relative L2 and cosine 0.995 (measured 3e-2 to 6e-2, cosine >= 0.998 on
-the deepest layer); the errors are printed."""
+Tolerances.  The network keeps its inputs, weights, hidden activations
+and back-propagated gradients in BF16 (8 significant bits).  What that
+storage costs on a given input is a property of the arithmetic, not of the
+kernels: the oracle measures it by running in FP64 with every stored value
+rounded to BF16 (``store=round_bf16``) and comparing with its plain FP64
+run; call that gap g.  The GPU rounds at the same points, so it differs
+from the BF16-storage oracle only where its FP32 accumulation order moves a
+value across a BF16 rounding boundary: a K-term FP32 dot product is off by
+about sqrt(K) 2^-24 of its value (K = 27 x 32 = 864), i.e. P = sqrt(K)
+2^-16 of a BF16 unit in the last place, so a fraction P of the stored
+values flip by one unit, against the uniformly distributed rounding error
+(rms one unit / sqrt(12)) behind g.  The GPU's distance to the BF16-storage
+oracle is then about sqrt(12 P) g = 0.074 g; the tests allow LAMBDA = 4 times
+that, and g (1 + LAMBDA sqrt(12 P)) against the plain FP64 oracle.  The
+kernels' indexing is checked separately with zero tolerance on exactly
+representable operands (test_gpu_surrogate_exact.py)."""
 import numpy as np
 import pytest
 
@@ -21,6 +30,15 @@ pytestmark = pytest.mark.gpu
 
 REAL_IN = 6      # used input channels of layer 0
 REAL_OUT = 3     # used output channels of layer 5
+
+P_FLIP = np.sqrt(27 * 32) * 2.0 ** -16       # FP32 accumulation error in BF16 units
+FLIP = np.sqrt(12 * P_FLIP)                  # flips' rms against BF16 rounding's rms
+LAMBDA = 4.0
+
+
+def _bounds(gap):
+    """(allowed distance to the BF16-storage oracle, to the FP64 oracle)."""
+    return LAMBDA * FLIP * gap, gap * (1 + LAMBDA * FLIP)
 
 
 @pytest.fixture(scope="module")
@@ -91,10 +109,15 @@ def test_forward_matches_oracle_and_conserves(rk):
     torch.cuda.synchronize()
     x = S.features(T, b, kappa0, True, ratio)
     ref, _ = S.forward(_oracle_params(params), x, hs, dx)
+    ref16, _ = S.forward(_oracle_params(params), x, hs, dx, store=S.round_bf16)
     got = host(dT)
+    gap = _stats(ref16, ref)[0]
+    to16, to64 = _bounds(gap)
+    rl2_16, _ = _stats(got, ref16)
     rl2, cos = _stats(got, ref)
-    print(f"surrogate forward: rel-L2 {rl2:.3e}, cosine {cos:.6f}")
-    assert rl2 < 5e-2 and cos > 0.998
+    print(f"surrogate forward: BF16 storage gap {gap:.3e}; GPU vs BF16-storage oracle {rl2_16:.3e} "
+          f"(bound {to16:.3e}), vs FP64 oracle {rl2:.3e} (bound {to64:.3e}), cosine {cos:.6f}")
+    assert rl2_16 < to16 and rl2 < to64
     # flux form: the increment sums to zero
     assert abs(got.sum()) <= 1e-5 * np.abs(got).sum()
     rk._lib.rkl_sur_destroy(sur)
@@ -111,22 +134,33 @@ def test_gradients_match_oracle(rk):
     rk._lib.rkl_sur_forward(sur, hs)
     loss = rk._lib.rkl_sur_backward(sur, torch_dev(target))
     x = S.features(T, b, kappa0, True, ratio)
-    loss_ref, grads, _ = S.loss_and_grad(_oracle_params(params), x, target.astype(np.float32).astype(np.float64),
-                                         hs, dx)
-    print(f"surrogate loss {loss:.6e} oracle {loss_ref:.6e}")
-    assert loss == pytest.approx(loss_ref, rel=2e-2)
+    tgt = target.astype(np.float32).astype(np.float64)
+    loss_ref, grads, _ = S.loss_and_grad(_oracle_params(params), x, tgt, hs, dx)
+    loss16, grads16, _ = S.loss_and_grad(_oracle_params(params), x, tgt, hs, dx, store=S.round_bf16)
+    lgap = abs(loss16 - loss_ref) / loss_ref
+    print(f"surrogate loss {loss:.6e} oracle {loss_ref:.6e} BF16-storage oracle {loss16:.6e}")
+    assert abs(loss - loss16) / loss16 <= LAMBDA * FLIP * lgap + 1e-6
+    assert abs(loss - loss_ref) / loss_ref <= lgap * (1 + LAMBDA * FLIP) + 1e-6
     for l in range(6):
         gw, gb = rk._lib.rkl_sur_get_grads(sur, l)
         co, ci = gw.shape[1], gw.shape[2]
         gw_or = gw.astype(np.float64).transpose(1, 2, 0).reshape(co, ci, 3, 3, 3)
         rci = REAL_IN if l == 0 else ci
         rco = REAL_OUT if l == 5 else co
+        gap = _stats(grads16[l][0], grads[l][0])[0]
+        to16, to64 = _bounds(gap)
+        rl2_16 = _stats(gw_or[:rco, :rci], grads16[l][0])[0]
         rl2, cos = _stats(gw_or[:rco, :rci], grads[l][0])
-        rlb, cosb = _stats(gb[:rco], grads[l][1])
-        print(f"layer {l}: dW rel-L2 {rl2:.3e} cos {cos:.6f}; db rel-L2 {rlb:.3e} cos {cosb:.6f}")
-        assert rl2 < 1e-1 and cos > 0.995, l
+        print(f"layer {l}: dW BF16 gap {gap:.3e}; GPU vs BF16-storage oracle {rl2_16:.3e} (bound {to16:.3e}), "
+              f"vs FP64 {rl2:.3e} (bound {to64:.3e}) cos {cos:.6f}")
+        assert rl2_16 < to16 and rl2 < to64, l
         if l < 5:
-            assert rlb < 1e-1 and cosb > 0.995, l
+            gapb = _stats(grads16[l][1], grads[l][1])[0]
+            b16, b64 = _bounds(gapb)
+            rlb16 = _stats(gb[:rco], grads16[l][1])[0]
+            rlb = _stats(gb[:rco], grads[l][1])[0]
+            print(f"layer {l}: db BF16 gap {gapb:.3e}; vs BF16-storage {rlb16:.3e}, vs FP64 {rlb:.3e}")
+            assert rlb16 < b16 and rlb < b64, l
         else:
             # a constant face flux has no divergence: the head's bias gradient
             # is exactly zero (the adjoint telescopes); only rounding remains
@@ -216,8 +250,10 @@ def test_tcgen05_backend_matches_warp_mma_and_oracle(rk):
     assert rl2 < 1e-2 and cos > 0.9999
     x = S.features(T, b, kappa0, True, ratio)
     ref, _ = S.forward(_oracle_params(params), x, hs, dx)
-    rl2, cos = _stats(out[1], ref)
-    assert rl2 < 5e-2 and cos > 0.998
+    ref16, _ = S.forward(_oracle_params(params), x, hs, dx, store=S.round_bf16)
+    to16, to64 = _bounds(_stats(ref16, ref)[0])
+    for backend in (0, 1):
+        assert _stats(out[backend], ref16)[0] < to16 and _stats(out[backend], ref)[0] < to64, backend
     assert abs(out[1].sum()) <= 1e-5 * np.abs(out[1]).sum()
     # backward with tcgen05 backward-data against the oracle's gradients
     rng = np.random.default_rng(5)
@@ -227,15 +263,20 @@ def test_tcgen05_backend_matches_warp_mma_and_oracle(rk):
     rk._lib.rkl_sur_forward(sur, hs)
     rk._lib.rkl_sur_backward(sur, torch_dev(target))
     rk._lib.rkl_sur_check(sur)
-    _, grads, _ = S.loss_and_grad(_oracle_params(params), x, target.astype(np.float32).astype(np.float64), hs, dx)
+    tgt = target.astype(np.float32).astype(np.float64)
+    _, grads, _ = S.loss_and_grad(_oracle_params(params), x, tgt, hs, dx)
+    _, grads16, _ = S.loss_and_grad(_oracle_params(params), x, tgt, hs, dx, store=S.round_bf16)
     for l in range(5):
         gw, gb = rk._lib.rkl_sur_get_grads(sur, l)
         co, ci = gw.shape[1], gw.shape[2]
         gw_or = gw.astype(np.float64).transpose(1, 2, 0).reshape(co, ci, 3, 3, 3)
         rci = REAL_IN if l == 0 else ci
+        to16, to64 = _bounds(_stats(grads16[l][0], grads[l][0])[0])
+        rl2_16 = _stats(gw_or[:, :rci], grads16[l][0])[0]
         rl2, cos = _stats(gw_or[:, :rci], grads[l][0])
-        print(f"tcgen05 backward layer {l}: dW rel-L2 {rl2:.3e} cos {cos:.6f}")
-        assert rl2 < 1e-1 and cos > 0.995, l
+        print(f"tcgen05 backward layer {l}: dW vs BF16-storage {rl2_16:.3e} (bound {to16:.3e}), "
+              f"vs FP64 {rl2:.3e} (bound {to64:.3e}) cos {cos:.6f}")
+        assert rl2_16 < to16 and rl2 < to64, l
     rk._lib.rkl_sur_destroy(sur)
 
 

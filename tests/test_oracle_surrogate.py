@@ -102,3 +102,37 @@ def test_adam_first_step_closed_form():
     # bias-corrected m/sqrt(v) = g/|g| on the first step
     assert np.allclose(p1, p - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-12)
     assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_round_bf16_against_torch_and_ties():
+    """round_bf16 against torch's FP32 -> BF16 conversion (round to nearest
+    even) on FP32 values, where one rounding from FP64 and torch's agree,
+    and on hand-made ties."""
+    import torch
+    from oracle.surrogate import round_bf16
+    rng = np.random.default_rng(0)
+    x32 = np.concatenate([rng.normal(size=20000), rng.normal(size=2000) * 1e-30, rng.normal(size=2000) * 1e30,
+                          [0.0, -0.0, 1.0, -2.5]]).astype(np.float32)
+    want = torch.from_numpy(x32).to(torch.bfloat16).float().numpy().astype(np.float64)
+    assert np.array_equal(round_bf16(x32.astype(np.float64)), want)
+    # ties: 1 + 2^-8 lies halfway between 1 and 1 + 2^-7 (even: 1);
+    # 1 + 3 2^-8 halfway between 1 + 2^-7 and 1 + 2^-6 (even: 1 + 2^-6)
+    t = np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, -(1 + 2.0 ** -8), 1 + 2.0 ** -8 + 2.0 ** -40])
+    assert list(round_bf16(t)) == [1.0, 1 + 2.0 ** -6, -1.0, 1 + 2.0 ** -7]
+    y = round_bf16(rng.normal(size=1000))
+    assert np.array_equal(round_bf16(y), y)
+
+
+def test_bf16_storage_emulation_reduces_to_rounded_operands():
+    """One linear layer: storing in BF16 is the FP64 convolution of the
+    rounded input and weights (the store points are exactly those)."""
+    from oracle.surrogate import round_bf16
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(3, 4, 4, 8))
+    w = rng.normal(size=(3, 3, 3, 3, 3)) * 0.2
+    b = rng.normal(size=3)
+    got, _ = S.forward([(w, b)], x, 1.0, (1.0, 1.0, 1.0), store=round_bf16)
+    want, _ = S.forward([(round_bf16(w), b)], round_bf16(x), 1.0, (1.0, 1.0, 1.0))
+    assert np.array_equal(got, want)
+    plain, _ = S.forward([(w, b)], x, 1.0, (1.0, 1.0, 1.0))
+    assert 0 < np.abs(got - plain).max() < 1e-2 * np.abs(plain).max()
