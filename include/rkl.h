@@ -442,6 +442,20 @@ rkl_status rkl_sur_features(rkl_surrogate *sur, const void *T, const void *b, do
  * patch allows it.  Weight gradients use the warp-level kernel either way.
  */
 rkl_status rkl_sur_set_backend(rkl_surrogate *sur, int backend);
+/*
+ * The input features with three more channels (6, 7, 8): flux_scale times
+ * the face fluxes F_x, F_y, F_z of T (Eqs. Fclass, qN, qT, Fsat as the
+ * plan evaluates them, rkl_flux: the flux on face i + 1/2 stored at i).
+ * T's flux carries the field-aligned product b (b . grad T) that a ReLU
+ * network would otherwise have to learn; the kappa model is the plan's.
+ * The plan must describe the surrogate's periodic 3D FP32 patch.
+ */
+rkl_status rkl_sur_features_flux(rkl_surrogate *sur, rkl_plan *plan, const void *T, const void *b,
+                                 double ratio, double flux_scale);
+/* c > 0: rkl_sur_super_step builds its features with rkl_sur_features_flux
+ * and flux_scale = c dt / head_scale (dt: the super-step); c = 0 (the
+ * default): rkl_sur_features */
+rkl_status rkl_sur_set_flux_features(rkl_surrogate *sur, double c);
 /* waits for the stream; RKL_ERR_TIMEOUT if a tcgen05 kernel's bounded wait
  * gave up since the last check (the word is then cleared) */
 rkl_status rkl_sur_check(rkl_surrogate *sur);

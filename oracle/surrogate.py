@@ -81,11 +81,15 @@ def _identity(a):
     return a
 
 
-def features(T, b, kappa0, spitzer, ratio):
+def features(T, b, kappa0, spitzer, ratio, flux=None):
     """Network input channels [6][z][y][x]: T - 1, b_x, b_y, b_z,
-    log10(kappa_par(T) / 0.01), (dt / dt_expl) / 100."""
+    log10(kappa_par(T) / 0.01), (dt / dt_expl) / 100; with flux ([3][z][y]
+    [x], the face fluxes of T already scaled) three more channels."""
     kap = kappa0 * T ** 2.5 if spitzer else np.full_like(T, kappa0)
-    return np.stack([T - 1.0, b[0], b[1], b[2], np.log10(kap) + 2.0, np.full_like(T, ratio / 100.0)])
+    ch = [T - 1.0, b[0], b[1], b[2], np.log10(kap) + 2.0, np.full_like(T, ratio / 100.0)]
+    if flux is not None:
+        ch += [flux[0], flux[1], flux[2]]
+    return np.stack(ch)
 
 
 def flux_divergence(G, tau, dx):

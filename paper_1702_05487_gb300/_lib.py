@@ -109,6 +109,8 @@ SIGNATURES = {
     "rkl_sur_train_step": (ctypes.c_int, [_vp, ctypes.c_double, _vp, ctypes.c_double, _dp]),
     "rkl_sur_super_step": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, ctypes.c_double, ctypes.c_double,
                                           _ip, _dp, _ip]),
+    "rkl_sur_features_flux": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double]),
+    "rkl_sur_set_flux_features": (ctypes.c_int, [_vp, ctypes.c_double]),
     "rkl_sur_layer_forward": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "rkl_sur_layer_backward_data": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
     "rkl_sur_layer_weight_grad": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
@@ -437,6 +439,17 @@ def rkl_sur_layer_weight_grad(sur, layer, dz, x):
 
 def rkl_sur_features(sur, T, b, kappa_par0, spitzer, ratio):
     _scheck(load().rkl_sur_features(sur, _ptr(T), _ptr(b), float(kappa_par0), int(bool(spitzer)), float(ratio)), sur)
+
+
+def rkl_sur_features_flux(sur, plan, T, b, ratio, flux_scale):
+    """Features with flux_scale times T's face fluxes (as the plan evaluates
+    them) in channels 6, 7, 8."""
+    _scheck(load().rkl_sur_features_flux(sur, plan, _ptr(T), _ptr(b), float(ratio), float(flux_scale)), sur)
+
+
+def rkl_sur_set_flux_features(sur, c):
+    """c > 0: rkl_sur_super_step uses flux features scaled by c dt / head_scale."""
+    _scheck(load().rkl_sur_set_flux_features(sur, float(c)), sur)
 
 
 def rkl_sur_set_backend(sur, backend: int):

@@ -288,10 +288,12 @@ wgrad_kernel(const __nv_bfloat16* __restrict__ dz, const __nv_bfloat16* __restri
 }
 
 // --------------------------------------------------------------------------
-// Surrogate input features (channels last, 16 channels, 6 used):
-//   T - 1, b_x, b_y, b_z, log10(kappa_par(T) / 0.01), dt/dt_expl / 100.
+// Surrogate input features (channels last, 16 channels, 6 or 9 used):
+//   T - 1, b_x, b_y, b_z, log10(kappa_par(T) / 0.01), dt/dt_expl / 100, and
+//   with F (face fluxes of T, [3][V]) fscale * F_x, F_y, F_z.
 __global__ void features_kernel(const float* __restrict__ T, const float* __restrict__ b, int64_t V, float kappa0,
-                                int spitzer, float ratio, __nv_bfloat16* __restrict__ X)
+                                int spitzer, float ratio, const float* __restrict__ F, float fscale,
+                                __nv_bfloat16* __restrict__ X)
 {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
         const float t = T[v];
@@ -305,6 +307,11 @@ __global__ void features_kernel(const float* __restrict__ T, const float* __rest
         f[3] = b[2 * V + v];
         f[4] = log10f(kap) + 2.f;
         f[5] = ratio * 0.01f;
+        if (F) {
+            f[6] = fscale * F[v];
+            f[7] = fscale * F[V + v];
+            f[8] = fscale * F[2 * V + v];
+        }
         __nv_bfloat162* out = reinterpret_cast<__nv_bfloat162*>(X + v * 16);
 #pragma unroll
         for (int c = 0; c < 8; ++c) out[c] = __floats2bfloat162_rn(f[2 * c], f[2 * c + 1]);
@@ -483,10 +490,11 @@ cudaError_t conv_forward(int cin, int cout, int mode, const void* in, const void
 
 static int grid_for(int64_t n) { return (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096); }
 
-cudaError_t features(const float* T, const float* b, int64_t V, float kappa0, int spitzer, float ratio, void* X,
-                     cudaStream_t st)
+cudaError_t features(const float* T, const float* b, int64_t V, float kappa0, int spitzer, float ratio, const float* F,
+                     float fscale, void* X, cudaStream_t st)
 {
-    features_kernel<<<grid_for(V), 256, 0, st>>>(T, b, V, kappa0, spitzer, ratio, static_cast<__nv_bfloat16*>(X));
+    features_kernel<<<grid_for(V), 256, 0, st>>>(T, b, V, kappa0, spitzer, ratio, F, fscale,
+                                                 static_cast<__nv_bfloat16*>(X));
     return cudaGetLastError();
 }
 

@@ -32,8 +32,8 @@ cudaError_t conv_wgrad(int cin, int cout, const void* dz, const void* x, float* 
 constexpr int kBgradBlocks = 304;
 cudaError_t conv_bgrad(int c, const void* dz, float* db, float* part, int64_t V, cudaStream_t st);
 
-cudaError_t features(const float* T, const float* b, int64_t V, float kappa0, int spitzer, float ratio, void* X,
-                     cudaStream_t st);
+cudaError_t features(const float* T, const float* b, int64_t V, float kappa0, int spitzer, float ratio, const float* F,
+                     float fscale, void* X, cudaStream_t st);
 cudaError_t head_div(const float* G, int D, int H, int W, float tau, const float inv_dx[3], float* dT,
                      cudaStream_t st);
 cudaError_t loss_and_adjoint(const float* dT, const float* target, int D, int H, int W, float tau,

@@ -94,6 +94,8 @@ struct rkl_surrogate {
     void* dG = nullptr;            // bf16 [V][16]
     void* dZ[2] = {};              // bf16 [V][32]
     float* gpart = nullptr;        // per-CTA partial weight / bias gradients (fixed-order sums)
+    float* F3 = nullptr;           // f32 [3][V] face fluxes of T (flux features)
+    double flux_c = 0.0;           // > 0: rkl_sur_super_step feeds flux features, scale flux_c dt / head_scale
     float* Yp = nullptr;
     float* M0 = nullptr;
     float* Mp = nullptr;
@@ -251,6 +253,7 @@ rkl_status rkl_sur_create(int D, int H, int W, const double* dx, void* cuda_stre
     if ((c = cudaMalloc(&s->Yp, (size_t)V * 4)) != cudaSuccess) return bail(c, "Yp");
     if ((c = cudaMalloc(&s->M0, (size_t)V * 4)) != cudaSuccess) return bail(c, "M0");
     if ((c = cudaMalloc(&s->Mp, (size_t)V * 4)) != cudaSuccess) return bail(c, "Mp");
+    if ((c = cudaMalloc(&s->F3, (size_t)V * 12)) != cudaSuccess) return bail(c, "flux features");
     if ((c = cudaMalloc(&s->d_part, sizeof(double) * 2 * kPartials)) != cudaSuccess) return bail(c, "partials");
     const size_t gpart = std::max(conv::wgrad_workspace_floats(), (size_t)conv::kBgradBlocks * 32);
     if ((c = cudaMalloc(&s->gpart, sizeof(float) * gpart)) != cudaSuccess) return bail(c, "gradient partials");
@@ -277,7 +280,7 @@ rkl_status rkl_sur_destroy(rkl_surrogate* s)
     for (int l = 0; l < kLayers - 1; ++l) cudaFree(s->A[l]);
     cudaFree(s->G); cudaFree(s->dT); cudaFree(s->r); cudaFree(s->dG);
     cudaFree(s->dZ[0]); cudaFree(s->dZ[1]);
-    cudaFree(s->Yp); cudaFree(s->M0); cudaFree(s->Mp);
+    cudaFree(s->Yp); cudaFree(s->M0); cudaFree(s->Mp); cudaFree(s->F3);
     cudaFree(s->d_part);
     cudaFree(s->gpart);
     cudaFree(s->d_tcst);
@@ -322,8 +325,43 @@ rkl_status rkl_sur_features(rkl_surrogate* s, const void* T, const void* b, doub
     if (!s || !T || !b) return RKL_ERR_INVALID_ARG;
     if (!(kappa0 > 0.0) || !(ratio > 0.0)) return sfail(s, RKL_ERR_INVALID_ARG, "kappa0 and ratio must be > 0");
     SUR_CK(s, conv::features(static_cast<const float*>(T), static_cast<const float*>(b), s->V, (float)kappa0,
-                             spitzer ? 1 : 0, (float)ratio, s->X0, s->stream));
+                             spitzer ? 1 : 0, (float)ratio, nullptr, 0.f, s->X0, s->stream));
     s->forward_done = false;
+    return RKL_OK;
+}
+
+namespace {
+rkl_status check_patch_plan(rkl_surrogate* s, rkl_plan* plan)
+{
+    const rkl_grid& g = *plan_grid(plan);
+    if (g.ndim != 3 || g.dtype != RKL_F32 || g.bc != RKL_PERIODIC || g.n[0] != s->W || g.n[1] != s->H ||
+        g.n[2] != s->D)
+        return sfail(s, RKL_ERR_INVALID_ARG, "plan must be the surrogate's periodic 3D FP32 patch");
+    return RKL_OK;
+}
+}  // namespace
+
+rkl_status rkl_sur_features_flux(rkl_surrogate* s, rkl_plan* plan, const void* T, const void* b, double ratio,
+                                 double flux_scale)
+{
+    if (!s || !plan || !T || !b) return RKL_ERR_INVALID_ARG;
+    if (!(ratio > 0.0) || !std::isfinite(flux_scale)) return sfail(s, RKL_ERR_INVALID_ARG, "bad ratio or scale");
+    rkl_status st = check_patch_plan(s, plan);
+    if (st != RKL_OK) return st;
+    const rkl_phys& ph = *plan_phys(plan);
+    st = rkl_flux(plan, T, b, s->F3, s->F3 + s->V, s->F3 + 2 * s->V);
+    if (st != RKL_OK) return sfail(s, st, "flux of the plan failed");
+    SUR_CK(s, conv::features(static_cast<const float*>(T), static_cast<const float*>(b), s->V, (float)ph.kappa_par0,
+                             ph.kappa_model == RKL_KAPPA_SPITZER ? 1 : 0, (float)ratio, s->F3, (float)flux_scale,
+                             s->X0, s->stream));
+    s->forward_done = false;
+    return RKL_OK;
+}
+
+rkl_status rkl_sur_set_flux_features(rkl_surrogate* s, double c)
+{
+    if (!s || !(c >= 0.0) || !std::isfinite(c)) return RKL_ERR_INVALID_ARG;
+    s->flux_c = c;
     return RKL_OK;
 }
 
@@ -419,15 +457,18 @@ rkl_status rkl_sur_super_step(rkl_surrogate* s, rkl_plan* plan, double dt, void*
                               double head_scale, double threshold, int* accepted, double* residual, int* s_used)
 {
     if (!s || !plan || !T || !b || !accepted) return RKL_ERR_INVALID_ARG;
-    const rkl_grid& g = *plan_grid(plan);
     const rkl_phys& ph = *plan_phys(plan);
-    if (g.ndim != 3 || g.dtype != RKL_F32 || g.bc != RKL_PERIODIC || g.n[0] != s->W || g.n[1] != s->H ||
-        g.n[2] != s->D)
-        return sfail(s, RKL_ERR_INVALID_ARG, "plan must be the surrogate's periodic 3D FP32 patch");
-    double dte = 0.0;
-    rkl_status st = rkl_dt_expl(plan, T, &dte);
+    rkl_status st = check_patch_plan(s, plan);
     if (st != RKL_OK) return st;
-    st = rkl_sur_features(s, T, b, ph.kappa_par0, ph.kappa_model == RKL_KAPPA_SPITZER, dt / dte);
+    double dte = 0.0;
+    st = rkl_dt_expl(plan, T, &dte);
+    if (st != RKL_OK) return st;
+    if (s->flux_c > 0.0 && !(head_scale > 0.0))
+        return sfail(s, RKL_ERR_INVALID_ARG, "flux features need head_scale > 0");
+    if (s->flux_c > 0.0)
+        st = rkl_sur_features_flux(s, plan, T, b, dt / dte, s->flux_c * dt / head_scale);
+    else
+        st = rkl_sur_features(s, T, b, ph.kappa_par0, ph.kappa_model == RKL_KAPPA_SPITZER, dt / dte);
     if (st != RKL_OK) return st;
     st = forward_impl(s, head_scale);
     if (st != RKL_OK) return st;

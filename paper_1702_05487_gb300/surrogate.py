@@ -57,6 +57,7 @@ class SurrogateConfig:
     kappa_perp_ratio: float = 1e-4
     lr: float = 2e-3
     head_scale: float = 0.0           # 0: set from the first targets
+    flux_c: float = 0.0625            # > 0: flux features scaled by flux_c dt / head_scale (0: none)
 
 
 @dataclass
@@ -73,6 +74,7 @@ class Surrogate:
         self.handle = _lib.rkl_sur_create(n, n, n, self.dx, self.stream.cuda_stream)
         self.rng = np.random.default_rng(self.cfg.seed0)
         self._init_params()
+        _lib.rkl_sur_set_flux_features(self.handle, self.cfg.flux_c)
         pool_T, pool_b = [], []
         for k in range(self.cfg.pool):
             T, b = workloads.tangled_box(n, n, n, self.cfg.seed0 + k)
@@ -85,7 +87,7 @@ class Surrogate:
     def _init_params(self):
         for l in range(6):
             co, ci = _lib.rkl_sur_layer_shape(l)
-            rci = 6 if l == 0 else ci
+            rci = (9 if self.cfg.flux_c > 0 else 6) if l == 0 else ci
             rco = 3 if l == 5 else co
             w = np.zeros((27, co, ci), dtype=np.float32)
             scale = math.sqrt(2.0 / (27 * rci)) * (0.1 if l == 5 else 1.0)
@@ -130,25 +132,47 @@ class Surrogate:
             if self.cfg.head_scale <= 0.0:
                 rms = float(target.double().pow(2).mean().sqrt())
                 self.cfg.head_scale = rms * self.dx[0]
-            _lib.rkl_sur_features(self.handle, T0, b, kappa0, True, ratio)
+            self._features(T0, b, kappa0, ratio, dt)
             lr = self.cfg.lr * (0.5 * (1 + math.cos(math.pi * i / max(1, n_pairs))) * 0.9 + 0.1)
             losses.append(_lib.rkl_sur_train_step(self.handle, self.cfg.head_scale, target, lr))
             if log_every and (i + 1) % log_every == 0:
                 print(f"pair {i + 1}/{n_pairs}: loss {np.mean(losses[-log_every:]):.4e}", flush=True)
         return losses
 
+    def _features(self, T0, b, kappa0, ratio, dt):
+        if self.cfg.flux_c > 0.0:
+            _lib.rkl_sur_features_flux(self.handle, self.plan(kappa0).handle, T0, b, ratio,
+                                       self.cfg.flux_c * dt / self.cfg.head_scale)
+        else:
+            _lib.rkl_sur_features(self.handle, T0, b, kappa0, True, ratio)
+
     def predict(self, T0, b, kappa0, ratio):
         import torch
         dT = torch.empty_like(T0)
-        _lib.rkl_sur_features(self.handle, T0, b, kappa0, True, ratio)
+        dt = ratio * self.plan(kappa0).dt_expl(T0)
+        self._features(T0, b, kappa0, ratio, dt)
         _lib.rkl_sur_forward(self.handle, self.cfg.head_scale, dT)
         return dT
 
+    def heldout_pool(self, count=4):
+        """Tangled-field patches of seeds the training pool does not use."""
+        import torch
+        import workloads
+        n = self.cfg.n
+        out = []
+        for k in range(count):
+            T, b = workloads.tangled_box(n, n, n, self.cfg.seed0 + 2000 + k)
+            out.append((torch.from_numpy(T.astype(np.float32)).cuda(), torch.from_numpy(b.astype(np.float32)).cuda()))
+        return out
+
     def calibrate(self, n_pairs, accuracy=1e-3):
-        """Held-out pairs: the true state error ||T_pred - T_rkl2|| / ||T_rkl2||
-        and the residual of each prediction; the threshold is the largest
-        residual below which every held-out prediction met `accuracy`."""
+        """Held-out pairs (fields outside the training pool, their own seeded
+        draws): the true state error ||T_pred - T_rkl2|| / ||T_rkl2|| and the
+        residual of each prediction; the threshold is the largest residual
+        below which every held-out prediction met `accuracy`."""
         rows = []
+        train_pool, train_rng = self.pool, self.rng
+        self.pool, self.rng = self.heldout_pool(), np.random.default_rng(self.cfg.seed0 + 3000)
         for _ in range(n_pairs):
             T0, b, kappa0, ratio, dt, target = self.draw()
             plan = self.plan(kappa0)
@@ -158,6 +182,7 @@ class Surrogate:
             Tt = T0 + target
             err = float((Tp - Tt).double().norm() / Tt.double().norm())
             rows.append((rho, err))
+        self.pool, self.rng = train_pool, train_rng
         rows.sort()
         thr = 0.0
         for rho, err in rows:
@@ -167,12 +192,17 @@ class Surrogate:
         self.threshold = thr
         return thr, rows
 
-    def time_to_solution(self, n_steps, kappa0=0.01, ratio=100.0, pool_index=0, accuracy=1e-3):
-        """n_steps super-steps from one held-out field, plain RKL2 against the
-        surrogate with fallback; wall times on the GPU (CUDA events) and the
-        surrogate run's final relative L2 error against the plain run."""
+    def time_to_solution(self, n_steps, kappa0=0.01, ratio=100.0, seed=None, accuracy=1e-3):
+        """n_steps super-steps from one held-out field (tangled-field seed
+        outside the training pool; default seed0 + 1000), plain RKL2 against
+        the surrogate with fallback; wall times on the GPU (CUDA events) and
+        the surrogate run's final relative L2 error against the plain run."""
         import torch
-        T0, b = self.pool[pool_index]
+        import workloads
+        n = self.cfg.n
+        Th, bh = workloads.tangled_box(n, n, n, self.cfg.seed0 + 1000 if seed is None else seed)
+        T0 = torch.from_numpy(Th.astype(np.float32)).cuda()
+        b = torch.from_numpy(bh.astype(np.float32)).cuda()
         plan = self.plan(kappa0)
         dt = ratio * plan.dt_expl(T0)
         thr = self.threshold if self.threshold is not None else 0.0

@@ -9,14 +9,19 @@ storage costs on a given input is a property of the arithmetic, not of the
 kernels: the oracle measures it by running in FP64 with every stored value
 rounded to BF16 (``store=round_bf16``) and comparing with its plain FP64
 run; call that gap g.  The GPU rounds at the same points, so it differs
-from the BF16-storage oracle only where its FP32 accumulation order moves a
-value across a BF16 rounding boundary: a K-term FP32 dot product is off by
-about sqrt(K) 2^-24 of its value (K = 27 x 32 = 864), i.e. P = sqrt(K)
-2^-16 of a BF16 unit in the last place, so a fraction P of the stored
-values flip by one unit, against the uniformly distributed rounding error
-(rms one unit / sqrt(12)) behind g.  The GPU's distance to the BF16-storage
-oracle is then about sqrt(12 P) g = 0.074 g; the tests allow LAMBDA = 4 times
-that, and g (1 + LAMBDA sqrt(12 P)) against the plain FP64 oracle.  The
+from the BF16-storage oracle only where its FP32 accumulation moves a value
+across a BF16 rounding boundary.  Tensor cores add the products of each
+K = 16 step with truncated alignment, so one step can lose up to 2^-23 of
+the magnitudes it adds, with a bias that makes the losses add up: a dot
+product of n steps is off by at most n 2^-23 sum|w x| = n 2^-23 c |z|,
+c the conditioning sum|w x| / |sum w x| of that layer's dot products, which
+the oracle computes on the same input.  A stored value therefore crosses a
+rounding boundary with probability P = n c 2^-23 / 2^-8 (its position
+inside a BF16 unit is uniform) and then moves by one unit, against the
+uniformly distributed rounding error (rms one unit / sqrt(12)) behind g:
+the GPU's distance to the BF16-storage oracle is about sqrt(12 P) g, its
+distance to the FP64 oracle about g (1 + sqrt(12 P)).  The tests allow
+LAMBDA = 2 times the flip term (P from the worst-conditioned layer).  The
 kernels' indexing is checked separately with zero tolerance on exactly
 representable operands (test_gpu_surrogate_exact.py)."""
 import numpy as np
@@ -31,14 +36,42 @@ pytestmark = pytest.mark.gpu
 REAL_IN = 6      # used input channels of layer 0
 REAL_OUT = 3     # used output channels of layer 5
 
-P_FLIP = np.sqrt(27 * 32) * 2.0 ** -16       # FP32 accumulation error in BF16 units
-FLIP = np.sqrt(12 * P_FLIP)                  # flips' rms against BF16 rounding's rms
-LAMBDA = 4.0
+LAMBDA = 2.0
 
 
-def _bounds(gap):
+def _cond(a_abs, a):
+    return float(np.linalg.norm(a_abs.ravel()) / max(np.linalg.norm(a.ravel()), 1e-300))
+
+
+def _flip(params, x, hs, dx, target=None):
+    """sqrt(12 P) for the worst-conditioned stored dot product of the BF16
+    network's forward (and, with a target, backward-data) convolutions on
+    this input: P = n c 2^-15, n the K = 16 steps of a dot product."""
+    st = S.round_bf16
+    h = st(x)
+    pre, conds = [], []
+    for li, (w, b) in enumerate(params):
+        ws = st(w)
+        z = S.conv3d(h, ws, b)
+        conds.append((27 * h.shape[0] / 16, _cond(S.conv3d(np.abs(h), np.abs(ws), np.abs(b)), z)))
+        pre.append(z)
+        h = st(np.maximum(z, 0.0)) if li < len(params) - 1 else z
+    if target is not None:
+        r = S.flux_divergence(h, hs, dx) - target
+        g = st(S.flux_divergence_adjoint(r / r.size, hs, dx))
+        for li in range(len(params) - 1, 0, -1):
+            ws = st(params[li][0])
+            m = pre[li - 1] > 0.0
+            gi = S.conv3d_grad_input(g, ws) * m
+            conds.append((27 * g.shape[0] / 16, _cond(S.conv3d_grad_input(np.abs(g), np.abs(ws)) * m, gi)))
+            g = st(gi)
+    P = min(1.0, max(n * c for n, c in conds) * 2.0 ** -15)
+    return float(np.sqrt(12.0 * P))
+
+
+def _bounds(gap, flip):
     """(allowed distance to the BF16-storage oracle, to the FP64 oracle)."""
-    return LAMBDA * FLIP * gap, gap * (1 + LAMBDA * FLIP)
+    return LAMBDA * flip * gap, gap * (1 + LAMBDA * flip)
 
 
 @pytest.fixture(scope="module")
@@ -51,12 +84,12 @@ def rk():
     return rk
 
 
-def _init_params(rk, seed=0):
+def _init_params(rk, seed=0, real_in=REAL_IN):
     rng = np.random.default_rng(seed)
     params = []
     for l in range(6):
         co, ci = rk._lib.rkl_sur_layer_shape(l)
-        rci = REAL_IN if l == 0 else ci
+        rci = real_in if l == 0 else ci
         rco = REAL_OUT if l == 5 else co
         w = np.zeros((27, co, ci), dtype=np.float32)
         w[:, :rco, :rci] = rng.normal(scale=np.sqrt(2.0 / (27 * rci)), size=(27, rco, rci))
@@ -66,12 +99,12 @@ def _init_params(rk, seed=0):
     return params
 
 
-def _oracle_params(params):
+def _oracle_params(params, real_in=REAL_IN):
     out = []
     for l, (w, b) in enumerate(params):
         co, ci = w.shape[1], w.shape[2]
         wo = w.astype(np.float64).transpose(1, 2, 0).reshape(co, ci, 3, 3, 3)
-        rci = REAL_IN if l == 0 else ci
+        rci = real_in if l == 0 else ci
         rco = REAL_OUT if l == 5 else co
         out.append((wo[:rco, :rci], b.astype(np.float64)[:rco]))
     return out
@@ -112,14 +145,55 @@ def test_forward_matches_oracle_and_conserves(rk):
     ref16, _ = S.forward(_oracle_params(params), x, hs, dx, store=S.round_bf16)
     got = host(dT)
     gap = _stats(ref16, ref)[0]
-    to16, to64 = _bounds(gap)
+    flip = _flip(_oracle_params(params), x, hs, dx)
+    to16, to64 = _bounds(gap, flip)
     rl2_16, _ = _stats(got, ref16)
     rl2, cos = _stats(got, ref)
-    print(f"surrogate forward: BF16 storage gap {gap:.3e}; GPU vs BF16-storage oracle {rl2_16:.3e} "
+    print(f"surrogate forward: BF16 storage gap {gap:.3e}, flip factor {flip:.3f}; "
+          f"GPU vs BF16-storage oracle {rl2_16:.3e} "
           f"(bound {to16:.3e}), vs FP64 oracle {rl2:.3e} (bound {to64:.3e}), cosine {cos:.6f}")
     assert rl2_16 < to16 and rl2 < to64
     # flux form: the increment sums to zero
     assert abs(got.sum()) <= 1e-5 * np.abs(got).sum()
+    rk._lib.rkl_sur_destroy(sur)
+
+
+def test_forward_with_flux_features_matches_oracle(rk, orc):
+    """Channels 6-8 carry the scaled face fluxes of T as the plan evaluates
+    them (Eqs. Fclass, qN, qT); the forward pass on these nine features
+    against the oracle's forward on its own FP64 fluxes."""
+    import torch
+    from oracle import Problem
+    sur, params, T, b, Td, bd, dx = _setup(rk)
+    params = _init_params(rk, seed=4, real_in=9)
+    for l, (w, bb) in enumerate(params):
+        rk._lib.rkl_sur_set_params(sur, l, w, bb)
+    shape = T.shape
+    prm = dict(dx=dx, kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
+    plan = rk.Plan(shape, "f32", params=prm)
+    ratio, hs, fscale = 100.0, 2e-3, 300.0      # flux channels of rms about 1
+    rk._lib.rkl_sur_features_flux(sur, plan.handle, Td, bd, ratio, fscale)
+    dT = torch.empty_like(Td)
+    rk._lib.rkl_sur_forward(sur, hs, dT)
+    torch.cuda.synchronize()
+    F = [fscale * f for f in orc.flux(Problem(shape, **prm), T, b)]
+    x = S.features(T, b, 0.01, True, ratio, flux=F)
+    op = _oracle_params(params, 9)
+    ref, _ = S.forward(op, x, hs, dx)
+    ref16, _ = S.forward(op, x, hs, dx, store=S.round_bf16)
+    gap = _stats(ref16, ref)[0]
+    to16, to64 = _bounds(gap, _flip(op, x, hs, dx))
+    got = host(dT)
+    rl2_16, rl2 = _stats(got, ref16)[0], _stats(got, ref)[0]
+    print(f"flux features: BF16 gap {gap:.3e}; GPU vs BF16-storage oracle {rl2_16:.3e} (bound {to16:.3e}), "
+          f"vs FP64 {rl2:.3e} (bound {to64:.3e})")
+    assert rl2_16 < to16 and rl2 < to64
+    # without the flux channels the same network sees zeros there: a different output
+    rk._lib.rkl_sur_features(sur, Td, bd, 0.01, True, ratio)
+    dT0 = torch.empty_like(Td)
+    rk._lib.rkl_sur_forward(sur, hs, dT0)
+    assert _stats(host(dT0), got)[0] > 10 * to16
+    plan.close()
     rk._lib.rkl_sur_destroy(sur)
 
 
@@ -137,10 +211,19 @@ def test_gradients_match_oracle(rk):
     tgt = target.astype(np.float32).astype(np.float64)
     loss_ref, grads, _ = S.loss_and_grad(_oracle_params(params), x, tgt, hs, dx)
     loss16, grads16, _ = S.loss_and_grad(_oracle_params(params), x, tgt, hs, dx, store=S.round_bf16)
-    lgap = abs(loss16 - loss_ref) / loss_ref
-    print(f"surrogate loss {loss:.6e} oracle {loss_ref:.6e} BF16-storage oracle {loss16:.6e}")
-    assert abs(loss - loss16) / loss16 <= LAMBDA * FLIP * lgap + 1e-6
-    assert abs(loss - loss_ref) / loss_ref <= lgap * (1 + LAMBDA * FLIP) + 1e-6
+    flip = _flip(_oracle_params(params), x, hs, dx, tgt)
+    # the loss 0.5 mean(r^2) moves by at most |r - r16| (|r| + |r16|) / (2 n)
+    # when dT does, and dT's distance to the BF16-storage oracle is bounded
+    # as in the forward test
+    dT16, _ = S.forward(_oracle_params(params), x, hs, dx, store=S.round_bf16)
+    dT64, _ = S.forward(_oracle_params(params), x, hs, dx)
+    to16, _ = _bounds(_stats(dT16, dT64)[0], flip)
+    r16 = dT16 - tgt
+    dr = to16 * np.linalg.norm(dT16)
+    lbound = dr * (2 * np.linalg.norm(r16) + dr) / (2 * r16.size)
+    print(f"surrogate loss {loss:.6e} oracle {loss_ref:.6e} BF16-storage oracle {loss16:.6e} "
+          f"(bound on the distance {lbound:.3e}); flip factor {flip:.3f}")
+    assert abs(loss - loss16) <= lbound + 1e-7 * loss16
     for l in range(6):
         gw, gb = rk._lib.rkl_sur_get_grads(sur, l)
         co, ci = gw.shape[1], gw.shape[2]
@@ -148,7 +231,7 @@ def test_gradients_match_oracle(rk):
         rci = REAL_IN if l == 0 else ci
         rco = REAL_OUT if l == 5 else co
         gap = _stats(grads16[l][0], grads[l][0])[0]
-        to16, to64 = _bounds(gap)
+        to16, to64 = _bounds(gap, flip)
         rl2_16 = _stats(gw_or[:rco, :rci], grads16[l][0])[0]
         rl2, cos = _stats(gw_or[:rco, :rci], grads[l][0])
         print(f"layer {l}: dW BF16 gap {gap:.3e}; GPU vs BF16-storage oracle {rl2_16:.3e} (bound {to16:.3e}), "
@@ -156,7 +239,7 @@ def test_gradients_match_oracle(rk):
         assert rl2_16 < to16 and rl2 < to64, l
         if l < 5:
             gapb = _stats(grads16[l][1], grads[l][1])[0]
-            b16, b64 = _bounds(gapb)
+            b16, b64 = _bounds(gapb, flip)
             rlb16 = _stats(gb[:rco], grads16[l][1])[0]
             rlb = _stats(gb[:rco], grads[l][1])[0]
             print(f"layer {l}: db BF16 gap {gapb:.3e}; vs BF16-storage {rlb16:.3e}, vs FP64 {rlb:.3e}")
@@ -251,7 +334,7 @@ def test_tcgen05_backend_matches_warp_mma_and_oracle(rk):
     x = S.features(T, b, kappa0, True, ratio)
     ref, _ = S.forward(_oracle_params(params), x, hs, dx)
     ref16, _ = S.forward(_oracle_params(params), x, hs, dx, store=S.round_bf16)
-    to16, to64 = _bounds(_stats(ref16, ref)[0])
+    to16, to64 = _bounds(_stats(ref16, ref)[0], _flip(_oracle_params(params), x, hs, dx))
     for backend in (0, 1):
         assert _stats(out[backend], ref16)[0] < to16 and _stats(out[backend], ref)[0] < to64, backend
     assert abs(out[1].sum()) <= 1e-5 * np.abs(out[1]).sum()
@@ -266,12 +349,13 @@ def test_tcgen05_backend_matches_warp_mma_and_oracle(rk):
     tgt = target.astype(np.float32).astype(np.float64)
     _, grads, _ = S.loss_and_grad(_oracle_params(params), x, tgt, hs, dx)
     _, grads16, _ = S.loss_and_grad(_oracle_params(params), x, tgt, hs, dx, store=S.round_bf16)
+    flip = _flip(_oracle_params(params), x, hs, dx, tgt)
     for l in range(5):
         gw, gb = rk._lib.rkl_sur_get_grads(sur, l)
         co, ci = gw.shape[1], gw.shape[2]
         gw_or = gw.astype(np.float64).transpose(1, 2, 0).reshape(co, ci, 3, 3, 3)
         rci = REAL_IN if l == 0 else ci
-        to16, to64 = _bounds(_stats(grads16[l][0], grads[l][0])[0])
+        to16, to64 = _bounds(_stats(grads16[l][0], grads[l][0])[0], flip)
         rl2_16 = _stats(gw_or[:, :rci], grads16[l][0])[0]
         rl2, cos = _stats(gw_or[:, :rci], grads[l][0])
         print(f"tcgen05 backward layer {l}: dW vs BF16-storage {rl2_16:.3e} (bound {to16:.3e}), "
