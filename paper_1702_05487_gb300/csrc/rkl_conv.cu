@@ -192,10 +192,13 @@ conv_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restric
 // then stores them to the CTA's own slice of part ([gridDim.x][27][COUT]
 // [CIN]); sum_partials adds the slices to dW in CTA order, so the result
 // does not depend on which CTA finishes first.
+// The bias gradient sum_v dz[v][co] rides along: each thread adds up one
+// channel's values of every staged dz tile (thread t: channel t % COUT),
+// and the CTA stores its per-channel sums to partb[blockIdx.x][COUT].
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(NTHR, 1)
 wgrad_kernel(const __nv_bfloat16* __restrict__ dz, const __nv_bfloat16* __restrict__ x, float* __restrict__ part,
-             int D, int H, int W)
+             float* __restrict__ partb, int D, int H, int W)
 {
     constexpr int SZ = COUT + 8, SXC = CIN + 8;
     constexpr int MT = COUT / 16;                       // m16 tiles over co
@@ -211,6 +214,7 @@ wgrad_kernel(const __nv_bfloat16* __restrict__ dz, const __nv_bfloat16* __restri
     const int tilesx = W / TX, tilesy = H / TY, tilesz = D / TZ;
     const int ntiles = tilesx * tilesy * tilesz;
 
+    float bacc = 0.f;
     float acc[UPW][MT][4];
 #pragma unroll
     for (int i = 0; i < UPW; ++i)
@@ -239,6 +243,8 @@ wgrad_kernel(const __nv_bfloat16* __restrict__ dz, const __nv_bfloat16* __restri
         cp_commit();
         cp_wait_all();
         __syncthreads();
+#pragma unroll 8
+        for (int m = tid / COUT; m < TV; m += NTHR / COUT) bacc += __bfloat162float(sZ[m * SZ + tid % COUT]);
         for (int ks = 0; ks < TV / 16; ++ks) {
             const int v0 = ks * 16;                      // one x-row of the tile
             const int ty = (v0 / TX) % TY, tz = v0 / (TX * TY);
@@ -284,6 +290,16 @@ wgrad_kernel(const __nv_bfloat16* __restrict__ dz, const __nv_bfloat16* __restri
                 float* dst = part + (int64_t)blockIdx.x * (27 * COUT * CIN) + ((int64_t)o * COUT + co) * CIN + ci;
                 *reinterpret_cast<float2*>(dst) = make_float2(acc[i][mt][2 * h], acc[i][mt][2 * h + 1]);
             }
+    }
+    // the bias sums: NTHR / COUT threads per channel, added in thread order
+    __syncthreads();
+    float* red = reinterpret_cast<float*>(smem_raw);
+    red[tid] = bacc;
+    __syncthreads();
+    if (tid < COUT) {
+        float t = 0.f;
+        for (int k = 0; k < NTHR / COUT; ++k) t += red[k * COUT + tid];
+        partb[(int64_t)blockIdx.x * COUT + tid] = t;
     }
 }
 
@@ -409,39 +425,12 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
     }
 }
 
-// bias gradient: block b stores its sum of dz[v][c] over its voxels to
-// part[b][c]; sum_partials adds the blocks' sums to db in block order.
-template <int C>
-__global__ void __launch_bounds__(256) bgrad_kernel(const __nv_bfloat16* __restrict__ dz, float* part, int64_t V)
-{
-    float s[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) s[c] = 0.f;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x)
-#pragma unroll
-        for (int c = 0; c < C; ++c) s[c] += __bfloat162float(dz[v * C + c]);
-    __shared__ float sh[8][C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        float t = s[c];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][c] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x < C) {
-        float t = 0.f;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) t += sh[w][threadIdx.x];
-        part[(int64_t)blockIdx.x * C + threadIdx.x] = t;
-    }
-}
-
 // out[i] += sum over b = 0 .. nparts - 1 of part[b][i], in that order.
 __global__ void sum_partials_kernel(const float* __restrict__ part, int nparts, int n, float* __restrict__ out)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         float t = 0.f;
+#pragma unroll 8
         for (int b = 0; b < nparts; ++b) t += part[(int64_t)b * n + i];
         out[i] += t;
     }
@@ -532,7 +521,7 @@ cudaError_t adam(float* p, const float* g, float* m, float* v, int n, float lr, 
 }
 
 template <int CIN, int COUT>
-static cudaError_t wgrad_t(const void* dz, const void* x, float* dW, float* part, int D, int H, int W,
+static cudaError_t wgrad_t(const void* dz, const void* x, float* dW, float* db, float* part, int D, int H, int W,
                            cudaStream_t st)
 {
     constexpr int SZ = COUT + 8, SXC = CIN + 8;
@@ -546,11 +535,14 @@ static cudaError_t wgrad_t(const void* dz, const void* x, float* dW, float* part
     const int ntiles = (D / TZ) * (H / TY) * (W / TX);
     const int sms = wgrad_max_ctas();
     const int grid = ntiles < sms ? ntiles : sms;
+    float* partb = part + (size_t)grid * 27 * COUT * CIN;
     wgrad_kernel<CIN, COUT><<<grid, NTHR, smem, st>>>(static_cast<const __nv_bfloat16*>(dz),
-                                                     static_cast<const __nv_bfloat16*>(x), part, D, H, W);
+                                                     static_cast<const __nv_bfloat16*>(x), part, partb, D, H, W);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     sum_partials_kernel<<<grid_for(27 * COUT * CIN), 256, 0, st>>>(part, grid, 27 * COUT * CIN, dW);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    sum_partials_kernel<<<1, 32, 0, st>>>(partb, grid, COUT, db);
     return cudaGetLastError();
 }
 
@@ -566,28 +558,18 @@ int wgrad_max_ctas()
     return sms;
 }
 
-size_t wgrad_workspace_floats() { return (size_t)wgrad_max_ctas() * 27 * 32 * 32; }
+size_t wgrad_workspace_floats() { return (size_t)wgrad_max_ctas() * (27 * 32 * 32 + 32); }
 
-cudaError_t conv_wgrad(int cin, int cout, const void* dz, const void* x, float* dW, float* part, int D, int H, int W,
-                       cudaStream_t st)
+cudaError_t conv_wgrad(int cin, int cout, const void* dz, const void* x, float* dW, float* db, float* part, int D,
+                       int H, int W, cudaStream_t st)
 {
     if (D % TZ || H % TY || W % TX) return cudaErrorInvalidValue;
-    if (cin == 16 && cout == 32) return wgrad_t<16, 32>(dz, x, dW, part, D, H, W, st);
-    if (cin == 32 && cout == 32) return wgrad_t<32, 32>(dz, x, dW, part, D, H, W, st);
-    if (cin == 32 && cout == 16) return wgrad_t<32, 16>(dz, x, dW, part, D, H, W, st);
+    if (cin == 16 && cout == 32) return wgrad_t<16, 32>(dz, x, dW, db, part, D, H, W, st);
+    if (cin == 32 && cout == 32) return wgrad_t<32, 32>(dz, x, dW, db, part, D, H, W, st);
+    if (cin == 32 && cout == 16) return wgrad_t<32, 16>(dz, x, dW, db, part, D, H, W, st);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t conv_bgrad(int c, const void* dz, float* db, float* part, int64_t V, cudaStream_t st)
-{
-    if (c == 32) bgrad_kernel<32><<<kBgradBlocks, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(dz), part, V);
-    else if (c == 16) bgrad_kernel<16><<<kBgradBlocks, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(dz), part, V);
-    else return cudaErrorInvalidValue;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    sum_partials_kernel<<<1, 32, 0, st>>>(part, kBgradBlocks, c, db);
-    return cudaGetLastError();
-}
 
 }  // namespace conv
 }  // namespace rkl

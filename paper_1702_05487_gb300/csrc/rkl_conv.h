@@ -19,18 +19,15 @@ cudaError_t conv_forward(int cin, int cout, int mode, const void* in, const void
 cudaError_t conv_forward_tc(int cin, int cout, int mode, const void* in, const void* wt, const float* bias,
                             const void* mask, void* out, int D, int H, int W, int nzc, unsigned* status,
                             cudaStream_t st);
-// dW[27][cout][cin] += sum_v dz[v][cout] x[v + off][cin]; (cin, cout) in
-// {(16,32), (32,32), (32,16)}.  Each CTA writes its partial sums to its own
-// slice of part (wgrad_workspace_floats() floats), which are then added to
-// dW in a fixed order: the result is the same from run to run.
+// dW[27][cout][cin] += sum_v dz[v][cout] x[v + off][cin] and db[cout] +=
+// sum_v dz[v][cout]; (cin, cout) in {(16,32), (32,32), (32,16)}.  Each CTA
+// writes its partial sums to its own slice of part
+// (wgrad_workspace_floats() floats), which are then added to dW and db in
+// a fixed order: the result is the same from run to run.
 int wgrad_max_ctas();
 size_t wgrad_workspace_floats();
-cudaError_t conv_wgrad(int cin, int cout, const void* dz, const void* x, float* dW, float* part, int D, int H, int W,
-                       cudaStream_t st);
-// db[c] += sum_v dz[v][c]; c in {16, 32}; part holds kBgradBlocks * 32
-// floats (per-block sums, added in block order).
-constexpr int kBgradBlocks = 304;
-cudaError_t conv_bgrad(int c, const void* dz, float* db, float* part, int64_t V, cudaStream_t st);
+cudaError_t conv_wgrad(int cin, int cout, const void* dz, const void* x, float* dW, float* db, float* part, int D,
+                       int H, int W, cudaStream_t st);
 
 cudaError_t features(const float* T, const float* b, int64_t V, float kappa0, int spitzer, float ratio, const float* F,
                      float fscale, void* X, cudaStream_t st);

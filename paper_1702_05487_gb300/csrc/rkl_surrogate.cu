@@ -162,15 +162,13 @@ rkl_status backward_impl(rkl_surrogate* s, const float* target, double* loss)
     }
     // head
     const void* dz = s->dG;
-    SUR_CK(s, conv::conv_wgrad(32, 16, dz, s->A[4], s->gw[5], s->gpart, D, H, W, s->stream));
-    SUR_CK(s, conv::conv_bgrad(16, dz, s->gb[5], s->gpart, s->V, s->stream));
+    SUR_CK(s, conv::conv_wgrad(32, 16, dz, s->A[4], s->gw[5], s->gb[5], s->gpart, D, H, W, s->stream));
     SUR_CK(s, conv_fwd(s, 16, 32, 2, dz, s->wb[5], nullptr, s->A[4], s->dZ[0]));
     int cur = 0;
     for (int l = kLayers - 2; l >= 0; --l) {
         dz = s->dZ[cur];
         const void* x = l > 0 ? s->A[l - 1] : s->X0;
-        SUR_CK(s, conv::conv_wgrad(kCin[l], 32, dz, x, s->gw[l], s->gpart, D, H, W, s->stream));
-        SUR_CK(s, conv::conv_bgrad(32, dz, s->gb[l], s->gpart, s->V, s->stream));
+        SUR_CK(s, conv::conv_wgrad(kCin[l], 32, dz, x, s->gw[l], s->gb[l], s->gpart, D, H, W, s->stream));
         if (l > 0) {
             SUR_CK(s, conv_fwd(s, 32, 32, 2, dz, s->wb[l], nullptr, s->A[l - 1], s->dZ[1 - cur]));
             cur = 1 - cur;
@@ -255,8 +253,8 @@ rkl_status rkl_sur_create(int D, int H, int W, const double* dx, void* cuda_stre
     if ((c = cudaMalloc(&s->Mp, (size_t)V * 4)) != cudaSuccess) return bail(c, "Mp");
     if ((c = cudaMalloc(&s->F3, (size_t)V * 12)) != cudaSuccess) return bail(c, "flux features");
     if ((c = cudaMalloc(&s->d_part, sizeof(double) * 2 * kPartials)) != cudaSuccess) return bail(c, "partials");
-    const size_t gpart = std::max(conv::wgrad_workspace_floats(), (size_t)conv::kBgradBlocks * 32);
-    if ((c = cudaMalloc(&s->gpart, sizeof(float) * gpart)) != cudaSuccess) return bail(c, "gradient partials");
+    if ((c = cudaMalloc(&s->gpart, sizeof(float) * conv::wgrad_workspace_floats())) != cudaSuccess)
+        return bail(c, "gradient partials");
     if ((c = cudaMalloc(&s->d_tcst, sizeof(unsigned))) != cudaSuccess) return bail(c, "status");
     if ((c = cudaMemsetAsync(s->d_tcst, 0, sizeof(unsigned), s->stream)) != cudaSuccess) return bail(c, "status");
     if ((c = cudaMallocHost(&s->h_part, sizeof(double) * 2 * kPartials)) != cudaSuccess) return bail(c, "partials");
@@ -447,9 +445,8 @@ rkl_status rkl_sur_layer_weight_grad(rkl_surrogate* s, int layer, const void* dz
     if (!s || layer < 0 || layer >= kLayers || !dz || !x) return RKL_ERR_INVALID_ARG;
     SUR_CK(s, cudaMemsetAsync(s->gw[layer], 0, sizeof(float) * wcount(layer), s->stream));
     SUR_CK(s, cudaMemsetAsync(s->gb[layer], 0, sizeof(float) * kCout[layer], s->stream));
-    SUR_CK(s, conv::conv_wgrad(kCin[layer], kCout[layer], dz, x, s->gw[layer], s->gpart, s->D, s->H, s->W,
-                               s->stream));
-    SUR_CK(s, conv::conv_bgrad(kCout[layer], dz, s->gb[layer], s->gpart, s->V, s->stream));
+    SUR_CK(s, conv::conv_wgrad(kCin[layer], kCout[layer], dz, x, s->gw[layer], s->gb[layer], s->gpart, s->D, s->H,
+                               s->W, s->stream));
     return RKL_OK;
 }
 
