@@ -264,7 +264,11 @@ rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
  * periodic grids with nx >= 72, else as 3), 7 = the paired-cell kernel with
  * the Y0 / Y_{j-2} / M(Y0) bundles of stages j >= 2 copied by the TMA engine
  * from tensor maps (cp.async.bulk.tensor, one issuing thread; as 3 where the
- * driver offers no tensor-map encoder).  With the MC limiter at every face
+ * driver offers no tensor-map encoder), 8 = the paired-cell kernel with
+ * every plane bundle (T and b with their halo ring, Y0, Y_{j-2}, M(Y0))
+ * copied by the TMA engine from tensor maps, the periodic images at the
+ * grid's edges patched in by a few threads (periodic grids with nx >= 72
+ * and ny >= 6, no limiter; else as 3).  With the MC limiter at every face
  * (limiter_floor = +inf) variants 3, 4, 6 and 7 all launch the paired-cell
  * kernel's limited build (20 resident warps per SM, per-thread copies);
  * with a finite floor the paired-cell variants do not apply.

@@ -222,9 +222,9 @@ rkl_status launch_stage(rkl_plan* p, const StageIO& io, double mu, double nu, do
         KCoef<float> cf{(float)mu, (float)nu, (float)mt, (float)gt};
         bool al = aligned16(io.Y0) && aligned16(io.MY0) && aligned16(io.Yjm1) && aligned16(io.Yjm2) &&
                   aligned16(io.Yj) && aligned16(io.b);
-        if (p->x2ok && al && (p->variant == 0 || (p->variant >= 3 && p->variant <= 7)))
+        if (p->x2ok && al && (p->variant == 0 || (p->variant >= 3 && p->variant <= 8)))
             e = launch_stage_x2(p->cfg, p->gf, p->pf, io, cf, p->d_status, p->nzchunk,
-                                p->variant == 4 ? 3 : 2, st, p->variant == 6, p->variant == 7);
+                                p->variant == 4 ? 3 : 2, st, p->variant == 6, p->variant == 7, p->variant == 8);
         else if (p->fast && al && (p->variant == 0 || p->variant == 2))
             e = launch_stage_fast(p->cfg, p->gf, p->pf, io, cf, p->d_status, st);
         else
@@ -880,6 +880,8 @@ rkl_status rkl_plan_autotune(rkl_plan* p, double dt, const void* T, const void* 
     if (p->x2ok && !lim && p->gf.bc == 0 && p->gf.n[0] >= 72)
         for (int nz : {0, 32}) cands.push_back({6, nz});
     if (p->x2ok && !lim && x2_ytma_supported(p->cfg, p->gf)) cands.push_back({7, 0});
+    if (p->x2ok && x2_tmaps_supported(p->cfg, p->gf))
+        for (int nz : {0, -1, 32}) cands.push_back({8, nz});
     void* scratch = nullptr;
     RKL_CK(p, cudaMalloc(&scratch, (size_t)p->ncell * p->esize));
     cudaEvent_t a = nullptr, e = nullptr;
@@ -922,10 +924,10 @@ rkl_status rkl_plan_autotune(rkl_plan* p, double dt, const void* T, const void* 
 rkl_status rkl_plan_set_variant(rkl_plan* p, int variant, int nzchunk)
 {
     if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
-    if (variant < 0 || variant > 7) return fail(p, RKL_ERR_INVALID_ARG, "variant must be 0 to 7");
+    if (variant < 0 || variant > 8) return fail(p, RKL_ERR_INVALID_ARG, "variant must be 0 to 8");
     if (nzchunk > 4096) return fail(p, RKL_ERR_INVALID_ARG, "nzchunk must be <= 4096");
     if (variant == 2 && !p->fast) return fail(p, RKL_ERR_UNSUPPORTED, "no tiled kernel for this grid");
-    if ((variant == 3 || variant == 4 || variant == 6 || variant == 7) && !p->x2ok)
+    if ((variant == 3 || variant == 4 || variant == 6 || variant == 7 || variant == 8) && !p->x2ok)
         return fail(p, RKL_ERR_UNSUPPORTED, "no paired-cell kernel for this grid");
     if (variant == 5 && !(p->pairok && p->x2ok))
         return fail(p, RKL_ERR_UNSUPPORTED, "no two-stage kernel for this grid (periodic FP32 3D, nx % 4 == 0)");

@@ -66,9 +66,13 @@ bool x2_bulk_supported(const LaunchCfg& c, const KGrid<float>& g);
 // the TMA engine from tensor maps (cp.async.bulk.tensor, one thread, mbarrier
 // completion) instead of per-thread 16-byte copies.
 bool x2_ytma_supported(const LaunchCfg& c, const KGrid<float>& g);
+// With tmaps every plane bundle is copied by the TMA engine from tensor maps
+// (periodic, nx >= 72, ny >= 6, no limiter); the zero-filled periodic images
+// at the grid's edges are patched by per-thread 16-byte chunks.
+bool x2_tmaps_supported(const LaunchCfg& c, const KGrid<float>& g);
 cudaError_t launch_stage_x2(const LaunchCfg& c, const KGrid<float>& g, const KPhys<float>& p, const StageIO& io,
                             const KCoef<float>& coef, unsigned* status, int nzchunk, int occupancy,
-                            cudaStream_t st, bool bulk = false, bool ytma = false);
+                            cudaStream_t st, bool bulk = false, bool ytma = false, bool tmaps = false);
 
 // Two-stage paired-cell FP32 3D kernel: stages j (io, coefficients at
 // io.coef_tab[4 j]) and j + 1 (written to Yj1) in one pass, 60 x 7 tiles of

@@ -14,11 +14,11 @@ namespace {
 template <int OCC, bool BULK>
 cudaError_t launch_phys(const LaunchCfg& c, int mode, const KGrid<float>& g, const KPhys<float>& p,
                         const x2::FastArgs& a, const KCoef<float>& cf, unsigned* status, int nzchunk, cudaStream_t st,
-                        const x2::YMaps* ym = nullptr)
+                        const x2::YMaps* ym = nullptr, const x2::TMaps* tm = nullptr)
 {
-    if (c.saturate) return launch_x2_sat(c.spitzer, OCC, BULK, mode, g, p, a, cf, status, nzchunk, st, ym);
-    if (c.spitzer) return launch_mode<true, false, OCC, BULK>(mode, g, p, a, cf, status, nzchunk, st, ym);
-    return launch_mode<false, false, OCC, BULK>(mode, g, p, a, cf, status, nzchunk, st, ym);
+    if (c.saturate) return launch_x2_sat(c.spitzer, OCC, BULK, mode, g, p, a, cf, status, nzchunk, st, ym, tm);
+    if (c.spitzer) return launch_mode<true, false, OCC, BULK>(mode, g, p, a, cf, status, nzchunk, st, ym, tm);
+    return launch_mode<false, false, OCC, BULK>(mode, g, p, a, cf, status, nzchunk, st, ym, tm);
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
@@ -54,6 +54,22 @@ bool encode_ymap(CUtensorMap* m, const void* base, const KGrid<float>& g)
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tensor map of one grid-sized FP32 array with boxes of a tile's rows and
+// their halo ring: SXS x (TY + 2) x 1 (columns from i0 - 4, rows from
+// j0 - 1; cells outside the grid are filled with zeros).
+bool encode_halo_map(CUtensorMap* m, const void* base, const KGrid<float>& g)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || !base) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.n[0] * 4u, (cuuint64_t)g.n[0] * (cuuint64_t)g.n[1] * 4u};
+    const cuuint32_t box[3] = {(cuuint32_t)x2::SXS, (cuuint32_t)x2::ROWS, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 bool x2_stage_supported(const LaunchCfg& c, const KGrid<float>& g)
@@ -69,6 +85,12 @@ bool x2_bulk_supported(const LaunchCfg& c, const KGrid<float>& g)
 bool x2_ytma_supported(const LaunchCfg& c, const KGrid<float>& g)
 {
     return x2_stage_supported(c, g) && tensor_map_encoder() != nullptr;
+}
+bool x2_tmaps_supported(const LaunchCfg& c, const KGrid<float>& g)
+{
+    // boxes no larger than the grid: nx >= SXS (> TX) and ny >= TY + 2
+    return x2_stage_supported(c, g) && !c.limiter && g.bc == 0 && g.n[0] >= x2::SXS && g.n[1] >= x2::ROWS &&
+           tensor_map_encoder() != nullptr;
 }
 
 // Planes per CTA when none is given: the chunk length in [16, 48] that
@@ -114,7 +136,7 @@ x2::FastArgs x2_args(const StageIO& io)
 
 cudaError_t launch_stage_x2(const LaunchCfg& c, const KGrid<float>& g, const KPhys<float>& p, const StageIO& io,
                             const KCoef<float>& coef, unsigned* status, int nzchunk, int occupancy, cudaStream_t st,
-                            bool bulk, bool ytma)
+                            bool bulk, bool ytma, bool tmaps)
 {
     const x2::FastArgs a = x2_args(io);
     if (c.limiter) {
@@ -127,6 +149,16 @@ cudaError_t launch_stage_x2(const LaunchCfg& c, const KGrid<float>& g, const KPh
     else if (nzchunk < 0) nzchunk = 0;
     if (occupancy == 3) return launch_phys<3, false>(c, io.mode, g, p, a, coef, status, nzchunk, st);
     if (bulk && x2_bulk_supported(c, g)) return launch_phys<2, true>(c, io.mode, g, p, a, coef, status, nzchunk, st);
+    if (tmaps && x2_tmaps_supported(c, g)) {
+        x2::TMaps tm{};
+        if (!encode_halo_map(&tm.m[0], a.Tin, g) || !encode_halo_map(&tm.m[1], a.b, g) ||
+            !encode_halo_map(&tm.m[2], a.b + g.ncell, g) || !encode_halo_map(&tm.m[3], a.b + 2 * g.ncell, g))
+            return cudaErrorInvalidValue;
+        if (io.mode == 2 && (!encode_ymap(&tm.m[4], io.Y0, g) || !encode_ymap(&tm.m[5], io.Yjm2, g) ||
+                             !encode_ymap(&tm.m[6], io.MY0, g)))
+            return cudaErrorInvalidValue;
+        return launch_phys<2, false>(c, io.mode, g, p, a, coef, status, nzchunk, st, nullptr, &tm);
+    }
     if (ytma && io.mode == 2 && x2_ytma_supported(c, g)) {
         x2::YMaps ym;
         if (!encode_ymap(&ym.m[0], io.Y0, g) || !encode_ymap(&ym.m[1], io.Yjm2, g) ||

@@ -20,6 +20,9 @@ constexpr int SXS = 72;                 // smem row: halo chunk (4), 64 interior
 constexpr int CPR = SXS / 4;            // 16-byte chunks per smem row
 constexpr int ROWS = TY + 2;
 constexpr int PLANE = ROWS * SXS;
+// plane stride of the rings whose slots tensor copies fill: a multiple of
+// 128 bytes (a tensor copy's shared-memory destination is 128-byte aligned)
+constexpr int PSTR = (PLANE + 31) / 32 * 32;
 
 struct FastArgs {
     const float* Tin;       // field whose M is taken (Y_{j-1}, or Y_0 at stage 1)
@@ -36,11 +39,12 @@ struct FastArgs {
 // Plane rings for a prefetch distance of PD planes: while plane q is
 // computed, planes q+1 .. q+PD are in flight and plane q+PD+1 is being
 // issued into the slots that plane q-2 (T) or q-1 (b, Y) released.
-template <int PD>
+template <int PD, int PS = PLANE>
 struct SmemT {
     static constexpr int NT = 3 + PD, NB = 2 + PD, NY = 2 + PD;
-    float T[NT][PLANE];             // Y_{j-1} planes q-1, q, q+1 and those in flight
-    float B[NB][3][PLANE];          // b planes q, q+1 and those in flight
+    static constexpr int PSTRIDE = PS;          // floats from one ring slot to the next
+    alignas(128) float T[NT][PS];   // Y_{j-1} planes q-1, q, q+1 and those in flight
+    float B[NB][3][PS];             // b planes q, q+1 and those in flight
     alignas(128) float Y[NY][3][TY * TX];   // Y0, Y_{j-2}, M(Y0) of plane q and those in flight
     float Fy[2][TY + 1][TX];        // y-face fluxes (row 0: the tile's lower boundary)
     float FxLo[2][TY];              // x-faces on the tile's left boundary
@@ -52,6 +56,14 @@ struct SmemT {
 // the variant whose Y bundles the TMA engine copies (cp.async.bulk.tensor).
 struct YMaps {
     CUtensorMap m[3];
+};
+
+// Tensor maps of every bundle for the variant whose plane bundles all come
+// from the TMA engine: T (Y_{j-1}) and bx, by, bz with boxes of SXS x
+// (TY + 2) x 1 (a tile's rows with their one-cell halo ring, columns from
+// i0 - 4), then Y0, Y_{j-2}, M(Y0) with boxes of TX x TY x 1.
+struct TMaps {
+    CUtensorMap m[7];
 };
 constexpr int kPD = 2;              // prefetch distance of the default build
 using Smem = SmemT<kPD>;

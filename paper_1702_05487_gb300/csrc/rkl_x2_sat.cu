@@ -7,7 +7,7 @@ namespace rkl {
 
 cudaError_t launch_x2_sat(bool spitzer, int occ, bool bulk, int mode, const KGrid<float>& g, const KPhys<float>& p,
                           const x2::FastArgs& a, const KCoef<float>& cf, unsigned* status, int nzchunk,
-                          cudaStream_t st, const x2::YMaps* ym)
+                          cudaStream_t st, const x2::YMaps* ym, const x2::TMaps* tm)
 {
     if (occ == 3) {
         if (spitzer) return launch_mode<true, true, 3, false>(mode, g, p, a, cf, status, nzchunk, st);
@@ -17,8 +17,8 @@ cudaError_t launch_x2_sat(bool spitzer, int occ, bool bulk, int mode, const KGri
         if (spitzer) return launch_mode<true, true, 2, true>(mode, g, p, a, cf, status, nzchunk, st);
         return launch_mode<false, true, 2, true>(mode, g, p, a, cf, status, nzchunk, st);
     }
-    if (spitzer) return launch_mode<true, true, 2, false>(mode, g, p, a, cf, status, nzchunk, st, ym);
-    return launch_mode<false, true, 2, false>(mode, g, p, a, cf, status, nzchunk, st, ym);
+    if (spitzer) return launch_mode<true, true, 2, false>(mode, g, p, a, cf, status, nzchunk, st, ym, tm);
+    return launch_mode<false, true, 2, false>(mode, g, p, a, cf, status, nzchunk, st, ym, tm);
 }
 
 }  // namespace rkl

@@ -357,13 +357,70 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map
         : "memory");
 }
 
+namespace x2 {
+// Tensor-map bundles (TB): the TMA engine fills the halo ring of a tile that
+// touches the grid's edge with zeros where a box leaves the grid; the
+// periodic images of those cells come from per-thread 16-byte chunks, at
+// most one per thread.  For each of T, bx, by, bz: the chunk holding column
+// -1 (x-left edge, i0 == 0) or column nx - i0 (x-right edge) in rows -1 ..
+// TY, and the whole row -1 (y-low edge) or row ny - j0 (y-high edge) except
+// the chunks already listed.  Needs nx > TX and ny > TY (a tile has at most
+// one x edge and one y edge): at most 4 (6 + 17) = 92 chunks, taken by the
+// threads of warps 1 .. 3.
+struct FixTask {
+    const float* src;     // chunk in plane 0 (wrapped coordinates), nullptr: none
+    unsigned dst;         // smem byte address in ring slot 0
+    unsigned bring;       // 1: the chunk belongs to the b ring, 0: to the T ring
+};
+
+template <class SM>
+__device__ __forceinline__ FixTask make_fix(const SM& sm, const KGrid<float>& g, const FastArgs& a, int tid, int i0,
+                                            int j0)
+{
+    FixTask f{nullptr, 0u, 0u};
+    const int nx = g.n[0], ny = g.n[1];
+    const int xl = i0 == 0, xr = nx - i0 <= TX, yl = j0 == 0, yh = ny - j0 <= TY;
+    const int kr = (nx - i0 + 4) / 4;                   // chunk of column nx - i0 (smem column nx - i0 + 4)
+    const int ny_ch = CPR - xl - xr;                    // y-strip chunks not in an x strip
+    const int nxs = (xl + xr) * ROWS, n = nxs + (yl + yh) * ny_ch;
+    // chunks go to warps 1 .. 3 (warp 0 issues the plane's tensor copies)
+    const int t = tid - 32;
+    if (t < 0 || t >= 4 * n) return f;
+    const int arr = t / n, i = t % n;
+    int row, k;
+    if (i < nxs) {
+        row = i % ROWS - 1;
+        k = (i / ROWS == 0 && xl) ? 0 : kr;
+    } else {
+        const int jj = i - nxs;
+        row = (jj / ny_ch == 0 && yl) ? -1 : ny - j0;
+        k = jj % ny_ch + xl;
+        if (xr && k >= kr) ++k;
+    }
+    const int gx = pmod(i0 + 4 * k - 4, nx), gy = pmod(j0 + row, ny);
+    const float* base = arr == 0 ? a.Tin : a.b + (int64_t)(arr - 1) * g.ncell;
+    f.src = base + (int64_t)gy * nx + gx;
+    f.dst = arr == 0 ? smem_u32(&sm.T[0][(row + 1) * SXS + 4 * k]) : smem_u32(&sm.B[0][arr - 1][(row + 1) * SXS + 4 * k]);
+    f.bring = arr == 0 ? 0u : 1u;
+    return f;
+}
+}  // namespace x2
+
 // YT: the Y0 / Y_{j-2} / M(Y0) bundle of each plane is one tensor copy per
 // array issued by a single thread (ym: tensor maps in kernel-parameter space)
 // instead of per-thread 16-byte copies; plane q completes on ybar[q & 3].
-template <bool SP, bool SAT, int MODE, int PD, bool BULK = false, bool YT = false, bool LIM = false>
-__device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g, const KPhys<float>& p,
-                                        const x2::FastArgs& a, KCoef<float> cf, unsigned* status, int i0, int j0,
-                                        int z0, int nzc, const x2::YMaps* ym = nullptr)
+// TB: every bundle of each plane (T and b with their halo ring, and the Y
+// arrays) is a tensor copy; lanes 0-6 of warp 0 issue one box each after
+// lane 0 announced the plane's bytes on its barrier, every thread waits for
+// the barrier, and the wrapped halo chunks (make_fix) are stored over the
+// zero fill before the plane's first reader passes the CTA barrier.
+// Periodic grids with nx > TX and ny > TY only.
+template <bool SP, bool SAT, int MODE, int PD, bool BULK = false, bool YT = false, bool LIM = false,
+          bool TB = false>
+__device__ __forceinline__ void tile_x2(x2::SmemT<PD, TB ? x2::PSTR : x2::PLANE>& sm, const KGrid<float>& g,
+                                        const KPhys<float>& p, const x2::FastArgs& a, KCoef<float> cf,
+                                        unsigned* status, int i0, int j0, int z0, int nzc,
+                                        const x2::YMaps* ym = nullptr, const x2::TMaps* tm = nullptr)
 {
     using namespace x2;
     const int tid = threadIdx.x;
@@ -377,11 +434,26 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         cf.mu = t[0]; cf.nu = t[1]; cf.mt = t[2]; cf.gt = t[3];
     }
 
+    static_assert(!(TB && (BULK || YT)), "tensor-map bundles replace the other copy paths");
     constexpr bool kYT = YT && MODE == 2 && !BULK;
-    constexpr int kTk = BULK ? 1 : (kYT ? kSlotY : kSlots);
+    constexpr int kTk = (BULK || TB) ? 1 : (kYT ? kSlotY : kSlots);
     Task tk[kTk];
     RowTask rt{};
-    if constexpr (BULK) {
+    FixTask fx{nullptr, 0u, 0u};
+    float4 fv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (TB) {
+        fx = make_fix(sm, g, a, tid, i0, j0);
+        if (fx.src && (((uintptr_t)fx.src & 15u) != 0u || (fx.dst & 15u) != 0u)) {   // 16-byte chunks only
+            atomicOr(status, ST_TIMEOUT);
+            fx.src = nullptr;
+        }
+        if (tid == 0) {
+#pragma unroll
+            for (int i = 0; i < PD + 2; ++i) mbar_init(smem_u32(&sm.bar[i]), 1u);
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        }
+        __syncthreads();
+    } else if constexpr (BULK) {
         rt = make_rowtask<MODE>(sm, g, a, tid, i0, j0);
         if (tid == 0) {
 #pragma unroll
@@ -408,7 +480,8 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
     const unsigned ybytes =
         MODE == 2 ? 3u * (unsigned)min(TY, ny - j0) * (unsigned)min(TX, nx - i0) * 4u : 0u;
 
-    using SM = SmemT<PD>;
+    using SM = SmemT<PD, TB ? PSTR : PLANE>;
+    constexpr int PS = SM::PSTRIDE;
     // slot of plane q >= -1 in a ring of n (a mask when n is a power of two)
     auto slot = [](int q, int n) { return (n & (n - 1)) == 0 ? (q + 1) & (n - 1) : (q + 1) % n; };
     auto tslot = [&](int q) { return slot(q, SM::NT); };
@@ -420,10 +493,35 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
     const bool plain = g.bc == 0;
     auto load = [&](int q, bool withY) {
         const PlaneOff po = plane_offsets(g, z0 + q);
-        const unsigned ts = (unsigned)(tslot(q) * PLANE * 4);
-        const unsigned bs = (unsigned)(bslot(q) * 3 * PLANE * 4);
+        const unsigned ts = (unsigned)(tslot(q) * PS * 4);
+        const unsigned bs = (unsigned)(bslot(q) * 3 * PS * 4);
         const unsigned ys = (unsigned)(yslot(q) * 3 * TY * TX * 4);
-        if constexpr (BULK) {
+        if constexpr (TB) {
+            if (r == 0) {
+                // only the stages j >= 2 read the Y bundles (and only they
+                // are given the Y tensor maps)
+                const bool ytm = MODE == 2 && withY;
+                const unsigned bar = bar_of(q);
+                if (lane == 0) mbar_expect_tx(bar, 4u * PLANE * 4u + (ytm ? 3u * TY * TX * 4u : 0u));
+                __syncwarp();
+                if (lane < (ytm ? 7 : 4)) {
+                    int kz = z0 + q;                    // periodic: wrap the plane index
+                    kz += kz < 0 ? g.n[2] : 0;
+                    kz -= kz >= g.n[2] ? g.n[2] : 0;
+                    unsigned dst;
+                    if (lane == 0) dst = smem_u32(&sm.T[0][0]) + ts;
+                    else if (lane < 4) dst = smem_u32(&sm.B[0][lane - 1][0]) + bs;
+                    else dst = smem_u32(&sm.Y[0][lane - 4][0]) + ys;
+                    // a tensor copy needs a 128-byte aligned destination: a
+                    // layout that breaks this reports a timeout instead of
+                    // faulting (the plane's barrier then never completes)
+                    if ((dst & 127u) == 0u)
+                        tma_load_3d(dst, &tm->m[lane], lane < 4 ? i0 - 4 : i0, lane < 4 ? j0 - 1 : j0, kz, bar);
+                    else
+                        atomicOr(status, ST_TIMEOUT);
+                }
+            }
+        } else if constexpr (BULK) {
             const unsigned bar = bar_of(q);
             if (tid == 0) mbar_expect_tx(bar, (unsigned)(kRowTB * SXS * 4) + (withY ? ybytes : 0u));
             const unsigned off = (rt.flags & TK_T) ? ts : ((rt.flags & TK_Y) ? ys : bs);
@@ -456,6 +554,22 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         }
     };
 
+    // TB: the wrapped halo chunk of plane q (read in one 16-byte load, stored
+    // over the zero fill once the plane's boxes have landed)
+    auto fix_src = [&](int q) {
+        int kz = z0 + q;
+        kz += kz < 0 ? g.n[2] : 0;
+        kz -= kz >= g.n[2] ? g.n[2] : 0;
+        return reinterpret_cast<const float4*>(fx.src + (int64_t)kz * g.plane);
+    };
+    auto fix_store = [&](int q, float4 v) {
+        const unsigned d = fx.dst + (fx.bring ? (unsigned)(bslot(q) * 3 * PS * 4) : (unsigned)(tslot(q) * PS * 4));
+        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(d), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                     : "memory");
+        // the next box into this slot is written by the async proxy
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    };
+
     // planes -1 .. PD in flight; -1 and 0 must land before the first reads
     load(-1, false);
     cp_commit();
@@ -464,7 +578,19 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         if (k <= nzc) load(k, k < nzc);
         cp_commit();
     }
-    if constexpr (BULK) {
+    if constexpr (TB) {
+        if (fx.src) {
+            const float4 f0 = __ldg(fix_src(-1)), f1 = __ldg(fix_src(0));
+            wait_bundle(-1);
+            wait_bundle(0);
+            fix_store(-1, f0);
+            fix_store(0, f1);
+            if (1 <= nzc) fv = __ldg(fix_src(1));
+        } else {
+            wait_bundle(-1);
+            wait_bundle(0);
+        }
+    } else if constexpr (BULK) {
         wait_bundle(-1);
         wait_bundle(0);
     } else {
@@ -531,8 +657,14 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
 
     // one plane: cur holds plane q, nxt receives plane q + 1
     auto step = [&](int q, QZ& cur, QZ& nxt) {
-        if constexpr (BULK) wait_bundle(q + 1);     // bundle q + 1 has landed
-        else cp_wait<PD - 1>();
+        if constexpr (TB) {
+            wait_bundle(q + 1);                     // bundle q + 1 has landed
+            if (fx.src) fix_store(q + 1, fv);
+        } else if constexpr (BULK) {
+            wait_bundle(q + 1);
+        } else {
+            cp_wait<PD - 1>();
+        }
         if constexpr (kYT) {
             // plane q's Y bundle (read after the barrier); a polling wait,
             // bounded, that records a timeout and lets the tile finish
@@ -547,6 +679,9 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         // the slots of bundle q + PD + 1 held planes no thread reads any more
         if (q + PD + 1 <= nzc) load(q + PD + 1, q + PD + 1 < nzc);
         cp_commit();
+        if constexpr (TB) {
+            if (fx.src && q + 2 <= nzc) fv = __ldg(fix_src(q + 2));
+        }
         if (q > 0) finish(q - 1);
 
         const float2 TmRp = make_float2(TmO.y, TmR);
@@ -613,10 +748,10 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD>& sm, const KGrid<float>& g
         step(q + 1, A, B);
     }
     if (q < nzc) step(q, B, A);
-    if constexpr (!BULK) cp_wait<0>();
+    if constexpr (!BULK && !TB) cp_wait<0>();
     __syncthreads();
     finish(nzc - 1);
-    if constexpr (BULK) {
+    if constexpr (BULK || TB) {
         if (tid == 0) {
 #pragma unroll
             for (int i = 0; i < PD + 2; ++i) mbar_inval(smem_u32(&sm.bar[i]));
@@ -647,20 +782,29 @@ namespace {
 constexpr int ctas_per_sm(int occ) { return occ == 2 ? x2::kCtasPerSm : (occ == 4 ? 5 : 6); }
 constexpr int occ_pd(int occ) { return occ == 3 ? 1 : x2::kPD; }
 
-template <bool SP, bool SAT, int MODE, int OCC, bool BULK, bool YT = false>
+// TB: all bundles copied from tensor maps (maps: x2::TMaps, else x2::YMaps)
+template <bool TB>
+using MapsT = typename std::conditional<TB, x2::TMaps, x2::YMaps>::type;
+
+template <bool SP, bool SAT, int MODE, int OCC, bool BULK, bool YT = false, bool TB = false>
 __global__ void __launch_bounds__(x2::NTHREADS, ctas_per_sm(OCC))
 stage_x2_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf, unsigned* status, int nzchunk,
-                const __grid_constant__ x2::YMaps ym)
+                const __grid_constant__ MapsT<TB> maps)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];     // tensor copies land 128-byte aligned
     constexpr int PD = occ_pd(OCC);
     constexpr bool LIM = OCC == 4;
-    x2::SmemT<PD>& sm = *reinterpret_cast<x2::SmemT<PD>*>(smem_raw);
+    using SMT = x2::SmemT<PD, TB ? x2::PSTR : x2::PLANE>;
+    SMT& sm = *reinterpret_cast<SMT*>(smem_raw);
+    const x2::YMaps* ym = nullptr;
+    const x2::TMaps* tm = nullptr;
+    if constexpr (TB) tm = &maps;
+    else ym = &maps;
     if (nzchunk > 0) {
         // one tile column, one chunk of nzchunk planes per CTA
         const int z0 = blockIdx.z * nzchunk;
-        tile_x2<SP, SAT, MODE, PD, BULK, YT, LIM>(sm, g, p, a, cf, status, blockIdx.x * x2::TX,
-                                                  blockIdx.y * x2::TY, z0, min(nzchunk, g.n[2] - z0), &ym);
+        tile_x2<SP, SAT, MODE, PD, BULK, YT, LIM, TB>(sm, g, p, a, cf, status, blockIdx.x * x2::TX,
+                                                      blockIdx.y * x2::TY, z0, min(nzchunk, g.n[2] - z0), ym, tm);
         return;
     }
     // Balanced schedule: the column-planes (tile column, plane) in column-major
@@ -676,8 +820,8 @@ stage_x2_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf,
         const int64_t col = u / nz;
         const int z0 = (int)(u - col * nz);
         const int nzc = (int)min((int64_t)(nz - z0), u1 - u);
-        tile_x2<SP, SAT, MODE, PD, BULK, YT, LIM>(sm, g, p, a, cf, status, (int)(col % ntx) * x2::TX,
-                                                  (int)(col / ntx) * x2::TY, z0, nzc, &ym);
+        tile_x2<SP, SAT, MODE, PD, BULK, YT, LIM, TB>(sm, g, p, a, cf, status, (int)(col % ntx) * x2::TX,
+                                                      (int)(col / ntx) * x2::TY, z0, nzc, ym, tm);
         u += nzc;
     }
 }
@@ -694,15 +838,15 @@ int sm_count()
     return n;
 }
 
-template <bool SP, bool SAT, int MODE, int OCC, bool BULK, bool YT = false>
+template <bool SP, bool SAT, int MODE, int OCC, bool BULK, bool YT = false, bool TB = false>
 cudaError_t launch3(const KGrid<float>& g, const KPhys<float>& p, const x2::FastArgs& a, const KCoef<float>& cf,
-                    unsigned* status, int nzchunk, cudaStream_t st, const x2::YMaps& ym)
+                    unsigned* status, int nzchunk, cudaStream_t st, const MapsT<TB>& ym)
 {
     constexpr int kCtasPerSm = ctas_per_sm(OCC);
-    const int smem = (int)sizeof(x2::SmemT<occ_pd(OCC)>);
+    const int smem = (int)sizeof(x2::SmemT<occ_pd(OCC), TB ? x2::PSTR : x2::PLANE>);
     static bool attr_set = false;       // the attribute is per function, set once
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(stage_x2_kernel<SP, SAT, MODE, OCC, BULK, YT>,
+        cudaError_t e = cudaFuncSetAttribute(stage_x2_kernel<SP, SAT, MODE, OCC, BULK, YT, TB>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -715,18 +859,27 @@ cudaError_t launch3(const KGrid<float>& g, const KPhys<float>& p, const x2::Fast
         grid = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)kCtasPerSm * sm_count(), U / 8)), 1, 1);
         nzchunk = 0;
     }
-    stage_x2_kernel<SP, SAT, MODE, OCC, BULK, YT><<<grid, x2::NTHREADS, smem, st>>>(g, p, a, cf, status, nzchunk,
-                                                                               ym);
+    stage_x2_kernel<SP, SAT, MODE, OCC, BULK, YT, TB><<<grid, x2::NTHREADS, smem, st>>>(g, p, a, cf, status,
+                                                                                   nzchunk, ym);
     return cudaGetLastError();
 }
 
 // ym: tensor maps of the Y arrays for the stages j >= 2 of the default
-// build (OCC 2, no bulk copies), or nullptr for per-thread Y copies.
+// build (OCC 2, no bulk copies), or nullptr for per-thread Y copies; tm:
+// tensor maps of every bundle (OCC 2, periodic, nx > TX, ny > TY), or
+// nullptr.
 template <bool SP, bool SAT, int OCC, bool BULK>
 cudaError_t launch_mode(int mode, const KGrid<float>& g, const KPhys<float>& p, const x2::FastArgs& a,
                         const KCoef<float>& cf, unsigned* status, int nzchunk, cudaStream_t st,
-                        const x2::YMaps* ym = nullptr)
+                        const x2::YMaps* ym = nullptr, const x2::TMaps* tm = nullptr)
 {
+    if constexpr (OCC == 2 && !BULK) {
+        if (tm) {
+            if (mode == 0) return launch3<SP, SAT, 0, OCC, BULK, false, true>(g, p, a, cf, status, nzchunk, st, *tm);
+            if (mode == 1) return launch3<SP, SAT, 1, OCC, BULK, false, true>(g, p, a, cf, status, nzchunk, st, *tm);
+            return launch3<SP, SAT, 2, OCC, BULK, false, true>(g, p, a, cf, status, nzchunk, st, *tm);
+        }
+    }
     static const x2::YMaps none{};
     if (mode == 0) return launch3<SP, SAT, 0, OCC, BULK>(g, p, a, cf, status, nzchunk, st, none);
     if (mode == 1) return launch3<SP, SAT, 1, OCC, BULK>(g, p, a, cf, status, nzchunk, st, none);
@@ -746,6 +899,6 @@ cudaError_t launch_x2_lim(bool spitzer, bool saturate, int mode, const KGrid<flo
 // The saturated-flux launches (rkl_x2_sat.cu).
 cudaError_t launch_x2_sat(bool spitzer, int occ, bool bulk, int mode, const KGrid<float>& g, const KPhys<float>& p,
                           const x2::FastArgs& a, const KCoef<float>& cf, unsigned* status, int nzchunk,
-                          cudaStream_t st, const x2::YMaps* ym);
+                          cudaStream_t st, const x2::YMaps* ym, const x2::TMaps* tm);
 
 }  // namespace rkl

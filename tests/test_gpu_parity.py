@@ -144,8 +144,8 @@ def _variant_cases():
     # grids with nx % 4 == 0 (the paired-cell kernel) and Dirichlet partial tiles
     spitz = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
     sat = dict(kappa_model="spitzer", kappa_par0=0.01, saturate=True, phi=0.3)
-    for v in (2, 3, 4, 5, 6, 7):
-        if v not in (5, 6):     # the two-stage kernel and bulk copies are periodic only
+    for v in (2, 3, 4, 5, 6, 7, 8):
+        if v not in (5, 6, 8):  # the two-stage kernel, bulk and tensor-map copies are periodic only
             out.append(("3d_x4_dirichlet", (21, 19, 36), dict(spitz, bc="dirichlet", bc_value=0.9), "f32", v))
         out.append(("3d_x4_sat", (18, 26, 68), sat, "f32", v))
         out.append(("3d_x4_sat_upwind", (10, 9, 132), dict(sat, phi=0.05, sat_upwind=True), "f32", v))
@@ -170,6 +170,12 @@ def _variant_cases():
     # bulk (TMA-engine) copies: x-halo rows split at the periodic edge, ragged y
     out.append(("3d_bulk_spitzer", (37, 21, 200), spitz, "f32", 6))
     out.append(("3d_bulk_x72", (9, 16, 72), spitz, "f32", 6))
+    # tensor-map bundles: zero-filled boxes at every edge patched with the
+    # periodic images (ragged x and y tiles; the smallest grid they take,
+    # 72 x 6, with a second tile column of 8 and a tile row of 2)
+    out.append(("3d_tmaps_ragged", (37, 21, 200), spitz, "f32", 8))
+    out.append(("3d_tmaps_thin", (11, 6, 72), spitz, "f32", 8))
+    out.append(("3d_tmaps_sat", (13, 12, 132), sat, "f32", 8))
     return out
 
 
@@ -215,7 +221,7 @@ def test_tiled_kernels_match_generic(rk, orc, shape, nzchunk):
     whose runs cross tile columns) and the generic kernel (variant 1) on
     tile-aligned, ragged and degenerate shapes; all against the oracle."""
     params = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
-    variants = (1, 2, 3, 4, 5, 6) if shape[2] % 4 == 0 else (1, 2)
+    variants = (1, 2, 3, 4, 5, 6, 8) if shape[2] % 4 == 0 else (1, 2)
     res = {}
     for v in variants:
         P, plan, T, b, Td, bd = _setup(rk, "x", shape, params, "f32", v)
