@@ -706,7 +706,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", type=int, default=0,
                     help="stage kernel: 0 auto, 1 generic, 2 tiled, 3/4 paired-cell at 5/6 CTAs per SM, 5 two-stage, "
-                         "6 bulk copies, 7 tensor-map Y copies, 8 every bundle from tensor maps")
+                         "6 bulk copies, 7 tensor-map Y copies, 8 every bundle from tensor maps, "
+                         "9 32-column tiles")
     ap.add_argument("--nzchunk", type=int, default=0, help="planes per CTA (0 automatic, < 0 balanced runs)")
     ap.add_argument("--limiter", default="none", choices=["none", "mc"],
                     help="transverse gradients: plain averages, or MC-limited at every face (Appendix C; "

@@ -268,7 +268,10 @@ rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
  * every plane bundle (T and b with their halo ring, Y0, Y_{j-2}, M(Y0))
  * copied by the TMA engine from tensor maps, the periodic images at the
  * grid's edges patched in by a few threads (periodic grids with nx >= 72
- * and ny >= 6, no limiter; else as 3).  With the MC limiter at every face
+ * and ny >= 6, no limiter; else as 3), 9 = the paired-cell kernel with
+ * tiles 32 columns wide and 8 rows high (two rows of 16 lanes per warp;
+ * for grids whose width is an odd multiple of 32, where 64-column tiles
+ * leave a quarter to a half of the last tile idle; no limiter, else as 3).  With the MC limiter at every face
  * (limiter_floor = +inf) variants 3, 4, 6 and 7 all launch the paired-cell
  * kernel's limited build (20 resident warps per SM, per-thread copies);
  * with a finite floor the paired-cell variants do not apply.

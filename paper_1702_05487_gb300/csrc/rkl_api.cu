@@ -222,9 +222,10 @@ rkl_status launch_stage(rkl_plan* p, const StageIO& io, double mu, double nu, do
         KCoef<float> cf{(float)mu, (float)nu, (float)mt, (float)gt};
         bool al = aligned16(io.Y0) && aligned16(io.MY0) && aligned16(io.Yjm1) && aligned16(io.Yjm2) &&
                   aligned16(io.Yj) && aligned16(io.b);
-        if (p->x2ok && al && (p->variant == 0 || (p->variant >= 3 && p->variant <= 8)))
+        if (p->x2ok && al && (p->variant == 0 || (p->variant >= 3 && p->variant <= 9)))
             e = launch_stage_x2(p->cfg, p->gf, p->pf, io, cf, p->d_status, p->nzchunk,
-                                p->variant == 4 ? 3 : 2, st, p->variant == 6, p->variant == 7, p->variant == 8);
+                                p->variant == 4 ? 3 : (p->variant == 9 ? 6 : 2), st, p->variant == 6,
+                                p->variant == 7, p->variant == 8);
         else if (p->fast && al && (p->variant == 0 || p->variant == 2))
             e = launch_stage_fast(p->cfg, p->gf, p->pf, io, cf, p->d_status, st);
         else
@@ -874,6 +875,7 @@ rkl_status rkl_plan_autotune(rkl_plan* p, double dt, const void* T, const void* 
         for (int nz : {0, -1, 16, 32, 64}) {
             cands.push_back({3, nz});
             if (!lim) cands.push_back({4, nz});
+            if (!lim) cands.push_back({9, nz});
         }
     if (p->x2ok && p->pairok)
         for (int nz : {16, 32, 64}) cands.push_back({5, nz});
@@ -924,10 +926,10 @@ rkl_status rkl_plan_autotune(rkl_plan* p, double dt, const void* T, const void* 
 rkl_status rkl_plan_set_variant(rkl_plan* p, int variant, int nzchunk)
 {
     if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
-    if (variant < 0 || variant > 8) return fail(p, RKL_ERR_INVALID_ARG, "variant must be 0 to 8");
+    if (variant < 0 || variant > 9) return fail(p, RKL_ERR_INVALID_ARG, "variant must be 0 to 9");
     if (nzchunk > 4096) return fail(p, RKL_ERR_INVALID_ARG, "nzchunk must be <= 4096");
     if (variant == 2 && !p->fast) return fail(p, RKL_ERR_UNSUPPORTED, "no tiled kernel for this grid");
-    if ((variant == 3 || variant == 4 || variant == 6 || variant == 7 || variant == 8) && !p->x2ok)
+    if ((variant == 3 || variant == 4 || variant >= 6) && !p->x2ok)
         return fail(p, RKL_ERR_UNSUPPORTED, "no paired-cell kernel for this grid");
     if (variant == 5 && !(p->pairok && p->x2ok))
         return fail(p, RKL_ERR_UNSUPPORTED, "no two-stage kernel for this grid (periodic FP32 3D, nx % 4 == 0)");

@@ -68,6 +68,21 @@ struct rkl_ensemble {
 
 namespace {
 
+// Tile width and counts of one problem: 32-column tiles where they cover
+// the width with fewer idle columns than 64-column ones (nx an odd
+// multiple of 32, e.g. 32 or 96), else 64-column tiles.
+void set_tiles(x2::EnsProb& d, int nzchunk)
+{
+    const int nx = d.g.n[0];
+    const bool narrow = (nx + 31) / 32 * 32 < (nx + 63) / 64 * 64;
+    d.txw = narrow ? 32 : x2::TX;
+    const int tyh = x2::NTHREADS / (d.txw / 2);
+    d.tx = (nx + d.txw - 1) / d.txw;
+    d.ty = (d.g.n[1] + tyh - 1) / tyh;
+    d.tz = (d.g.n[2] + nzchunk - 1) / nzchunk;
+    d.ntiles = d.tx * d.ty * d.tz;
+}
+
 rkl_status efail(rkl_ensemble* e, rkl_status st, const std::string& m)
 {
     if (e) e->err = m;
@@ -167,10 +182,7 @@ rkl_status ens_run(rkl_ensemble* e, const double* dt, const int* s, float* T_all
         d.coef = e->d_coef + cofs[p];
         d.s = s[p];
         d.nzchunk = e->nzchunk;
-        d.tx = (d.g.n[0] + x2::TX - 1) / x2::TX;
-        d.ty = (d.g.n[1] + x2::TY - 1) / x2::TY;
-        d.tz = (d.g.n[2] + e->nzchunk - 1) / e->nzchunk;
-        d.ntiles = d.tx * d.ty * d.tz;
+        set_tiles(d, e->nzchunk);
         total_items += d.ntiles * s[p];
     }
     ENS_CK(e, cudaMemcpyAsync(e->d_coef, e->h_coef, sizeof(float) * cofs[np], cudaMemcpyHostToDevice, e->stream));
@@ -223,7 +235,8 @@ rkl_status ens_run(rkl_ensemble* e, const double* dt, const int* s, float* T_all
                 }
                 LaunchCfg cfg{0, 3, e->spitzer ? 1 : 0, e->saturate ? 1 : 0, 0};
                 KCoef<float> cf{0.f, 0.f, 0.f, 0.f};
-                cudaError_t c = launch_stage_x2(cfg, d.g, d.p, io, cf, e->d_status, e->nzchunk, 2, e->stream);
+                cudaError_t c = launch_stage_x2(cfg, d.g, d.p, io, cf, e->d_status, e->nzchunk,
+                                                d.txw == 32 ? 6 : 2, e->stream);
                 if (c != cudaSuccess) return efail(e, RKL_ERR_CUDA, std::string("stage launch: ") + cudaGetErrorString(c));
             }
     }
@@ -504,10 +517,7 @@ rkl_status rkl_ensemble_selftest_timeout(rkl_ensemble* e, int* status_out)
     d.g = e->kg[0];
     d.p = e->kp[0];
     d.nzchunk = e->nzchunk;
-    d.tx = (d.g.n[0] + x2::TX - 1) / x2::TX;
-    d.ty = (d.g.n[1] + x2::TY - 1) / x2::TY;
-    d.tz = (d.g.n[2] + e->nzchunk - 1) / e->nzchunk;
-    d.ntiles = d.tx * d.ty * d.tz;
+    set_tiles(d, e->nzchunk);
     d.s = 2;
     e->h_probs[0] = d;
     rkl_status st = grow_pinned(e, &e->d_segs, &e->h_segs, &e->seg_cap, 1);

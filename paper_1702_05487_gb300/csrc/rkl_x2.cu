@@ -148,6 +148,7 @@ cudaError_t launch_stage_x2(const LaunchCfg& c, const KGrid<float>& g, const KPh
     if (nzchunk == 0) nzchunk = auto_nzchunk(g, occupancy);
     else if (nzchunk < 0) nzchunk = 0;
     if (occupancy == 3) return launch_phys<3, false>(c, io.mode, g, p, a, coef, status, nzchunk, st);
+    if (occupancy == 6) return launch_phys<6, false>(c, io.mode, g, p, a, coef, status, nzchunk, st);
     if (bulk && x2_bulk_supported(c, g)) return launch_phys<2, true>(c, io.mode, g, p, a, coef, status, nzchunk, st);
     if (tmaps && x2_tmaps_supported(c, g)) {
         x2::TMaps tm{};
@@ -194,7 +195,8 @@ ensemble_x2_kernel(const x2::EnsProb* __restrict__ probs, const x2::EnsSeg* __re
                    int total, int* work, unsigned* done, unsigned* status, int* abort_flag, long long spin_limit)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    x2::Smem& sm = *reinterpret_cast<x2::Smem*>(smem_raw);
+    x2::Smem& sm = *reinterpret_cast<x2::Smem*>(smem_raw);                  // 64-column tiles
+    x2::SmemT<x2::kPD, 32>& sm32 = *reinterpret_cast<x2::SmemT<x2::kPD, 32>*>(smem_raw);   // 32-column tiles
     __shared__ int s_go, s_p, s_j, s_tile;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -231,6 +233,8 @@ ensemble_x2_kernel(const x2::EnsProb* __restrict__ probs, const x2::EnsSeg* __re
         const x2::EnsProb& d = probs[s_p];
         const int j = s_j, tile = s_tile;
         const int bx = tile % d.tx, by = (tile / d.tx) % d.ty, bz = tile / (d.tx * d.ty);
+        const bool narrow = d.txw == 32;
+        const int i0 = bx * d.txw, j0 = by * (narrow ? x2::NTHREADS / 16 : x2::TY);
         const int z0 = bz * d.nzchunk;
         const int nzc = min(d.nzchunk, d.g.n[2] - z0);
         x2::FastArgs a;
@@ -245,14 +249,22 @@ ensemble_x2_kernel(const x2::EnsProb* __restrict__ probs, const x2::EnsSeg* __re
             a.MY0in = nullptr;
             a.MY0out = d.my0;
             a.out = d.buf[0];
-            tile_x2<SP, SAT, 1, x2::kPD>(sm, d.g, d.p, a, cf, status, bx * x2::TX, by * x2::TY, z0, nzc);
+            if (narrow)
+                tile_x2<SP, SAT, 1, x2::kPD, false, false, false, false, 32>(sm32, d.g, d.p, a, cf, status, i0, j0,
+                                                                            z0, nzc);
+            else
+                tile_x2<SP, SAT, 1, x2::kPD>(sm, d.g, d.p, a, cf, status, i0, j0, z0, nzc);
         } else {
             a.Tin = d.buf[(j - 2) % 3];
             a.Yjm2 = j == 2 ? d.T : d.buf[(j - 3) % 3];
             a.MY0in = d.my0;
             a.MY0out = nullptr;
             a.out = j == d.s ? d.T : d.buf[(j - 1) % 3];
-            tile_x2<SP, SAT, 2, x2::kPD>(sm, d.g, d.p, a, cf, status, bx * x2::TX, by * x2::TY, z0, nzc);
+            if (narrow)
+                tile_x2<SP, SAT, 2, x2::kPD, false, false, false, false, 32>(sm32, d.g, d.p, a, cf, status, i0, j0,
+                                                                            z0, nzc);
+            else
+                tile_x2<SP, SAT, 2, x2::kPD>(sm, d.g, d.p, a, cf, status, i0, j0, z0, nzc);
         }
         if (threadIdx.x == 0) {
             __threadfence();
@@ -266,7 +278,7 @@ cudaError_t ensemble_launch_t(const x2::EnsProb* probs, const x2::EnsSeg* segs, 
                               unsigned* done, unsigned* status, int* abort_flag, long long spin_limit, int grid,
                               cudaStream_t st)
 {
-    const int smem = (int)sizeof(x2::Smem);
+    const int smem = (int)std::max(sizeof(x2::Smem), sizeof(x2::SmemT<x2::kPD, 32>));
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(ensemble_x2_kernel<SP, SAT>,

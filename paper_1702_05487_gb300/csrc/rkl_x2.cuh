@@ -39,10 +39,21 @@ struct FastArgs {
 // Plane rings for a prefetch distance of PD planes: while plane q is
 // computed, planes q+1 .. q+PD are in flight and plane q+PD+1 is being
 // issued into the slots that plane q-2 (T) or q-1 (b, Y) released.
-template <int PD, int PS = PLANE>
+// Shared-memory plane of a tile TXW columns wide: TXW / 2 lanes per row
+// (two cells each), NTHREADS / (TXW / 2) rows, a halo chunk of 4 columns on
+// each side and one halo row above and below.
+constexpr int plane_of(int txw) { return (NTHREADS / (txw / 2) + 2) * (txw + 8); }
+
+// Geometry and rings of one tile: TXW = 64 (the default, one warp per row)
+// or 32 (two rows per warp, for grids whose width is an odd multiple of
+// 32).  PS: floats from one ring slot to the next.
+template <int PD, int TXW = TX, int PS = plane_of(TXW)>
 struct SmemT {
+    static constexpr int TX = TXW, LPR = TXW / 2, TY = NTHREADS / LPR;
+    static constexpr int SXS = TX + 8, CPR = SXS / 4, ROWS = TY + 2, PLANE = ROWS * SXS;
     static constexpr int NT = 3 + PD, NB = 2 + PD, NY = 2 + PD;
-    static constexpr int PSTRIDE = PS;          // floats from one ring slot to the next
+    static constexpr int PSTRIDE = PS;
+    static_assert(PS >= PLANE, "ring slot smaller than a plane");
     alignas(128) float T[NT][PS];   // Y_{j-1} planes q-1, q, q+1 and those in flight
     float B[NB][3][PS];             // b planes q, q+1 and those in flight
     alignas(128) float Y[NY][3][TY * TX];   // Y0, Y_{j-2}, M(Y0) of plane q and those in flight
@@ -50,6 +61,8 @@ struct SmemT {
     float FxLo[2][TY];              // x-faces on the tile's left boundary
     alignas(8) unsigned long long bar[PD + 2];    // bundle barriers of the bulk-copy path
     alignas(8) unsigned long long ybar[4];        // Y bundles copied by tensor maps (plane q: ybar[q & 3])
+    // offset of cell (row r, column c) of the tile in a plane, halo included
+    __device__ static int off(int r, int c) { return (r + 1) * SXS + c + 4; }
 };
 
 // Tensor maps of Y0, Y_{j-2} and M(Y0) (3D FP32, boxes of TX x TY x 1) for
@@ -80,6 +93,7 @@ struct EnsProb {
     int s;                  // stages this super-step
     int tx, ty, tz, ntiles; // tiles in x, y and z-chunks
     int nzchunk;
+    int txw;                // tile width: 64, or 32 (rows of 32 columns, two per warp)
 };
 
 // A run of work items: the tiles of stage j of problem p, items

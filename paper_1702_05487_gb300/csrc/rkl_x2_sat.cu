@@ -13,6 +13,10 @@ cudaError_t launch_x2_sat(bool spitzer, int occ, bool bulk, int mode, const KGri
         if (spitzer) return launch_mode<true, true, 3, false>(mode, g, p, a, cf, status, nzchunk, st);
         return launch_mode<false, true, 3, false>(mode, g, p, a, cf, status, nzchunk, st);
     }
+    if (occ == 6) {
+        if (spitzer) return launch_mode<true, true, 6, false>(mode, g, p, a, cf, status, nzchunk, st);
+        return launch_mode<false, true, 6, false>(mode, g, p, a, cf, status, nzchunk, st);
+    }
     if (bulk) {
         if (spitzer) return launch_mode<true, true, 2, true>(mode, g, p, a, cf, status, nzchunk, st);
         return launch_mode<false, true, 2, true>(mode, g, p, a, cf, status, nzchunk, st);

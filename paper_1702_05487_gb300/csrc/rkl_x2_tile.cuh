@@ -40,7 +40,6 @@ namespace x2 {
 // --------------------------------------------------------------------------
 // shared memory and copies
 
-__device__ __forceinline__ int off(int r, int c) { return (r + 1) * SXS + c + 4; }
 
 // Half the MC limit: MC(a, b) / 2 = sign(a) min(|a + b| / 4, |a|, |b|) if
 // a b > 0, else 0.  Both factors 2 of MC are powers of two, so they move
@@ -100,6 +99,9 @@ template <int MODE, class SM>
 __device__ __forceinline__ Task make_task(const SM& sm, const KGrid<float>& g, const FastArgs& a, int s, int tid,
                                           int i0, int j0)
 {
+    constexpr int TX = SM::TX, TY = SM::TY, CPR = SM::CPR, ROWS = SM::ROWS;
+    constexpr int kTT = ROWS * CPR, kTBc = 3 * ROWS * CPR, kY = 3 * TY * (TX / 4);
+    static_assert(kTT <= NTHREADS && kTBc <= 3 * NTHREADS && kY <= 2 * NTHREADS, "task slots");
     Task k{nullptr, 0u};
     const int nx = g.n[0], ny = g.n[1];
     if (s < kSlotY) {
@@ -121,10 +123,10 @@ __device__ __forceinline__ Task make_task(const SM& sm, const KGrid<float>& g, c
         const int64_t rowoff = (int64_t)gy * nx + gx;
         if (arr == 0) {
             k.src = a.Tin + rowoff;
-            k.dst = smem_u32(&sm.T[0][off(row, c)]) | TK_VALID | (ghost ? TK_GHOST : 0u);
+            k.dst = smem_u32(&sm.T[0][SM::off(row, c)]) | TK_VALID | (ghost ? TK_GHOST : 0u);
         } else {
             k.src = a.b + (int64_t)(arr - 1) * g.ncell + rowoff;
-            k.dst = smem_u32(&sm.B[0][arr - 1][off(row, c)]) | TK_VALID | (xghost ? TK_BCAST : 0u);
+            k.dst = smem_u32(&sm.B[0][arr - 1][SM::off(row, c)]) | TK_VALID | (xghost ? TK_BCAST : 0u);
         }
         return k;
     }
@@ -261,18 +263,18 @@ __device__ __forceinline__ QZ read_qz(const SM& sm, int ts, int bs, int c, int r
 {
     const float* T = sm.T[ts];
     QZ q;
-    const float2 Tc = lds2(&T[off(r, c)]);
-    const float2 Tl = lds2(&T[off(r, c - 2)]);
-    const float2 Trr = lds2(&T[off(r, c + 2)]);
-    const float2 Tu = lds2(&T[off(r + 1, c)]);
-    const float2 Td = lds2(&T[off(r - 1, c)]);
+    const float2 Tc = lds2(&T[SM::off(r, c)]);
+    const float2 Tl = lds2(&T[SM::off(r, c - 2)]);
+    const float2 Trr = lds2(&T[SM::off(r, c + 2)]);
+    const float2 Tu = lds2(&T[SM::off(r + 1, c)]);
+    const float2 Td = lds2(&T[SM::off(r - 1, c)]);
     q.To = Tc;
     q.Tr = Trr.x;
     q.TU = Tu;
     q.gxo = cslope<LIM>(make_float2(Tc.y, Trr.x), Tc, make_float2(Tl.y, Tc.x));
     q.gyo = cslope<LIM>(Tu, Tc, Td);
 #pragma unroll
-    for (int e = 0; e < 3; ++e) q.bo[e] = lds2(&sm.B[bs][e][off(r, c)]);
+    for (int e = 0; e < 3; ++e) q.bo[e] = lds2(&sm.B[bs][e][SM::off(r, c)]);
     return q;
 }
 
@@ -281,10 +283,10 @@ __device__ __forceinline__ QXY read_qxy(const SM& sm, int ts, int bs, int c, int
 {
     const float* T = sm.T[ts];
     QXY q;
-    const float2 Td = lds2(&T[off(r - 1, c)]);
-    const float2 Tur = lds2(&T[off(r + 1, c + 2)]);
-    const float2 Tdr = lds2(&T[off(r - 1, c + 2)]);
-    const float2 Tul = lds2(&T[off(r + 1, c - 2)]);
+    const float2 Td = lds2(&T[SM::off(r - 1, c)]);
+    const float2 Tur = lds2(&T[SM::off(r + 1, c + 2)]);
+    const float2 Tdr = lds2(&T[SM::off(r - 1, c + 2)]);
+    const float2 Tul = lds2(&T[SM::off(r + 1, c - 2)]);
     if (LIM)    // column 2l+1's limited slope is the pair's own
         q.gyR = make_float2(z.gyo.y, cslope1<LIM>(Tur.x, z.Tr, Tdr.x));
     else
@@ -293,8 +295,8 @@ __device__ __forceinline__ QXY read_qxy(const SM& sm, int ts, int bs, int c, int
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
         const float* B = sm.B[bs][e];
-        q.bR[e] = B[off(r, c + 2)];
-        q.bU[e] = lds2(&B[off(r + 1, c)]);
+        q.bR[e] = B[SM::off(r, c + 2)];
+        q.bU[e] = lds2(&B[SM::off(r + 1, c)]);
     }
     return q;
 }
@@ -307,16 +309,16 @@ __device__ __forceinline__ float2 low_yface2(const SM& sm, const KGrid<float>& g
                                              const FaceK& fk, int tm, int tc, int tp, int bs, int c)
 {
     const float* T = sm.T[tc];
-    const float2 TL = lds2(&T[off(-1, c)]), TR = lds2(&T[off(0, c)]);
-    const float2 Ll = lds2(&T[off(-1, c - 2)]), Lr = lds2(&T[off(-1, c + 2)]);
-    const float2 Rl = lds2(&T[off(0, c - 2)]), Rr = lds2(&T[off(0, c + 2)]);
+    const float2 TL = lds2(&T[SM::off(-1, c)]), TR = lds2(&T[SM::off(0, c)]);
+    const float2 Ll = lds2(&T[SM::off(-1, c - 2)]), Lr = lds2(&T[SM::off(-1, c + 2)]);
+    const float2 Rl = lds2(&T[SM::off(0, c - 2)]), Rr = lds2(&T[SM::off(0, c + 2)]);
     const float2 gxL = cslope<LIM>(make_float2(TL.y, Lr.x), TL, make_float2(Ll.y, TL.x));
     const float2 gxR = cslope<LIM>(make_float2(TR.y, Rr.x), TR, make_float2(Rl.y, TR.x));
-    const float2 gzL = cslope<LIM>(lds2(&sm.T[tp][off(-1, c)]), TL, lds2(&sm.T[tm][off(-1, c)]));
-    const float2 gzR = cslope<LIM>(lds2(&sm.T[tp][off(0, c)]), TR, lds2(&sm.T[tm][off(0, c)]));
+    const float2 gzL = cslope<LIM>(lds2(&sm.T[tp][SM::off(-1, c)]), TL, lds2(&sm.T[tm][SM::off(-1, c)]));
+    const float2 gzR = cslope<LIM>(lds2(&sm.T[tp][SM::off(0, c)]), TR, lds2(&sm.T[tm][SM::off(0, c)]));
     float2 b[3];
 #pragma unroll
-    for (int e = 0; e < 3; ++e) b[e] = add2(lds2(&sm.B[bs][e][off(-1, c)]), lds2(&sm.B[bs][e][off(0, c)]));
+    for (int e = 0; e < 3; ++e) b[e] = add2(lds2(&sm.B[bs][e][SM::off(-1, c)]), lds2(&sm.B[bs][e][SM::off(0, c)]));
     return face2s<SP, SAT>(TL, TR, mul2(sub2(TR, TL), bc2(g.inv_dx[1])),
                            fgrad<LIM>(gxL, gxR, bc2(g.inv_4dx[0]), bc2(4.f * g.inv_dx[0])),
                            fgrad<LIM>(gzL, gzR, bc2(g.inv_4dx[2]), bc2(4.f * g.inv_dx[2])), b[1], b[0], b[2], fk, p);
@@ -327,16 +329,16 @@ __device__ __forceinline__ float low_xface(const SM& sm, const KGrid<float>& g, 
                                            const FaceK& fk, int tm, int tc, int tp, int bs, int r)
 {
     const float* T = sm.T[tc];
-    const float TL = T[off(r, -1)], TR = T[off(r, 0)];
-    const float gyL = cslope1<LIM>(T[off(r + 1, -1)], TL, T[off(r - 1, -1)]);
-    const float gyR = cslope1<LIM>(T[off(r + 1, 0)], TR, T[off(r - 1, 0)]);
-    const float gzL = cslope1<LIM>(sm.T[tp][off(r, -1)], TL, sm.T[tm][off(r, -1)]);
-    const float gzR = cslope1<LIM>(sm.T[tp][off(r, 0)], TR, sm.T[tm][off(r, 0)]);
+    const float TL = T[SM::off(r, -1)], TR = T[SM::off(r, 0)];
+    const float gyL = cslope1<LIM>(T[SM::off(r + 1, -1)], TL, T[SM::off(r - 1, -1)]);
+    const float gyR = cslope1<LIM>(T[SM::off(r + 1, 0)], TR, T[SM::off(r - 1, 0)]);
+    const float gzL = cslope1<LIM>(sm.T[tp][SM::off(r, -1)], TL, sm.T[tm][SM::off(r, -1)]);
+    const float gzR = cslope1<LIM>(sm.T[tp][SM::off(r, 0)], TR, sm.T[tm][SM::off(r, 0)]);
     const float gy = LIM ? mc_half(gyL, gyR) * (4.f * g.inv_dx[1]) : (gyL + gyR) * g.inv_4dx[1];
     const float gz = LIM ? mc_half(gzL, gzR) * (4.f * g.inv_dx[2]) : (gzL + gzR) * g.inv_4dx[2];
     float b[3];
 #pragma unroll
-    for (int e = 0; e < 3; ++e) b[e] = sm.B[bs][e][off(r, -1)] + sm.B[bs][e][off(r, 0)];
+    for (int e = 0; e < 3; ++e) b[e] = sm.B[bs][e][SM::off(r, -1)] + sm.B[bs][e][SM::off(r, 0)];
     // the packed form on a duplicated scalar costs what the scalar form does
     return face2s<SP, SAT>(bc2(TL), bc2(TR), bc2((TR - TL) * g.inv_dx[0]), bc2(gy), bc2(gz), bc2(b[0]), bc2(b[1]),
                            bc2(b[2]), fk, p)
@@ -415,18 +417,25 @@ __device__ __forceinline__ FixTask make_fix(const SM& sm, const KGrid<float>& g,
 // the barrier, and the wrapped halo chunks (make_fix) are stored over the
 // zero fill before the plane's first reader passes the CTA barrier.
 // Periodic grids with nx > TX and ny > TY only.
+// TXW: tile width, 64 (one warp per row) or 32 (two rows of 16 lanes per
+// warp, 8 rows per tile; per-thread copies only).
 template <bool SP, bool SAT, int MODE, int PD, bool BULK = false, bool YT = false, bool LIM = false,
-          bool TB = false>
-__device__ __forceinline__ void tile_x2(x2::SmemT<PD, TB ? x2::PSTR : x2::PLANE>& sm, const KGrid<float>& g,
-                                        const KPhys<float>& p, const x2::FastArgs& a, KCoef<float> cf,
-                                        unsigned* status, int i0, int j0, int z0, int nzc,
+          bool TB = false, int TXW = x2::TX>
+__device__ __forceinline__ void tile_x2(x2::SmemT<PD, TXW, TB ? x2::PSTR : x2::plane_of(TXW)>& sm,
+                                        const KGrid<float>& g, const KPhys<float>& p, const x2::FastArgs& a,
+                                        KCoef<float> cf, unsigned* status, int i0, int j0, int z0, int nzc,
                                         const x2::YMaps* ym = nullptr, const x2::TMaps* tm = nullptr)
 {
     using namespace x2;
+    static_assert(TXW == x2::TX || !(BULK || YT || TB), "32-column tiles use per-thread copies");
+    using SM = SmemT<PD, TXW, TB ? PSTR : plane_of(TXW)>;
+    // the tile's geometry (shadows the 64-column defaults of namespace x2)
+    constexpr int TX = SM::TX, TY = SM::TY, LPR = SM::LPR;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const int r = tid >> 5;
-    const int c = 2 * lane;
+    const int lx = tid % LPR;                   // pair index in the row
+    const int r = tid / LPR;                    // row of the tile
+    const int c = 2 * lx;
     const int nx = g.n[0], ny = g.n[1];
 
     if (MODE != 0 && a.coef_tab) {
@@ -480,7 +489,6 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD, TB ? x2::PSTR : x2::PLANE>
     const unsigned ybytes =
         MODE == 2 ? 3u * (unsigned)min(TY, ny - j0) * (unsigned)min(TX, nx - i0) * 4u : 0u;
 
-    using SM = SmemT<PD, TB ? PSTR : PLANE>;
     constexpr int PS = SM::PSTRIDE;
     // slot of plane q >= -1 in a ring of n (a mask when n is a power of two)
     auto slot = [](int q, int n) { return (n & (n - 1)) == 0 ? (q + 1) & (n - 1) : (q + 1) % n; };
@@ -633,7 +641,7 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD, TB ? x2::PSTR : x2::PLANE>
     auto finish = [&](int qp) {
         const int par = qp & 1;
         float2 M = fma2(lds2(&sm.Fy[par][r][c]), bc2(-cmy.x), pend);
-        if (lane == 0) M.x = fmaf(sm.FxLo[par][r], -cmx.x, M.x);
+        if (lx == 0) M.x = fmaf(sm.FxLo[par][r], -cmx.x, M.x);
         if (in0) {
             float2* out = reinterpret_cast<float2*>(a.out + pcb);
             if (MODE == 0) {
@@ -718,9 +726,9 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD, TB ? x2::PSTR : x2::PLANE>
         if (r == wy) {
             *reinterpret_cast<float2*>(&sm.Fy[par][0][c]) =
                 low_yface2<SP, SAT, LIM>(sm, g, p, fk, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), c);
-        } else if (r == wx && lane < TY) {
-            sm.FxLo[par][lane] =
-                low_xface<SP, SAT, LIM>(sm, g, p, fk, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), lane);
+        } else if (r == wx && lx < TY) {
+            sm.FxLo[par][lx] =
+                low_xface<SP, SAT, LIM>(sm, g, p, fk, tslot(q - 1), tslot(q), tslot(q + 1), bslot(q), lx);
         }
         if (MODE == 2) {
             const int ys = yslot(q);
@@ -729,9 +737,9 @@ __device__ __forceinline__ void tile_x2(x2::SmemT<PD, TB ? x2::PSTR : x2::PLANE>
             pmy0 = lds2(&sm.Y[ys][2][r * TX + c]);
         }
         *reinterpret_cast<float2*>(&sm.Fy[par][r + 1][c]) = Fy;
-        const float fxl = __shfl_up_sync(0xffffffffu, Fx.y, 1);
-        // divergence without the y-face below (and, on lane 0, the left face)
-        const float2 Fx_lo = make_float2(lane == 0 ? 0.f : fxl, Fx.x);
+        const float fxl = __shfl_up_sync(0xffffffffu, Fx.y, 1, LPR);
+        // divergence without the y-face below (and, on a row's first lane, the left face)
+        const float2 Fx_lo = make_float2(lx == 0 ? 0.f : fxl, Fx.x);
         pend = fma2(sub2(Fx, Fx_lo), cmx, fma2(Fy, cmy, mul2(sub2(Fz, Fz_lo), cmz)));
         pTo = cur.To;
         pcb = cbase;
@@ -779,8 +787,10 @@ namespace {
 // per SM: 0.173 ms per 256^3 stage against 0.178 ms at four CTAs with 128
 // registers).
 // BULK: bundles copied by the TMA engine (periodic grids with nx >= 72).
-constexpr int ctas_per_sm(int occ) { return occ == 2 ? x2::kCtasPerSm : (occ == 4 ? 5 : 6); }
+// 6: the default build with 32-column tiles (two rows per warp).
+constexpr int ctas_per_sm(int occ) { return (occ == 2 || occ == 6) ? x2::kCtasPerSm : (occ == 4 ? 5 : 6); }
 constexpr int occ_pd(int occ) { return occ == 3 ? 1 : x2::kPD; }
+constexpr int occ_txw(int occ) { return occ == 6 ? 32 : x2::TX; }
 
 // TB: all bundles copied from tensor maps (maps: x2::TMaps, else x2::YMaps)
 template <bool TB>
@@ -794,7 +804,8 @@ stage_x2_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf,
     extern __shared__ __align__(128) unsigned char smem_raw[];     // tensor copies land 128-byte aligned
     constexpr int PD = occ_pd(OCC);
     constexpr bool LIM = OCC == 4;
-    using SMT = x2::SmemT<PD, TB ? x2::PSTR : x2::PLANE>;
+    constexpr int TXW = occ_txw(OCC);
+    using SMT = x2::SmemT<PD, TXW, TB ? x2::PSTR : x2::plane_of(TXW)>;
     SMT& sm = *reinterpret_cast<SMT*>(smem_raw);
     const x2::YMaps* ym = nullptr;
     const x2::TMaps* tm = nullptr;
@@ -803,25 +814,26 @@ stage_x2_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf,
     if (nzchunk > 0) {
         // one tile column, one chunk of nzchunk planes per CTA
         const int z0 = blockIdx.z * nzchunk;
-        tile_x2<SP, SAT, MODE, PD, BULK, YT, LIM, TB>(sm, g, p, a, cf, status, blockIdx.x * x2::TX,
-                                                      blockIdx.y * x2::TY, z0, min(nzchunk, g.n[2] - z0), ym, tm);
+        tile_x2<SP, SAT, MODE, PD, BULK, YT, LIM, TB, TXW>(sm, g, p, a, cf, status, blockIdx.x * SMT::TX,
+                                                           blockIdx.y * SMT::TY, z0, min(nzchunk, g.n[2] - z0), ym,
+                                                           tm);
         return;
     }
     // Balanced schedule: the column-planes (tile column, plane) in column-major
     // order are split into gridDim.x equal runs; each CTA marches its run,
     // switching columns where the run crosses one, so every CTA carries the
     // same number of planes and no partial last wave is left.
-    const int ntx = (g.n[0] + x2::TX - 1) / x2::TX;
+    const int ntx = (g.n[0] + SMT::TX - 1) / SMT::TX;
     const int nz = g.n[2];
-    const int64_t U = (int64_t)ntx * ((g.n[1] + x2::TY - 1) / x2::TY) * nz;
+    const int64_t U = (int64_t)ntx * ((g.n[1] + SMT::TY - 1) / SMT::TY) * nz;
     int64_t u = U * blockIdx.x / gridDim.x;
     const int64_t u1 = U * (blockIdx.x + 1) / gridDim.x;
     while (u < u1) {
         const int64_t col = u / nz;
         const int z0 = (int)(u - col * nz);
         const int nzc = (int)min((int64_t)(nz - z0), u1 - u);
-        tile_x2<SP, SAT, MODE, PD, BULK, YT, LIM, TB>(sm, g, p, a, cf, status, (int)(col % ntx) * x2::TX,
-                                                      (int)(col / ntx) * x2::TY, z0, nzc, ym, tm);
+        tile_x2<SP, SAT, MODE, PD, BULK, YT, LIM, TB, TXW>(sm, g, p, a, cf, status, (int)(col % ntx) * SMT::TX,
+                                                           (int)(col / ntx) * SMT::TY, z0, nzc, ym, tm);
         u += nzc;
     }
 }
@@ -843,7 +855,8 @@ cudaError_t launch3(const KGrid<float>& g, const KPhys<float>& p, const x2::Fast
                     unsigned* status, int nzchunk, cudaStream_t st, const MapsT<TB>& ym)
 {
     constexpr int kCtasPerSm = ctas_per_sm(OCC);
-    const int smem = (int)sizeof(x2::SmemT<occ_pd(OCC), TB ? x2::PSTR : x2::PLANE>);
+    using SMT = x2::SmemT<occ_pd(OCC), occ_txw(OCC), TB ? x2::PSTR : x2::plane_of(occ_txw(OCC))>;
+    const int smem = (int)sizeof(SMT);
     static bool attr_set = false;       // the attribute is per function, set once
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(stage_x2_kernel<SP, SAT, MODE, OCC, BULK, YT, TB>,
@@ -851,7 +864,7 @@ cudaError_t launch3(const KGrid<float>& g, const KPhys<float>& p, const x2::Fast
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int ntx = (g.n[0] + x2::TX - 1) / x2::TX, nty = (g.n[1] + x2::TY - 1) / x2::TY;
+    const int ntx = (g.n[0] + SMT::TX - 1) / SMT::TX, nty = (g.n[1] + SMT::TY - 1) / SMT::TY;
     dim3 grid(ntx, nty, nzchunk > 0 ? (g.n[2] + nzchunk - 1) / nzchunk : 1);
     if (nzchunk <= 0) {
         // balanced: one wave of resident CTAs, each run at least 8 planes long

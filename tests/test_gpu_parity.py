@@ -144,7 +144,7 @@ def _variant_cases():
     # grids with nx % 4 == 0 (the paired-cell kernel) and Dirichlet partial tiles
     spitz = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
     sat = dict(kappa_model="spitzer", kappa_par0=0.01, saturate=True, phi=0.3)
-    for v in (2, 3, 4, 5, 6, 7, 8):
+    for v in (2, 3, 4, 5, 6, 7, 8, 9):
         if v not in (5, 6, 8):  # the two-stage kernel, bulk and tensor-map copies are periodic only
             out.append(("3d_x4_dirichlet", (21, 19, 36), dict(spitz, bc="dirichlet", bc_value=0.9), "f32", v))
         out.append(("3d_x4_sat", (18, 26, 68), sat, "f32", v))
@@ -176,6 +176,11 @@ def _variant_cases():
     out.append(("3d_tmaps_ragged", (37, 21, 200), spitz, "f32", 8))
     out.append(("3d_tmaps_thin", (11, 6, 72), spitz, "f32", 8))
     out.append(("3d_tmaps_sat", (13, 12, 132), sat, "f32", 8))
+    # 32-column tiles (two rows of 16 lanes per warp, eight rows per tile):
+    # widths of one, two and a ragged three tiles, ragged rows, Dirichlet
+    out.append(("3d_cols32_ragged", (9, 21, 68), spitz, "f32", 9))
+    out.append(("3d_cols32_narrow", (12, 10, 32), spitz, "f32", 9))
+    out.append(("3d_cols32_dirichlet", (7, 13, 96), dict(spitz, bc="dirichlet", bc_value=0.9), "f32", 9))
     return out
 
 
@@ -221,7 +226,7 @@ def test_tiled_kernels_match_generic(rk, orc, shape, nzchunk):
     whose runs cross tile columns) and the generic kernel (variant 1) on
     tile-aligned, ragged and degenerate shapes; all against the oracle."""
     params = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
-    variants = (1, 2, 3, 4, 5, 6, 8) if shape[2] % 4 == 0 else (1, 2)
+    variants = (1, 2, 3, 4, 5, 6, 8, 9) if shape[2] % 4 == 0 else (1, 2)
     res = {}
     for v in variants:
         P, plan, T, b, Td, bd = _setup(rk, "x", shape, params, "f32", v)
