@@ -281,7 +281,7 @@ def test_autotune_keeps_input_and_parity(rk, orc):
     T_before = Td.clone()
     v, nz, ms = plan.autotune(dt, Td, bd)
     assert torch.equal(Td, T_before)
-    assert v in (1, 2, 3, 4, 5, 6) and ms > 0
+    assert 1 <= v <= 9 and ms > 0            # any kernel that applies to the grid
     plan.super_step(dt, Td, bd)
     Tref, _ = orc.super_step(P, T, b, dt)
     assert rel_l2(host(Td), Tref) < F32_STATE_REL_L2
