@@ -398,16 +398,16 @@ def run_ours(args):
     # end to end through the public host-buffer API: every step copies T and
     # b from pinned host memory, runs one super-step and copies T back.
     # rkl_run_host_batch streams the steps as jobs whose copies overlap the
-    # previous and next job's super-step (two host buffer pairs alternate:
-    # job i + 2 starts from job i's result); rkl_run_host does one job per
+    # previous and next job's super-step (three host buffer pairs rotate:
+    # job i + 3 starts from job i's result); rkl_run_host does one job per
     # call with its copies in series.
-    Th = [T0.clone().pin_memory() for _ in range(2)]
-    bh = [b0.clone().pin_memory() for _ in range(2)]
+    Th = [T0.clone().pin_memory() for _ in range(3)]
+    bh = [b0.clone().pin_memory() for _ in range(3)]
     plan.run_host_batch(dt, 1, Th, bh)        # warm the staging buffers and graphs
     barrier()
     t0 = time.perf_counter()
-    e_stages = sum(plan.run_host_batch(dt, 1, [Th[i % 2] for i in range(args.steps)],
-                                       [bh[i % 2] for i in range(args.steps)]))
+    e_stages = sum(plan.run_host_batch(dt, 1, [Th[i % 3] for i in range(args.steps)],
+                                       [bh[i % 3] for i in range(args.steps)]))
     barrier()
     e_s = time.perf_counter() - t0
     e_s, e_cell_stages = aggregate_over_ranks(dist, e_s, float(ncell) * e_stages, dev)

@@ -338,12 +338,14 @@ rkl_status rkl_run_host(rkl_plan *plan, double dt, int n_super, void *T_host,
  * Streams n_jobs independent problems of the plan's grid through the GPU:
  * job i copies T_host[i] and b_host[i] (the layouts of rkl_super_step) to
  * the device, performs n_super super-steps of length dt and copies T back
- * into T_host[i]; s_last[i] receives its last s (s_last may be NULL).  Two
+ * into T_host[i]; s_last[i] receives its last s (s_last may be NULL).  Three
  * device staging sets (kept with the plan) and two private copy streams
  * let the copy-in of job i + 1 and the copy-out of job i - 1 overlap the
- * super-steps of job i on the plan's stream, so with page-locked buffers
- * the jobs cost about max(copy-in, compute, copy-out) each.  Job i's
- * buffers must not alias those of jobs i - 1 .. i + 1.  Synchronises.
+ * super-steps of job i on the plan's stream and each other, so with
+ * page-locked buffers the jobs cost about max(copy-in, compute, copy-out)
+ * each.  Job i's buffers must not alias those of jobs i - 1 and i + 1; a
+ * T_host[i] equal to T_host[i - 2] is allowed (its copy-in then waits for
+ * job i - 2's copy-out).  Synchronises.
  */
 rkl_status rkl_run_host_batch(rkl_plan *plan, double dt, int n_super, int n_jobs, void *const *T_host,
                               const void *const *b_host, int *s_last);

@@ -54,8 +54,11 @@ struct rkl_plan {
     bool pairok = false;               // two-stage kernel applies to the grid
     void* my0 = nullptr;
     double* d_partials = nullptr;
-    double* d_scal = nullptr;          // {max, min, sum, status}
-    double* h_scal = nullptr;          // pinned mirror
+    // {max, min, sum, status} of the statistics pass, written by its last
+    // block straight into page-locked mapped host memory: the read-back
+    // needs no copy engine, so it never queues behind a large copy-out
+    double* h_scal = nullptr;
+    double* m_scal = nullptr;          // device address of h_scal
     unsigned* d_status = nullptr;
 
     int method = RKL_METHOD_RKL2;      // super-time-stepping method (Section 3.3)
@@ -77,12 +80,13 @@ struct rkl_plan {
 
     void* host_T = nullptr;            // device staging for rkl_run_host
     void* host_b = nullptr;
-    // rkl_run_host_batch: a second staging set, copy-in / copy-out streams and
-    // the events that order them around the plan's stream
-    void* batch_T = nullptr;
-    void* batch_b = nullptr;
+    // rkl_run_host_batch: two more staging sets (three in all with host_T /
+    // host_b), copy-in / copy-out streams and the events that order them
+    // around the plan's stream
+    void* batch_T[2] = {};
+    void* batch_b[2] = {};
     cudaStream_t s_in = nullptr, s_out = nullptr;
-    cudaEvent_t ev_in[2] = {}, ev_comp[2] = {}, ev_out[2] = {};
+    cudaEvent_t ev_in[3] = {}, ev_comp[3] = {}, ev_out[3] = {};
 
     std::string err;
 };
@@ -412,11 +416,9 @@ rkl_status collect_timing(rkl_plan* p)
 // h_scal[3] and cleared; otherwise h_scal[3] = 0 and the word is kept.
 rkl_status stats(rkl_plan* p, const void* T, bool take_status = true, bool need_sum = true)
 {
-    cudaError_t e = launch_stats(p->cfg.dtype, T, p->ncell, p->d_partials, p->d_scal,
+    cudaError_t e = launch_stats(p->cfg.dtype, T, p->ncell, p->d_partials, p->m_scal,
                                  take_status ? p->d_status : nullptr, p->stream, need_sum);
     if (e != cudaSuccess) return cuda_fail(p, e, "stats launch");
-    RKL_CK(p, cudaMemcpyAsync(p->h_scal, p->d_scal, 4 * sizeof(double), cudaMemcpyDeviceToHost,
-                              p->stream));
     RKL_CK(p, cudaStreamSynchronize(p->stream));
     return RKL_OK;
 }
@@ -626,8 +628,10 @@ rkl_status rkl_plan_create(const rkl_grid* grid, const rkl_phys* phys, void* cud
         return bail(e, "cudaMalloc(partials)");
     if ((e = cudaMemsetAsync(p->d_partials, 0, sizeof(double) * (3 * kStatsBlocks + 1), p->stream)) != cudaSuccess)
         return bail(e, "cudaMemset(partials)");
-    if ((e = cudaMalloc(&p->d_scal, sizeof(double) * 4)) != cudaSuccess) return bail(e, "cudaMalloc(scalars)");
-    if ((e = cudaMallocHost(&p->h_scal, sizeof(double) * 4)) != cudaSuccess) return bail(e, "cudaMallocHost");
+    if ((e = cudaHostAlloc(&p->h_scal, sizeof(double) * 4, cudaHostAllocMapped)) != cudaSuccess)
+        return bail(e, "cudaHostAlloc(scalars)");
+    if ((e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&p->m_scal), p->h_scal, 0)) != cudaSuccess)
+        return bail(e, "cudaHostGetDevicePointer(scalars)");
     if ((e = cudaMalloc(&p->d_status, sizeof(unsigned))) != cudaSuccess) return bail(e, "cudaMalloc(status)");
     if ((e = cudaMemsetAsync(p->d_status, 0, sizeof(unsigned), p->stream)) != cudaSuccess)
         return bail(e, "cudaMemset(status)");
@@ -655,9 +659,11 @@ rkl_status rkl_plan_destroy(rkl_plan* p)
     cudaFree(p->my0);
     if (p->s_in) cudaStreamSynchronize(p->s_in);
     if (p->s_out) cudaStreamSynchronize(p->s_out);
-    cudaFree(p->batch_T);
-    cudaFree(p->batch_b);
     for (int k = 0; k < 2; ++k) {
+        cudaFree(p->batch_T[k]);
+        cudaFree(p->batch_b[k]);
+    }
+    for (int k = 0; k < 3; ++k) {
         if (p->ev_in[k]) cudaEventDestroy(p->ev_in[k]);
         if (p->ev_comp[k]) cudaEventDestroy(p->ev_comp[k]);
         if (p->ev_out[k]) cudaEventDestroy(p->ev_out[k]);
@@ -665,7 +671,6 @@ rkl_status rkl_plan_destroy(rkl_plan* p)
     if (p->s_in) cudaStreamDestroy(p->s_in);
     if (p->s_out) cudaStreamDestroy(p->s_out);
     cudaFree(p->d_partials);
-    cudaFree(p->d_scal);
     if (p->h_scal) cudaFreeHost(p->h_scal);
     cudaFree(p->d_status);
     cudaFree(p->d_coef);
@@ -1021,24 +1026,31 @@ rkl_status rkl_run_host_batch(rkl_plan* p, double dt, int n_super, int n_jobs, v
     const size_t bytes = (size_t)p->ncell * p->esize, bbytes = bytes * p->grid.ndim;
     if (!p->host_T) RKL_CK(p, cudaMalloc(&p->host_T, bytes));
     if (!p->host_b) RKL_CK(p, cudaMalloc(&p->host_b, bbytes));
-    if (!p->batch_T) RKL_CK(p, cudaMalloc(&p->batch_T, bytes));
-    if (!p->batch_b) RKL_CK(p, cudaMalloc(&p->batch_b, bbytes));
+    for (int k = 0; k < 2; ++k) {
+        if (!p->batch_T[k]) RKL_CK(p, cudaMalloc(&p->batch_T[k], bytes));
+        if (!p->batch_b[k]) RKL_CK(p, cudaMalloc(&p->batch_b[k], bbytes));
+    }
     if (!p->s_in) RKL_CK(p, cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking));
     if (!p->s_out) RKL_CK(p, cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking));
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 3; ++k) {
         if (!p->ev_in[k]) RKL_CK(p, cudaEventCreateWithFlags(&p->ev_in[k], cudaEventDisableTiming));
         if (!p->ev_comp[k]) RKL_CK(p, cudaEventCreateWithFlags(&p->ev_comp[k], cudaEventDisableTiming));
         if (!p->ev_out[k]) RKL_CK(p, cudaEventCreateWithFlags(&p->ev_out[k], cudaEventDisableTiming));
     }
-    void* dT[2] = {p->host_T, p->batch_T};
-    void* db[2] = {p->host_b, p->batch_b};
+    void* dT[3] = {p->host_T, p->batch_T[0], p->batch_T[1]};
+    void* db[3] = {p->host_b, p->batch_b[0], p->batch_b[1]};
     // work already queued on the plan's stream may still use the staging set
     RKL_CK(p, cudaEventRecord(p->ev_comp[0], p->stream));
     RKL_CK(p, cudaStreamWaitEvent(p->s_in, p->ev_comp[0], 0));
     for (int i = 0; i < n_jobs; ++i) {
-        const int k = i & 1;
-        // copy-in of job i after the copy-out of job i - 2, which used the same set
-        if (i >= 2) RKL_CK(p, cudaStreamWaitEvent(p->s_in, p->ev_out[k], 0));
+        const int k = i % 3;
+        // copy-in of job i after the copy-out of job i - 3, which used the same
+        // set, and after that of job i - 2 if it returns into the same host
+        // buffer job i reads (the copy-in and copy-out streams otherwise run
+        // side by side)
+        if (i >= 3) RKL_CK(p, cudaStreamWaitEvent(p->s_in, p->ev_out[k], 0));
+        if (i >= 2 && T_host[i] == T_host[i - 2])
+            RKL_CK(p, cudaStreamWaitEvent(p->s_in, p->ev_out[(i - 2) % 3], 0));
         RKL_CK(p, cudaMemcpyAsync(dT[k], T_host[i], bytes, cudaMemcpyHostToDevice, p->s_in));
         RKL_CK(p, cudaMemcpyAsync(db[k], b_host[i], bbytes, cudaMemcpyHostToDevice, p->s_in));
         RKL_CK(p, cudaEventRecord(p->ev_in[k], p->s_in));

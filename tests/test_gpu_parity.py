@@ -404,6 +404,34 @@ def test_run_host_batch_matches_serial_and_oracle(rk, orc, n_jobs):
     assert plan.check() == 0
 
 
+@pytest.mark.parametrize("nbuf", [2, 3])
+def test_run_host_batch_rotating_host_buffers(rk, nbuf):
+    """Seven jobs over nbuf page-locked host buffers used in rotation (job
+    i + nbuf starts from job i's result, the way bench.py streams its
+    steps): with two buffers the copy-in of job i must wait for job i - 2's
+    copy-out into the same buffer; with three, copies of neighbouring jobs
+    run side by side.  Both give, bit for bit, the same sequence run one
+    rkl_run_host call at a time."""
+    import torch
+    shape = (12, 16, 64)
+    params = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
+    plan = rk.Plan(shape, "f32", params=params)
+    fields = [_fields(shape, seed=60 + k) for k in range(nbuf)]
+    dt = 3e-5
+    Th = [torch.from_numpy(T.astype(np.float32)).pin_memory() for T, _ in fields]
+    bh = [torch.from_numpy(b.astype(np.float32)).pin_memory() for _, b in fields]
+    n_jobs = 7
+    s_batch = plan.run_host_batch(dt, 1, [Th[i % nbuf] for i in range(n_jobs)], [bh[i % nbuf] for i in range(n_jobs)])
+    Tr = [np.ascontiguousarray(T, dtype=np.float32) for T, _ in fields]
+    br = [np.ascontiguousarray(b, dtype=np.float32) for _, b in fields]
+    for i in range(n_jobs):
+        s = plan.run_host(dt, 1, Tr[i % nbuf], br[i % nbuf])
+        assert s == s_batch[i], i
+    for k in range(nbuf):
+        assert np.array_equal(Th[k].numpy(), Tr[k]), k
+    assert plan.check() == 0
+
+
 def test_invalid_arguments_and_device_status(rk):
     import torch
     shape = (16, 16, 16)
