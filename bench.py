@@ -45,8 +45,9 @@ WORKLOAD = "tangled256_spitzer_rkl2"
 MEASURED_TRAFFIC = {"source_hash": "883ed3270244dc73", "bytes_per_launch": 541830912}
 
 
-# the sources of the default stage kernel (stage_x2_kernel)
-STAGE_KERNEL_SOURCES = ("rkl_x2.cu", "rkl_x2_tile.cuh", "rkl_x2.cuh", "rkl_pair.cuh", "rkl_device.cuh")
+# the sources of the default stage kernel (stage_q_kernel, the row-pair
+# kernel, built on the paired-cell kernel's face and copy helpers)
+STAGE_KERNEL_SOURCES = ("rkl_xq.cu", "rkl_x2_tile.cuh", "rkl_x2.cuh", "rkl_pair.cuh", "rkl_device.cuh")
 
 
 def kernel_source_hash() -> str:
@@ -432,7 +433,7 @@ def run_ours(args):
     avg_launch_ms = stage_ms / max(1, stage_launches)
     achieved = bytes_per_cs * ncell / (avg_launch_ms * 1e-3) / 1e9
     traffic = None
-    default_kernel = args.variant in (0, 3) and args.nzchunk == 0 and args.limiter == "none"
+    default_kernel = args.variant in (0, 10) and args.nzchunk == 0 and args.limiter == "none"
     if args.workload == "tangled256" and default_kernel and MEASURED_TRAFFIC["source_hash"] == kernel_source_hash():
         traffic = MEASURED_TRAFFIC["bytes_per_launch"]
     cpu = None
@@ -710,7 +711,7 @@ def main():
     ap.add_argument("--variant", type=int, default=0,
                     help="stage kernel: 0 auto, 1 generic, 2 tiled, 3/4 paired-cell at 5/6 CTAs per SM, 5 two-stage, "
                          "6 bulk copies, 7 tensor-map Y copies, 8 every bundle from tensor maps, "
-                         "9 32-column tiles")
+                         "9 32-column tiles, 10 row-pair (two cell pairs per thread)")
     ap.add_argument("--nzchunk", type=int, default=0, help="planes per CTA (0 automatic, < 0 balanced runs)")
     ap.add_argument("--limiter", default="none", choices=["none", "mc"],
                     help="transverse gradients: plain averages, or MC-limited at every face (Appendix C; "

@@ -252,8 +252,8 @@ rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
 
 /*
  * Kernel choice for the stage launches of this plan: 0 = automatic (the
- * paired-cell kernel where it applies, else the tiled kernel, else the
- * generic kernel), 1 = the generic one-thread-per-cell kernel, 2 = the
+ * row-pair kernel where it applies, else the paired-cell kernel, else the
+ * tiled kernel, else the generic kernel), 1 = the generic one-thread-per-cell kernel, 2 = the
  * tiled FP32 3D kernel (32 x 8 tiles, one cell per thread), 3 and 4 = the
  * paired-cell FP32 3D kernel (64 x 4 tiles, two cells per thread in packed
  * f32x2 arithmetic; needs nx % 4 == 0) built for 20 (variant 3) or 24
@@ -271,7 +271,12 @@ rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
  * and ny >= 6, no limiter; else as 3), 9 = the paired-cell kernel with
  * tiles 32 columns wide and 8 rows high (two rows of 16 lanes per warp;
  * for grids whose width is an odd multiple of 32, where 64-column tiles
- * leave a quarter to a half of the last tile idle; no limiter, else as 3).  With the MC limiter at every face
+ * leave a quarter to a half of the last tile idle; no limiter, else as 3),
+ * 10 = the row-pair kernel (the paired-cell arithmetic with two cell pairs
+ * per thread, rows 2w and 2w + 1 of 64 x 8 tiles, three CTAs per SM; the
+ * same bits as the paired-cell kernel; periodic grids with fewer than 2^31
+ * cells, nx % 4 == 0, no limiter, else RKL_ERR_UNSUPPORTED; nzchunk <= 0
+ * picks the chunk length).  With the MC limiter at every face
  * (limiter_floor = +inf) variants 3, 4, 6 and 7 all launch the paired-cell
  * kernel's limited build (20 resident warps per SM, per-thread copies);
  * with a finite floor the paired-cell variants do not apply.
@@ -297,7 +302,7 @@ rkl_status rkl_plan_set_method(rkl_plan *plan, int method, double sts_nu);
  * Autotuner: times one super-step of length dt (s from dt / dt_expl(T))
  * with every kernel variant and z-chunk that applies to the grid (generic;
  * tiled; paired-cell at 5 and 6 CTAs per SM, automatic, balanced or with 16,
- * 32, 64 planes per CTA; two-stage; bulk and tensor-map copies) on a
+ * 32, 64 planes per CTA; two-stage; bulk and tensor-map copies; row-pair) on a
  * scratch copy of T (T is not changed), keeps the fastest with
  * rkl_plan_set_variant and returns it.  Allocates and frees one grid-sized
  * scratch array.  Synchronises.

@@ -52,6 +52,7 @@ struct rkl_plan {
     void* ybuf[3] = {nullptr, nullptr, nullptr};
     void* ybuf4 = nullptr;             // fourth stage buffer of the two-stage kernel (allocated on use)
     bool pairok = false;               // two-stage kernel applies to the grid
+    bool xqok = false;                 // row-pair kernel applies to the grid
     void* my0 = nullptr;
     double* d_partials = nullptr;
     // {max, min, sum, status} of the statistics pass, written by its last
@@ -226,7 +227,9 @@ rkl_status launch_stage(rkl_plan* p, const StageIO& io, double mu, double nu, do
         KCoef<float> cf{(float)mu, (float)nu, (float)mt, (float)gt};
         bool al = aligned16(io.Y0) && aligned16(io.MY0) && aligned16(io.Yjm1) && aligned16(io.Yjm2) &&
                   aligned16(io.Yj) && aligned16(io.b);
-        if (p->x2ok && al && (p->variant == 0 || (p->variant >= 3 && p->variant <= 9)))
+        if ((p->variant == 0 || p->variant == 10) && p->xqok && al)
+            e = launch_stage_xq(p->cfg, p->gf, p->pf, io, cf, p->d_status, p->nzchunk, st);
+        else if (p->x2ok && al && (p->variant == 0 || (p->variant >= 3 && p->variant <= 9)))
             e = launch_stage_x2(p->cfg, p->gf, p->pf, io, cf, p->d_status, p->nzchunk,
                                 p->variant == 4 ? 3 : (p->variant == 9 ? 6 : 2), st, p->variant == 6,
                                 p->variant == 7, p->variant == 8);
@@ -608,6 +611,7 @@ rkl_status rkl_plan_create(const rkl_grid* grid, const rkl_phys* phys, void* cud
     p->fast = g.dtype == RKL_F32 && fast_stage_supported(p->cfg, p->gf);
     p->x2ok = g.dtype == RKL_F32 && x2_stage_supported(p->cfg, p->gf);
     p->pairok = g.dtype == RKL_F32 && pair_stage_supported(p->cfg, p->gf);
+    p->xqok = g.dtype == RKL_F32 && xq_stage_supported(p->cfg, p->gf);
 
     rkl_plan* P = p;
     auto bail = [&](cudaError_t e, const char* where) {
@@ -889,6 +893,8 @@ rkl_status rkl_plan_autotune(rkl_plan* p, double dt, const void* T, const void* 
     if (p->x2ok && !lim && x2_ytma_supported(p->cfg, p->gf)) cands.push_back({7, 0});
     if (p->x2ok && x2_tmaps_supported(p->cfg, p->gf))
         for (int nz : {0, -1, 32}) cands.push_back({8, nz});
+    if (p->xqok)
+        for (int nz : {0, 16, 32}) cands.push_back({10, nz});
     void* scratch = nullptr;
     RKL_CK(p, cudaMalloc(&scratch, (size_t)p->ncell * p->esize));
     cudaEvent_t a = nullptr, e = nullptr;
@@ -931,11 +937,14 @@ rkl_status rkl_plan_autotune(rkl_plan* p, double dt, const void* T, const void* 
 rkl_status rkl_plan_set_variant(rkl_plan* p, int variant, int nzchunk)
 {
     if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
-    if (variant < 0 || variant > 9) return fail(p, RKL_ERR_INVALID_ARG, "variant must be 0 to 9");
+    if (variant < 0 || variant > 10) return fail(p, RKL_ERR_INVALID_ARG, "variant must be 0 to 10");
     if (nzchunk > 4096) return fail(p, RKL_ERR_INVALID_ARG, "nzchunk must be <= 4096");
     if (variant == 2 && !p->fast) return fail(p, RKL_ERR_UNSUPPORTED, "no tiled kernel for this grid");
-    if ((variant == 3 || variant == 4 || variant >= 6) && !p->x2ok)
+    if ((variant == 3 || variant == 4 || (variant >= 6 && variant <= 9)) && !p->x2ok)
         return fail(p, RKL_ERR_UNSUPPORTED, "no paired-cell kernel for this grid");
+    if (variant == 10 && !p->xqok)
+        return fail(p, RKL_ERR_UNSUPPORTED,
+                    "no row-pair kernel for this grid (periodic FP32 3D, nx % 4 == 0, no limiter, < 2^31 cells)");
     if (variant == 5 && !(p->pairok && p->x2ok))
         return fail(p, RKL_ERR_UNSUPPORTED, "no two-stage kernel for this grid (periodic FP32 3D, nx % 4 == 0)");
     if (variant == 5 && !p->ybuf4) {

@@ -75,7 +75,7 @@ def _sampled_first_step(rk, orc, W, dtype, cells, variant=0, tol=F32_STATE_MAX):
     return plan, Td, bd, dt, e0, P
 
 
-@pytest.mark.parametrize("variant", [0, 5, 6, 7, 8, 9])
+@pytest.mark.parametrize("variant", [0, 5, 6, 7, 8, 9, 10])
 def test_tangled_256_sampled_and_conservation(rk, orc, variant):
     """The benchmark's 256^3 workload with the default single-stage kernel,
     the two-stage kernel (tile edges at multiples of 60 and 7) and the
@@ -92,12 +92,13 @@ def test_tangled_256_sampled_and_conservation(rk, orc, variant):
     assert plan.check() == 0
 
 
-def test_blob_512_saturated_sampled_and_conservation(rk, orc):
+@pytest.mark.parametrize("variant", [0, 3, 10])
+def test_blob_512_saturated_sampled_and_conservation(rk, orc, variant):
     W = workloads.blob(512, seed=2)
     rng = np.random.default_rng(1)
     cells = [(256, 256, 256), (256, 270, 240), (230, 256, 290)] + \
             [tuple(int(v) for v in rng.integers(0, 512, 3)) for _ in range(2)]
-    plan, Td, bd, dt, e0, P = _sampled_first_step(rk, orc, W, "f32", cells)
+    plan, Td, bd, dt, e0, P = _sampled_first_step(rk, orc, W, "f32", cells, variant)
     for _ in range(W.n_super - 1):
         s, eb, ea = plan.super_step(dt, Td, bd, energies=True)
         assert abs(ea - eb) <= 1e-6 * abs(eb)

@@ -144,8 +144,8 @@ def _variant_cases():
     # grids with nx % 4 == 0 (the paired-cell kernel) and Dirichlet partial tiles
     spitz = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
     sat = dict(kappa_model="spitzer", kappa_par0=0.01, saturate=True, phi=0.3)
-    for v in (2, 3, 4, 5, 6, 7, 8, 9):
-        if v not in (5, 6, 8):  # the two-stage kernel, bulk and tensor-map copies are periodic only
+    for v in (2, 3, 4, 5, 6, 7, 8, 9, 10):
+        if v not in (5, 6, 8, 10):  # two-stage, bulk, tensor-map and row-pair kernels are periodic only
             out.append(("3d_x4_dirichlet", (21, 19, 36), dict(spitz, bc="dirichlet", bc_value=0.9), "f32", v))
         out.append(("3d_x4_sat", (18, 26, 68), sat, "f32", v))
         out.append(("3d_x4_sat_upwind", (10, 9, 132), dict(sat, phi=0.05, sat_upwind=True), "f32", v))
@@ -181,6 +181,11 @@ def _variant_cases():
     out.append(("3d_cols32_ragged", (9, 21, 68), spitz, "f32", 9))
     out.append(("3d_cols32_narrow", (12, 10, 32), spitz, "f32", 9))
     out.append(("3d_cols32_dirichlet", (7, 13, 96), dict(spitz, bc="dirichlet", bc_value=0.9), "f32", 9))
+    # row-pair kernel (two rows per warp, 64 x 8 tiles): ragged tile rows and
+    # columns, a grid lower than one tile, one narrower than one tile
+    out.append(("3d_rowpair_ragged", (37, 21, 200), spitz, "f32", 10))
+    out.append(("3d_rowpair_low", (11, 5, 136), spitz, "f32", 10))
+    out.append(("3d_rowpair_narrow", (19, 17, 36), sat, "f32", 10))
     return out
 
 
@@ -226,7 +231,7 @@ def test_tiled_kernels_match_generic(rk, orc, shape, nzchunk):
     whose runs cross tile columns) and the generic kernel (variant 1) on
     tile-aligned, ragged and degenerate shapes; all against the oracle."""
     params = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
-    variants = (1, 2, 3, 4, 5, 6, 8, 9) if shape[2] % 4 == 0 else (1, 2)
+    variants = (1, 2, 3, 4, 5, 6, 8, 9, 10) if shape[2] % 4 == 0 else (1, 2)
     res = {}
     for v in variants:
         P, plan, T, b, Td, bd = _setup(rk, "x", shape, params, "f32", v)
@@ -242,6 +247,52 @@ def test_tiled_kernels_match_generic(rk, orc, shape, nzchunk):
     for v in variants:
         assert rel_l2(res[v], Tref) < F32_STATE_REL_L2, v
         assert norm_max(res[v], res[1]) < F32_STATE_MAX, v
+
+
+@pytest.mark.parametrize("params", [
+    dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4),
+    dict(kappa_model="spitzer", kappa_par0=0.01, saturate=True, phi=0.3),
+    dict(kappa_par0=0.02, kappa_perp_ratio=0.1, saturate=True, phi=0.003),
+    dict(kappa_model="spitzer", kappa_par0=0.01, saturate=True, phi=0.05, sat_upwind=True),
+    dict(kappa_par0=0.02, kappa_perp_ratio=0.1),
+], ids=["spitzer", "sat", "sat_const", "sat_upwind", "const"])
+@pytest.mark.parametrize("shape,nzchunk", [((37, 21, 200), 0), ((16, 16, 128), 0), ((40, 9, 68), 7),
+                                           ((3, 8, 64), 1), ((24, 40, 4), 0)])
+def test_row_pair_kernel_same_bits_as_paired_cell(rk, orc, params, shape, nzchunk):
+    """The row-pair kernel (variant 10) evaluates every face, slope,
+    divergence term and update as the paired-cell kernel (variant 3) does,
+    with tile boundaries at other rows (multiples of 8 against 4) and other
+    z-chunks: after two super-steps (every stage, the first one included)
+    the two states agree bit for bit, and with the oracle."""
+    import torch
+    res = {}
+    for v in (3, 10):
+        P, plan, T, b, Td, bd = _setup(rk, "x", shape, params, "f32", v)
+        plan.set_variant(v, nzchunk)
+        dt = 60 * orc.dt_expl(P, T)
+        for _ in range(2):
+            plan.super_step(dt, Td, bd)
+        assert plan.check() == 0
+        res[v] = Td.clone()
+    assert torch.equal(res[3], res[10])
+    Tref = T
+    for _ in range(2):
+        Tref, _ = orc.super_step(P, Tref, b, dt)
+    assert rel_l2(host(res[10]), Tref) < F32_STATE_REL_L2
+
+
+def test_row_pair_kernel_unsupported_plans(rk):
+    """Variant 10 takes periodic FP32 3D grids with nx % 4 == 0 and no
+    limiter; any other plan is refused, not silently routed elsewhere."""
+    spitz = dict(kappa_model="spitzer", kappa_par0=0.01)
+    for shape, params, dtype in [((8, 8, 30), spitz, "f32"),
+                                 ((8, 8, 32), dict(spitz, bc="dirichlet", bc_value=1.0), "f32"),
+                                 ((8, 8, 32), dict(spitz, limiter="mc"), "f32"),
+                                 ((8, 8, 32), spitz, "f64"),
+                                 ((16, 32), spitz, "f32")]:
+        plan = rk.Plan(shape, dtype, params=params)
+        with pytest.raises(Exception):
+            plan.set_variant(10)
 
 
 @pytest.mark.parametrize("shape,nzchunk", [((7, 9, 4), 0), ((40, 3, 68), 0), ((1, 33, 64), 0), ((37, 24, 128), 5),
@@ -281,7 +332,7 @@ def test_autotune_keeps_input_and_parity(rk, orc):
     T_before = Td.clone()
     v, nz, ms = plan.autotune(dt, Td, bd)
     assert torch.equal(Td, T_before)
-    assert 1 <= v <= 9 and ms > 0            # any kernel that applies to the grid
+    assert 1 <= v <= 10 and ms > 0           # any kernel that applies to the grid
     plan.super_step(dt, Td, bd)
     Tref, _ = orc.super_step(P, T, b, dt)
     assert rel_l2(host(Td), Tref) < F32_STATE_REL_L2
