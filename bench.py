@@ -509,7 +509,8 @@ def run_ensemble(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "ensemble64", "problems": 64, "cells": int(ens.offsets[-1]),
-                       "schedule": "persistent" if pers else "per-launch", "nzchunk": nz,
+                       "schedule": ("persistent" if pers & 1 else "per-launch")
+                       + (", row-pair tiles" if pers & 2 else ", paired-cell tiles"), "nzchunk": nz,
                        "step": "one super-step of every problem (statistics pass + stages)"},
             "roofline": {"bound": "hbm", "kernel": "whole ensemble step", "achieved": 32 * value,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": 32 * value / peak,
@@ -711,7 +712,7 @@ def main():
     ap.add_argument("--variant", type=int, default=0,
                     help="stage kernel: 0 auto, 1 generic, 2 tiled, 3/4 paired-cell at 5/6 CTAs per SM, 5 two-stage, "
                          "6 bulk copies, 7 tensor-map Y copies, 8 every bundle from tensor maps, "
-                         "9 32-column tiles, 10 row-pair (two cell pairs per thread)")
+                         "9 32-column tiles, 10 row-pair (two cell pairs per thread), 11 row-pair with 32-column tiles")
     ap.add_argument("--nzchunk", type=int, default=0, help="planes per CTA (0 automatic, < 0 balanced runs)")
     ap.add_argument("--limiter", default="none", choices=["none", "mc"],
                     help="transverse gradients: plain averages, or MC-limited at every face (Appendix C; "

@@ -276,7 +276,10 @@ rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
  * per thread, rows 2w and 2w + 1 of 64 x 8 tiles, three CTAs per SM; the
  * same bits as the paired-cell kernel; periodic grids with fewer than 2^31
  * cells, nx % 4 == 0, no limiter, else RKL_ERR_UNSUPPORTED; nzchunk <= 0
- * picks the chunk length).  With the MC limiter at every face
+ * picks the chunk length), 11 = the row-pair kernel with tiles 32 columns
+ * wide and 16 rows high (two row pairs per warp, one per half-warp; same
+ * conditions and bits as 10; variant 0 takes it where the width is an odd
+ * multiple of 32).  With the MC limiter at every face
  * (limiter_floor = +inf) variants 3, 4, 6 and 7 all launch the paired-cell
  * kernel's limited build (20 resident warps per SM, per-thread copies);
  * with a finite floor the paired-cell variants do not apply.
@@ -375,11 +378,18 @@ const char *rkl_ensemble_last_error(const rkl_ensemble *ens);
 rkl_status rkl_ensemble_layout(const rkl_ensemble *ens, int64_t *cell_offsets);
 
 /*
- * Schedule of rkl_ensemble_super_step: persistent = 1 runs every stage of
- * every problem in one persistent launch (work items (problem, stage, tile)
- * in stage-major order; a tile of stage j waits, with a bounded spin, until
- * all tiles of stage j-1 of its problem are done); persistent = 0 launches
- * one kernel per problem and stage.  nzchunk = planes per tile (<= 0: 32).
+ * Schedule of rkl_ensemble_super_step, two flags: bit 0 (persistent = 1 or
+ * 3) runs every stage of every problem in one persistent launch (work items
+ * (problem, stage, tile) in stage-major order; a tile of stage j waits,
+ * with a bounded spin, until all tiles of stage j-1 of its problem are
+ * done), else one kernel is launched per problem and stage; bit 1
+ * (persistent = 2 or 3) takes the row-pair tile body (64 x 8 tiles, or
+ * 32 x 16 for widths that are odd multiples of 32; three CTAs per SM)
+ * instead of the paired-cell one (64 x 4, or 32 x 8; five CTAs per SM).
+ * The two tile bodies write the same bits.  nzchunk = planes per tile
+ * (<= 0: 32).  RKL_ERR_INVALID_ARG for persistent outside 0..3;
+ * RKL_ERR_UNSUPPORTED for the row-pair tiles unless every problem is
+ * periodic with fewer than 2^31 cells (the autotuner then skips them).
  */
 rkl_status rkl_ensemble_set_schedule(rkl_ensemble *ens, int persistent, int nzchunk);
 
@@ -399,7 +409,8 @@ rkl_status rkl_ensemble_check(rkl_ensemble *ens);
 
 /*
  * Autotuner: times one super-step of every candidate schedule (persistent
- * with nzchunk 8, 16, 32; per-launch with 16, 32) on a scratch copy of
+ * with nzchunk 8, 16, 32; per-launch with 16, 32; each with either tile
+ * body) on a scratch copy of
  * T_all (T_all itself is not changed), keeps the fastest and returns it.
  * Allocates and frees one T_all-sized scratch array.
  */

@@ -343,8 +343,8 @@ def rkl_ensemble_layout(ens, nprob: int):
     return list(out)
 
 
-def rkl_ensemble_set_schedule(ens, persistent: bool, nzchunk: int = 0):
-    _echeck(load().rkl_ensemble_set_schedule(ens, int(bool(persistent)), int(nzchunk)), ens)
+def rkl_ensemble_set_schedule(ens, persistent: int, nzchunk: int = 0):
+    _echeck(load().rkl_ensemble_set_schedule(ens, int(persistent), int(nzchunk)), ens)
 
 
 def rkl_ensemble_super_step(ens, dt, T_all, b_all):

@@ -227,8 +227,12 @@ rkl_status launch_stage(rkl_plan* p, const StageIO& io, double mu, double nu, do
         KCoef<float> cf{(float)mu, (float)nu, (float)mt, (float)gt};
         bool al = aligned16(io.Y0) && aligned16(io.MY0) && aligned16(io.Yjm1) && aligned16(io.Yjm2) &&
                   aligned16(io.Yj) && aligned16(io.b);
-        if ((p->variant == 0 || p->variant == 10) && p->xqok && al)
-            e = launch_stage_xq(p->cfg, p->gf, p->pf, io, cf, p->d_status, p->nzchunk, st);
+        if ((p->variant == 0 || p->variant == 10 || p->variant == 11) && p->xqok && al) {
+            // automatic choice: 32-column tiles where they leave fewer columns idle
+            const int nx = (int)p->gf.n[0];
+            const bool narrow = p->variant == 11 || (p->variant == 0 && (nx + 31) / 32 * 32 < (nx + 63) / 64 * 64);
+            e = launch_stage_xq(p->cfg, p->gf, p->pf, io, cf, p->d_status, p->nzchunk, st, narrow ? 32 : 64);
+        }
         else if (p->x2ok && al && (p->variant == 0 || (p->variant >= 3 && p->variant <= 9)))
             e = launch_stage_x2(p->cfg, p->gf, p->pf, io, cf, p->d_status, p->nzchunk,
                                 p->variant == 4 ? 3 : (p->variant == 9 ? 6 : 2), st, p->variant == 6,
@@ -894,7 +898,10 @@ rkl_status rkl_plan_autotune(rkl_plan* p, double dt, const void* T, const void* 
     if (p->x2ok && x2_tmaps_supported(p->cfg, p->gf))
         for (int nz : {0, -1, 32}) cands.push_back({8, nz});
     if (p->xqok)
-        for (int nz : {0, 16, 32}) cands.push_back({10, nz});
+        for (int nz : {0, 16, 32}) {
+            cands.push_back({10, nz});
+            cands.push_back({11, nz});
+        }
     void* scratch = nullptr;
     RKL_CK(p, cudaMalloc(&scratch, (size_t)p->ncell * p->esize));
     cudaEvent_t a = nullptr, e = nullptr;
@@ -937,12 +944,12 @@ rkl_status rkl_plan_autotune(rkl_plan* p, double dt, const void* T, const void* 
 rkl_status rkl_plan_set_variant(rkl_plan* p, int variant, int nzchunk)
 {
     if (check_plan(p) != RKL_OK) return RKL_ERR_INVALID_ARG;
-    if (variant < 0 || variant > 10) return fail(p, RKL_ERR_INVALID_ARG, "variant must be 0 to 10");
+    if (variant < 0 || variant > 11) return fail(p, RKL_ERR_INVALID_ARG, "variant must be 0 to 11");
     if (nzchunk > 4096) return fail(p, RKL_ERR_INVALID_ARG, "nzchunk must be <= 4096");
     if (variant == 2 && !p->fast) return fail(p, RKL_ERR_UNSUPPORTED, "no tiled kernel for this grid");
     if ((variant == 3 || variant == 4 || (variant >= 6 && variant <= 9)) && !p->x2ok)
         return fail(p, RKL_ERR_UNSUPPORTED, "no paired-cell kernel for this grid");
-    if (variant == 10 && !p->xqok)
+    if ((variant == 10 || variant == 11) && !p->xqok)
         return fail(p, RKL_ERR_UNSUPPORTED,
                     "no row-pair kernel for this grid (periodic FP32 3D, nx % 4 == 0, no limiter, < 2^31 cells)");
     if (variant == 5 && !(p->pairok && p->x2ok))

@@ -1,8 +1,8 @@
 // Ensembles of independent problems advanced together (host side of the C
 // ABI's rkl_ensemble_* entry points).  One super-step of every problem is
-// either one persistent launch of the paired-cell tile body over a
-// stage-major work list (default) or, as the alternative schedule, one
-// kernel launch per problem and stage.  Problems keep their own grid size,
+// either one persistent launch of a tile body (paired-cell or row-pair)
+// over a stage-major work list (default) or, as the alternative schedule,
+// one kernel launch per problem and stage.  Problems keep their own grid size,
 // conductivity, super-step and stage count.
 #include <algorithm>
 #include <cmath>
@@ -59,8 +59,9 @@ struct rkl_ensemble {
     unsigned* d_status = nullptr;
     unsigned* h_status = nullptr;        // pinned
 
-    int persistent = 1;
+    int persistent = 1;                  // schedule: bit 0 persistent launch, bit 1 row-pair tiles
     int nzchunk = 32;
+    bool rowpair_ok = true;              // every problem periodic with < 2^31 cells
     long long spin_limit = 20000000;     // ~ a few seconds of bounded waiting
     std::vector<int> last_s;
     std::string err;
@@ -70,13 +71,14 @@ namespace {
 
 // Tile width and counts of one problem: 32-column tiles where they cover
 // the width with fewer idle columns than 64-column ones (nx an odd
-// multiple of 32, e.g. 32 or 96), else 64-column tiles.
-void set_tiles(x2::EnsProb& d, int nzchunk)
+// multiple of 32, e.g. 32 or 96), else 64-column tiles.  Paired-cell tiles
+// are 4 (64 columns) or 8 (32 columns) rows high, row-pair tiles 8 or 16.
+void set_tiles(x2::EnsProb& d, int nzchunk, bool rowpair)
 {
     const int nx = d.g.n[0];
     const bool narrow = (nx + 31) / 32 * 32 < (nx + 63) / 64 * 64;
     d.txw = narrow ? 32 : x2::TX;
-    const int tyh = x2::NTHREADS / (d.txw / 2);
+    const int tyh = (rowpair ? 2 : 1) * x2::NTHREADS / (d.txw / 2);
     d.tx = (nx + d.txw - 1) / d.txw;
     d.ty = (d.g.n[1] + tyh - 1) / tyh;
     d.tz = (d.g.n[2] + nzchunk - 1) / nzchunk;
@@ -182,11 +184,11 @@ rkl_status ens_run(rkl_ensemble* e, const double* dt, const int* s, float* T_all
         d.coef = e->d_coef + cofs[p];
         d.s = s[p];
         d.nzchunk = e->nzchunk;
-        set_tiles(d, e->nzchunk);
+        set_tiles(d, e->nzchunk, (e->persistent & 2) != 0);
         total_items += d.ntiles * s[p];
     }
     ENS_CK(e, cudaMemcpyAsync(e->d_coef, e->h_coef, sizeof(float) * cofs[np], cudaMemcpyHostToDevice, e->stream));
-    if (e->persistent) {
+    if (e->persistent & 1) {
         // stage-major work list
         int nseg = 0;
         for (int j = 1; j <= smax; ++j)
@@ -208,9 +210,13 @@ rkl_status ens_run(rkl_ensemble* e, const double* dt, const int* s, float* T_all
         ENS_CK(e, cudaMemsetAsync(e->d_work, 0, sizeof(int), e->stream));
         ENS_CK(e, cudaMemsetAsync(e->d_abort, 0, sizeof(int), e->stream));
         ENS_CK(e, cudaMemsetAsync(e->d_done, 0, sizeof(unsigned) * np, e->stream));
-        cudaError_t c = launch_ensemble_x2(e->spitzer, e->saturate, e->d_probs, e->d_segs, nseg, total_items,
-                                           e->d_work, e->d_done, e->d_status, e->d_abort, e->spin_limit, 0,
-                                           e->stream);
+        cudaError_t c = (e->persistent & 2)
+                            ? launch_ensemble_xq(e->spitzer, e->saturate, e->d_probs, e->d_segs, nseg, total_items,
+                                                 e->d_work, e->d_done, e->d_status, e->d_abort, e->spin_limit, 0,
+                                                 e->stream)
+                            : launch_ensemble_x2(e->spitzer, e->saturate, e->d_probs, e->d_segs, nseg, total_items,
+                                                 e->d_work, e->d_done, e->d_status, e->d_abort, e->spin_limit, 0,
+                                                 e->stream);
         if (c != cudaSuccess) return efail(e, RKL_ERR_CUDA, std::string("ensemble launch: ") + cudaGetErrorString(c));
     } else {
         // one launch per problem and stage, stage-major
@@ -235,8 +241,11 @@ rkl_status ens_run(rkl_ensemble* e, const double* dt, const int* s, float* T_all
                 }
                 LaunchCfg cfg{0, 3, e->spitzer ? 1 : 0, e->saturate ? 1 : 0, 0};
                 KCoef<float> cf{0.f, 0.f, 0.f, 0.f};
-                cudaError_t c = launch_stage_x2(cfg, d.g, d.p, io, cf, e->d_status, e->nzchunk,
-                                                d.txw == 32 ? 6 : 2, e->stream);
+                cudaError_t c = (e->persistent & 2)
+                                    ? launch_stage_xq(cfg, d.g, d.p, io, cf, e->d_status, e->nzchunk, e->stream,
+                                                      d.txw)
+                                    : launch_stage_x2(cfg, d.g, d.p, io, cf, e->d_status, e->nzchunk,
+                                                      d.txw == 32 ? 6 : 2, e->stream);
                 if (c != cudaSuccess) return efail(e, RKL_ERR_CUDA, std::string("stage launch: ") + cudaGetErrorString(c));
             }
     }
@@ -319,6 +328,7 @@ rkl_status rkl_ensemble_create(int nprob, const rkl_grid* grids, const rkl_phys*
         kg.bcv = (float)g.bc_value;
         kg.plane = g.n[0] * g.n[1];
         kg.ncell = n;
+        if (g.bc != RKL_PERIODIC || n >= ((int64_t)1 << 31)) e->rowpair_ok = false;
         kp.kappa0 = (float)phys[p].kappa_par0;
         kp.kperp = (float)phys[p].kappa_perp_ratio;
         kp.q0 = (float)(5.0 * phys[p].phi * phys[p].rho);
@@ -410,7 +420,10 @@ rkl_status rkl_ensemble_set_schedule(rkl_ensemble* e, int persistent, int nzchun
 {
     if (!e) return RKL_ERR_INVALID_ARG;
     if (nzchunk < 0 || nzchunk > 4096) return efail(e, RKL_ERR_INVALID_ARG, "nzchunk must be in [0, 4096]");
-    e->persistent = persistent ? 1 : 0;
+    if (persistent < 0 || persistent > 3) return efail(e, RKL_ERR_INVALID_ARG, "schedule must be 0 to 3");
+    if ((persistent & 2) && !e->rowpair_ok)
+        return efail(e, RKL_ERR_UNSUPPORTED, "row-pair tiles need every problem periodic with fewer than 2^31 cells");
+    e->persistent = persistent;
     e->nzchunk = nzchunk > 0 ? nzchunk : 32;
     return RKL_OK;
 }
@@ -465,11 +478,12 @@ rkl_status rkl_ensemble_autotune(rkl_ensemble* e, const double* dt, const void* 
     cudaEvent_t a = nullptr, b = nullptr;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    const int cand[][2] = {{1, 8}, {1, 16}, {1, 32}, {0, 16}, {0, 32}};
+    const int cand[][2] = {{1, 8}, {1, 16}, {1, 32}, {3, 8}, {3, 16}, {3, 32}, {0, 16}, {0, 32}, {2, 16}, {2, 32}};
     double best = 1e300;
     int bp = 1, bz = 32;
     const int keep_p = e->persistent, keep_z = e->nzchunk;
     for (const auto& c : cand) {
+        if ((c[0] & 2) && !e->rowpair_ok) continue;
         e->persistent = c[0];
         e->nzchunk = c[1];
         float ms_sum = 0.f;
@@ -517,7 +531,7 @@ rkl_status rkl_ensemble_selftest_timeout(rkl_ensemble* e, int* status_out)
     d.g = e->kg[0];
     d.p = e->kp[0];
     d.nzchunk = e->nzchunk;
-    set_tiles(d, e->nzchunk);
+    set_tiles(d, e->nzchunk, false);
     d.s = 2;
     e->h_probs[0] = d;
     rkl_status st = grow_pinned(e, &e->d_segs, &e->h_segs, &e->seg_cap, 1);

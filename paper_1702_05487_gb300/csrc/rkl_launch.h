@@ -76,12 +76,13 @@ cudaError_t launch_stage_x2(const LaunchCfg& c, const KGrid<float>& g, const KPh
 
 // Row-pair FP32 3D stage kernel: the paired-cell kernel's arithmetic with
 // two cell pairs per thread (rows 2w, 2w + 1 of 64 x 8 tiles, three CTAs per
-// SM), writing the same bits.  Periodic grids, nx % 4 == 0, no limiter,
-// fewer than 2^31 cells, 16-byte aligned arrays; nzchunk <= 0 picks the
-// chunk length.
+// SM; txw = 32: 32 x 16 tiles, two row pairs per warp), writing the same
+// bits.  Periodic grids, nx % 4 == 0, no limiter, fewer than 2^31 cells,
+// 16-byte aligned arrays; nzchunk <= 0 picks the chunk length.
 bool xq_stage_supported(const LaunchCfg& c, const KGrid<float>& g);
 cudaError_t launch_stage_xq(const LaunchCfg& c, const KGrid<float>& g, const KPhys<float>& p, const StageIO& io,
-                            const KCoef<float>& coef, unsigned* status, int nzchunk, cudaStream_t st);
+                            const KCoef<float>& coef, unsigned* status, int nzchunk, cudaStream_t st,
+                            int txw = 64);
 
 // Two-stage paired-cell FP32 3D kernel: stages j (io, coefficients at
 // io.coef_tab[4 j]) and j + 1 (written to Yj1) in one pass, 60 x 7 tiles of

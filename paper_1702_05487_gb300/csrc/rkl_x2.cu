@@ -182,13 +182,6 @@ cudaError_t launch_stage_x2(const LaunchCfg& c, const KGrid<float>& g, const KPh
 
 namespace {
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 template <bool SP, bool SAT>
 __global__ void __launch_bounds__(x2::NTHREADS, x2::kCtasPerSm)
 ensemble_x2_kernel(const x2::EnsProb* __restrict__ probs, const x2::EnsSeg* __restrict__ segs, int nseg,
@@ -200,33 +193,11 @@ ensemble_x2_kernel(const x2::EnsProb* __restrict__ probs, const x2::EnsSeg* __re
     __shared__ int s_go, s_p, s_j, s_tile;
     for (;;) {
         if (threadIdx.x == 0) {
-            int go = 1;
-            const int it = atomicAdd(work, 1);
-            if (it >= total || *reinterpret_cast<volatile int*>(abort_flag)) {
-                go = 0;
-            } else {
-                int lo = 0, hi = nseg - 1;                 // last segment with first <= it
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (segs[mid].first <= it) lo = mid; else hi = mid - 1;
-                }
-                const x2::EnsSeg sg = segs[lo];
-                const unsigned target = (unsigned)((sg.j - 1) * probs[sg.p].ntiles);
-                long long n = 0;
-                while (ld_acquire(&done[sg.p]) < target) {
-                    if (++n > spin_limit || *reinterpret_cast<volatile int*>(abort_flag)) {
-                        atomicOr(status, ST_TIMEOUT);
-                        atomicExch(abort_flag, 1);
-                        go = 0;
-                        break;
-                    }
-                    __nanosleep(128);
-                }
-                s_p = sg.p;
-                s_j = sg.j;
-                s_tile = it - sg.first;
-            }
-            s_go = go;
+            int p = 0, j = 0, tile = 0;
+            s_go = x2::ens_claim(probs, segs, nseg, total, work, done, status, abort_flag, spin_limit, p, j, tile);
+            s_p = p;
+            s_j = j;
+            s_tile = tile;
         }
         __syncthreads();
         if (!s_go) break;

@@ -105,7 +105,52 @@ struct EnsSeg {
     int count;
 };
 
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// The next work item of a persistent ensemble launch, claimed by thread 0
+// of the CTA from the global counter in the fixed stage-major order: sets
+// (p, j, tile) and returns true once the item may run (every tile of stage
+// j - 1 of problem p is done); false when the list is exhausted, another
+// CTA gave up, or this CTA's bounded wait ran out (then ST_TIMEOUT and the
+// abort flag are set).
+__device__ __forceinline__ bool ens_claim(const EnsProb* probs, const EnsSeg* segs, int nseg, int total, int* work,
+                                          const unsigned* done, unsigned* status, int* abort_flag,
+                                          long long spin_limit, int& p, int& j, int& tile)
+{
+    const int it = atomicAdd(work, 1);
+    if (it >= total || *reinterpret_cast<volatile int*>(abort_flag)) return false;
+    int lo = 0, hi = nseg - 1;                 // last segment with first <= it
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].first <= it) lo = mid; else hi = mid - 1;
+    }
+    const EnsSeg sg = segs[lo];
+    const unsigned target = (unsigned)((sg.j - 1) * probs[sg.p].ntiles);
+    long long n = 0;
+    while (ld_acquire(&done[sg.p]) < target) {
+        if (++n > spin_limit || *reinterpret_cast<volatile int*>(abort_flag)) {
+            atomicOr(status, ST_TIMEOUT);
+            atomicExch(abort_flag, 1);
+            return false;
+        }
+        __nanosleep(128);
+    }
+    p = sg.p;
+    j = sg.j;
+    tile = it - sg.first;
+    return true;
+}
+
 }  // namespace x2
+
+cudaError_t launch_ensemble_xq(bool spitzer, bool saturate, const x2::EnsProb* probs, const x2::EnsSeg* segs,
+                               int nseg, int total, int* work, unsigned* done, unsigned* status, int* abort_flag,
+                               long long spin_limit, int grid, cudaStream_t st);
 
 cudaError_t launch_ensemble_x2(bool spitzer, bool saturate, const x2::EnsProb* probs, const x2::EnsSeg* segs,
                                int nseg, int total, int* work, unsigned* done, unsigned* status, int* abort_flag,

@@ -1,6 +1,9 @@
 // Row-pair FP32 3D stage kernel for the RKL2 conduction super-step: the
 // paired-cell kernel's arithmetic with each thread owning two cell pairs,
 // (2l, 2l + 1) in rows 2w and 2w + 1 of a 64 x 8 tile (lane l, warp w).
+// With 32-column tiles (for grids whose width is an odd multiple of 32) a
+// warp holds two row pairs side by side in its lane halves: lanes 0-15 rows
+// 4w, 4w + 1 and lanes 16-31 rows 4w + 2, 4w + 3 of a 32 x 16 tile.
 //
 // What a thread shares between its two rows instead of reading or
 // exchanging it: the y-face between them (its own, in registers; only row
@@ -35,31 +38,36 @@ using x2::mul2;
 using x2::smem_u32;
 using x2::sub2;
 
-constexpr int TX = 64;                  // tile columns: 32 lanes x 2 cells
-constexpr int TY = 8;                   // tile rows: two per warp
 constexpr int NTHREADS = 128;
-constexpr int SXS = TX + 8;             // smem row: halo chunk, 64 interior, halo chunk
-constexpr int CPR = SXS / 4;            // 16-byte chunks per smem row
-constexpr int ROWS = TY + 2;
-constexpr int PLANE = ROWS * SXS;
+constexpr int NWARPS = NTHREADS / 32;
 constexpr int PD = 2;                   // planes in flight
 constexpr int kCtasPerSm = 3;
-constexpr int kPos = ROWS * CPR;        // T / b chunk positions of a plane (180)
-constexpr int kYPos = TY * (TX / 4);    // Y chunk positions (128: one per thread)
-static_assert(kPos <= 2 * NTHREADS && kYPos == NTHREADS, "copy positions");
 
-// Rings: T planes q-1, q, q+1 and those in flight; b planes q, q+1 and
-// those in flight; Y planes q and those in flight (a plane's Y bundle is
-// issued one plane after its T and b, as it is read one plane later).
-struct Smem {
+// Geometry and rings of one tile TXW columns wide (64 or 32): TXW / 2 lanes
+// per row pair, 32 / (TXW / 2) row pairs per warp.  Rings: T planes q-1,
+// q, q+1 and those in flight; b planes q, q+1 and those in flight; Y planes
+// q and those in flight (a plane's Y bundle is issued one plane after its T
+// and b, as it is read one plane later).
+template <int TXW>
+struct SmemQ {
+    static constexpr int TX = TXW, LPR = TXW / 2, SEGS = 32 / LPR;
+    static constexpr int TY = 2 * SEGS * NWARPS;        // 8 rows (64 columns) or 16 (32 columns)
+    static constexpr int NRP = TY / 2;                  // row pairs
+    static constexpr int SXS = TX + 8;                  // smem row: halo chunk, interior, halo chunk
+    static constexpr int CPR = SXS / 4;                 // 16-byte chunks per smem row
+    static constexpr int ROWS = TY + 2, PLANE = ROWS * SXS;
+    static constexpr int kPos = ROWS * CPR;             // T / b chunk positions of a plane (180)
+    static constexpr int kYPos = TY * (TX / 4);         // Y chunk positions (128: one per thread)
+    static_assert(kPos <= 2 * NTHREADS && kYPos == NTHREADS, "copy positions");
     static constexpr int NT = 3 + PD, NB = 2 + PD, NY = 1 + PD;
     alignas(16) float T[NT][PLANE];
     float B[NB][3][PLANE];
     float Y[NY][3][TY * TX];
-    float Fy[2][TY / 2 + 1][TX];    // row k: lower y-face of row 2k (k = 0: the tile's boundary)
+    float Fy[2][NRP + 1][TX];       // row k: lower y-face of row 2k (k = 0: the tile's boundary)
     float FxLo[2][TY];              // x-faces on the tile's left boundary
     __device__ static int off(int r, int c) { return (r + 1) * SXS + c + 4; }
 };
+using Smem = SmemQ<64>;
 
 // A thread's two rows of one plane: T, the x / y slopes (centred
 // differences) and b at the pair of each row, T at column c + 2, and T one
@@ -72,18 +80,19 @@ struct QZ2 {
     float2 b0[3], b1[3];
 };
 
-__device__ __forceinline__ QZ2 read_qz2(const Smem& sm, int ts, int bs, int c, int ra)
+template <class SM>
+__device__ __forceinline__ QZ2 read_qz2(const SM& sm, int ts, int bs, int c, int ra)
 {
     const int rb = ra + 1;
     const float* T = sm.T[ts];
     QZ2 q;
-    const float2 Td = lds2(&T[Smem::off(ra - 1, c)]);
-    const float2 Tc0 = lds2(&T[Smem::off(ra, c)]);
-    const float2 Tc1 = lds2(&T[Smem::off(rb, c)]);
-    const float2 Tu = lds2(&T[Smem::off(rb + 1, c)]);
-    const float l0 = T[Smem::off(ra, c - 1)], l1 = T[Smem::off(rb, c - 1)];
-    q.r0 = T[Smem::off(ra, c + 2)];
-    q.r1 = T[Smem::off(rb, c + 2)];
+    const float2 Td = lds2(&T[SM::off(ra - 1, c)]);
+    const float2 Tc0 = lds2(&T[SM::off(ra, c)]);
+    const float2 Tc1 = lds2(&T[SM::off(rb, c)]);
+    const float2 Tu = lds2(&T[SM::off(rb + 1, c)]);
+    const float l0 = T[SM::off(ra, c - 1)], l1 = T[SM::off(rb, c - 1)];
+    q.r0 = T[SM::off(ra, c + 2)];
+    q.r1 = T[SM::off(rb, c + 2)];
     q.T0 = Tc0;
     q.T1 = Tc1;
     q.TU = Tu;
@@ -93,8 +102,8 @@ __device__ __forceinline__ QZ2 read_qz2(const Smem& sm, int ts, int bs, int c, i
     q.gy1 = x2::cslope<false>(Tu, Tc1, Tc0);
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-        q.b0[e] = lds2(&sm.B[bs][e][Smem::off(ra, c)]);
-        q.b1[e] = lds2(&sm.B[bs][e][Smem::off(rb, c)]);
+        q.b0[e] = lds2(&sm.B[bs][e][SM::off(ra, c)]);
+        q.b1[e] = lds2(&sm.B[bs][e][SM::off(rb, c)]);
     }
     return q;
 }
@@ -107,30 +116,38 @@ struct Pos {
     unsigned src, dst;
 };
 
+template <class SM>
 __device__ __forceinline__ Pos tb_pos(const KGrid<float>& g, int t, int i0, int j0)
 {
-    if (t >= kPos) return Pos{0u, ~0u};
-    const int row = t / CPR - 1, cc = (t % CPR) * 4 - 4;
+    if (t >= SM::kPos) return Pos{0u, ~0u};
+    const int row = t / SM::CPR - 1, cc = (t % SM::CPR) * 4 - 4;
     const int gy = x2::pmod(j0 + row, g.n[1]), gx = x2::pmod(i0 + cc, g.n[0]);
-    return Pos{(unsigned)gy * (unsigned)g.n[0] + (unsigned)gx, (unsigned)(Smem::off(row, cc) * 4)};
+    return Pos{(unsigned)gy * (unsigned)g.n[0] + (unsigned)gx, (unsigned)(SM::off(row, cc) * 4)};
 }
 
+template <class SM>
 __device__ __forceinline__ Pos y_pos(const KGrid<float>& g, int t, int i0, int j0)
 {
+    constexpr int TX = SM::TX;
     const int row = t / (TX / 4), cc = (t % (TX / 4)) * 4;
     if (j0 + row >= g.n[1] || i0 + cc >= g.n[0]) return Pos{0u, ~0u};
     return Pos{(unsigned)(j0 + row) * (unsigned)g.n[0] + (unsigned)(i0 + cc), (unsigned)((row * TX + cc) * 4)};
 }
 
-template <bool SP, bool SAT, int MODE>
-__device__ __forceinline__ void tile_q(Smem& sm, const KGrid<float>& g, const KPhys<float>& p,
+template <bool SP, bool SAT, int MODE, int TXW>
+__device__ __forceinline__ void tile_q(SmemQ<TXW>& sm, const KGrid<float>& g, const KPhys<float>& p,
                                        const x2::FastArgs& a, KCoef<float> cf, unsigned* status, int i0, int j0,
                                        int z0, int nzc)
 {
+    using Smem = SmemQ<TXW>;
+    constexpr int TX = Smem::TX, TY = Smem::TY, LPR = Smem::LPR, SEGS = Smem::SEGS;
+    constexpr int PLANE = Smem::PLANE;
     const int tid = threadIdx.x;
-    const int lx = tid & 31;                    // pair index in the row
-    const int w = tid >> 5;                     // warp: rows 2w, 2w + 1
-    const int ra = 2 * w, rb = ra + 1;
+    const int lane = tid & 31;
+    const int lx = lane % LPR;                  // pair index in the row
+    const int w = tid >> 5;
+    const int rp = w * SEGS + lane / LPR;       // row pair: rows 2 rp, 2 rp + 1
+    const int ra = 2 * rp, rb = ra + 1;
     const int c = 2 * lx;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
 
@@ -139,8 +156,8 @@ __device__ __forceinline__ void tile_q(Smem& sm, const KGrid<float>& g, const KP
         cf.mu = t[0]; cf.nu = t[1]; cf.mt = t[2]; cf.gt = t[3];
     }
 
-    const Pos p0 = tb_pos(g, tid, i0, j0), p1 = tb_pos(g, tid + NTHREADS, i0, j0);
-    const Pos py = MODE == 2 ? y_pos(g, tid, i0, j0) : Pos{0u, ~0u};
+    const Pos p0 = tb_pos<Smem>(g, tid, i0, j0), p1 = tb_pos<Smem>(g, tid + NTHREADS, i0, j0);
+    const Pos py = MODE == 2 ? y_pos<Smem>(g, tid, i0, j0) : Pos{0u, ~0u};
     const float* bxp = a.b;
     const float* byp = a.b + g.ncell;
     const float* bzp = a.b + 2 * g.ncell;
@@ -249,7 +266,7 @@ __device__ __forceinline__ void tile_q(Smem& sm, const KGrid<float>& g, const KP
     // Tm0 / Tm1 hold T of plane qp when finish(qp) runs
     auto finish = [&](int qp) {
         const int par = qp & 1;
-        float2 M0 = fma2(lds2(&sm.Fy[par][w][c]), bc2(-cmy.x), pend0);
+        float2 M0 = fma2(lds2(&sm.Fy[par][rp][c]), bc2(-cmy.x), pend0);
         float2 M1 = pend1;
         if (lx == 0) {
             M0.x = fmaf(sm.FxLo[par][ra], -cmx.x, M0.x);
@@ -324,13 +341,15 @@ __device__ __forceinline__ void tile_q(Smem& sm, const KGrid<float>& g, const KP
                                                add2(cur.b1[1], nxt.b1[1]), fk, p);
 
         // the tile's bottom y-faces and left x-faces, by warps that rotate
-        // over the schedulers from plane to plane
+        // over the schedulers from plane to plane (32-column tiles: one
+        // warp, its lower half the y-faces, its upper half the x-faces)
         const int par = q & 1;
-        const int wy = q & 3, wx = (q + 2) & 3;
-        if (w == wy) {
+        const bool ydo = SEGS == 1 ? w == (q & 3) : (w == (q & 3) && rp == SEGS * w);
+        const bool xdo = SEGS == 1 ? (w == ((q + 2) & 3) && lx < TY) : (w == (q & 3) && rp != SEGS * w);
+        if (ydo) {
             *reinterpret_cast<float2*>(&sm.Fy[par][0][c]) =
                 x2::low_yface2<SP, SAT, false>(sm, g, p, fk, tslot(q - 1), ts, tslot(q + 1), bs, c);
-        } else if (w == wx && lx < TY) {
+        } else if (xdo) {
             sm.FxLo[par][lx] = x2::low_xface<SP, SAT, false>(sm, g, p, fk, tslot(q - 1), ts, tslot(q + 1), bs, lx);
         }
         if (MODE == 2) {
@@ -342,9 +361,9 @@ __device__ __forceinline__ void tile_q(Smem& sm, const KGrid<float>& g, const KP
             my0 = lds2(&Yp[2 * TY * TX + ra * TX + c]);
             my1 = lds2(&Yp[2 * TY * TX + rb * TX + c]);
         }
-        *reinterpret_cast<float2*>(&sm.Fy[par][w + 1][c]) = Fy1;
-        const float fl0 = __shfl_up_sync(0xffffffffu, Fx0.y, 1);
-        const float fl1 = __shfl_up_sync(0xffffffffu, Fx1.y, 1);
+        *reinterpret_cast<float2*>(&sm.Fy[par][rp + 1][c]) = Fy1;
+        const float fl0 = __shfl_up_sync(0xffffffffu, Fx0.y, 1, LPR);
+        const float fl1 = __shfl_up_sync(0xffffffffu, Fx1.y, 1, LPR);
         const float2 Fxl0 = make_float2(lx == 0 ? 0.f : fl0, Fx0.x);
         const float2 Fxl1 = make_float2(lx == 0 ? 0.f : fl1, Fx1.x);
         pend0 = fma2(sub2(Fx0, Fxl0), cmx, fma2(Fy0, cmy, mul2(sub2(Fz0, Fzl0), cmz)));
@@ -378,49 +397,144 @@ __device__ __forceinline__ void tile_q(Smem& sm, const KGrid<float>& g, const KP
     __syncthreads();
 }
 
-template <bool SP, bool SAT, int MODE>
+template <bool SP, bool SAT, int MODE, int TXW>
 __global__ void __launch_bounds__(NTHREADS, kCtasPerSm)
 stage_q_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf, unsigned* status, int nzchunk)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+    SmemQ<TXW>& sm = *reinterpret_cast<SmemQ<TXW>*>(smem_raw);
     const int z0 = blockIdx.z * nzchunk;
-    tile_q<SP, SAT, MODE>(sm, g, p, a, cf, status, blockIdx.x * TX, blockIdx.y * TY, z0, min(nzchunk, g.n[2] - z0));
+    tile_q<SP, SAT, MODE, TXW>(sm, g, p, a, cf, status, blockIdx.x * SmemQ<TXW>::TX, blockIdx.y * SmemQ<TXW>::TY,
+                               z0, min(nzchunk, g.n[2] - z0));
 }
 
-template <bool SP, bool SAT, int MODE>
+template <bool SP, bool SAT, int MODE, int TXW>
 cudaError_t launch_q(const KGrid<float>& g, const KPhys<float>& p, const x2::FastArgs& a, const KCoef<float>& cf,
                      unsigned* status, int nzchunk, cudaStream_t st)
 {
-    const int smem = (int)sizeof(Smem);
+    using SM = SmemQ<TXW>;
+    const int smem = (int)sizeof(SM);
     static bool attr_set = false;       // the attribute is per function, set once
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(stage_q_kernel<SP, SAT, MODE>,
+        cudaError_t e = cudaFuncSetAttribute(stage_q_kernel<SP, SAT, MODE, TXW>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + nzchunk - 1) / nzchunk);
-    stage_q_kernel<SP, SAT, MODE><<<grid, NTHREADS, smem, st>>>(g, p, a, cf, status, nzchunk);
+    const dim3 grid((g.n[0] + SM::TX - 1) / SM::TX, (g.n[1] + SM::TY - 1) / SM::TY, (g.n[2] + nzchunk - 1) / nzchunk);
+    stage_q_kernel<SP, SAT, MODE, TXW><<<grid, NTHREADS, smem, st>>>(g, p, a, cf, status, nzchunk);
     return cudaGetLastError();
 }
 
-template <bool SP, bool SAT>
+template <bool SP, bool SAT, int TXW>
 cudaError_t launch_q_mode(int mode, const KGrid<float>& g, const KPhys<float>& p, const x2::FastArgs& a,
                           const KCoef<float>& cf, unsigned* status, int nzchunk, cudaStream_t st)
 {
-    if (mode == 0) return launch_q<SP, SAT, 0>(g, p, a, cf, status, nzchunk, st);
-    if (mode == 1) return launch_q<SP, SAT, 1>(g, p, a, cf, status, nzchunk, st);
-    return launch_q<SP, SAT, 2>(g, p, a, cf, status, nzchunk, st);
+    if (mode == 0) return launch_q<SP, SAT, 0, TXW>(g, p, a, cf, status, nzchunk, st);
+    if (mode == 1) return launch_q<SP, SAT, 1, TXW>(g, p, a, cf, status, nzchunk, st);
+    return launch_q<SP, SAT, 2, TXW>(g, p, a, cf, status, nzchunk, st);
+}
+
+template <bool SP, bool SAT>
+cudaError_t launch_q_txw(int txw, int mode, const KGrid<float>& g, const KPhys<float>& p, const x2::FastArgs& a,
+                         const KCoef<float>& cf, unsigned* status, int nzchunk, cudaStream_t st)
+{
+    if (txw == 32) return launch_q_mode<SP, SAT, 32>(mode, g, p, a, cf, status, nzchunk, st);
+    return launch_q_mode<SP, SAT, 64>(mode, g, p, a, cf, status, nzchunk, st);
+}
+
+// Persistent ensemble kernel on the row-pair tile body: the work list,
+// dependency waits and completion counters of the paired-cell ensemble
+// kernel (x2::ens_claim), each item a 64 x 8 tile (or 32 x 16 where the
+// problem's txw is 32) of one stage of one problem.
+template <bool SP, bool SAT>
+__global__ void __launch_bounds__(NTHREADS, kCtasPerSm)
+ensemble_q_kernel(const x2::EnsProb* __restrict__ probs, const x2::EnsSeg* __restrict__ segs, int nseg, int total,
+                  int* work, unsigned* done, unsigned* status, int* abort_flag, long long spin_limit)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    SmemQ<64>& sm = *reinterpret_cast<SmemQ<64>*>(smem_raw);
+    SmemQ<32>& sm32 = *reinterpret_cast<SmemQ<32>*>(smem_raw);
+    __shared__ int s_go, s_p, s_j, s_tile;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int p = 0, j = 0, tile = 0;
+            s_go = x2::ens_claim(probs, segs, nseg, total, work, done, status, abort_flag, spin_limit, p, j, tile);
+            s_p = p;
+            s_j = j;
+            s_tile = tile;
+        }
+        __syncthreads();
+        if (!s_go) break;
+        const x2::EnsProb& d = probs[s_p];
+        const int j = s_j, tile = s_tile;
+        const int bx = tile % d.tx, by = (tile / d.tx) % d.ty, bz = tile / (d.tx * d.ty);
+        const bool narrow = d.txw == 32;
+        const int i0 = bx * d.txw, j0 = by * (narrow ? SmemQ<32>::TY : SmemQ<64>::TY);
+        const int z0 = bz * d.nzchunk;
+        const int nzc = min(d.nzchunk, d.g.n[2] - z0);
+        x2::FastArgs a;
+        a.b = d.b;
+        a.Y0 = d.T;
+        a.coef_tab = d.coef;
+        a.j = j;
+        KCoef<float> cf{0.f, 0.f, 0.f, 0.f};
+        if (j == 1) {
+            a.Tin = d.T;
+            a.Yjm2 = nullptr;
+            a.MY0in = nullptr;
+            a.MY0out = d.my0;
+            a.out = d.buf[0];
+            if (narrow) tile_q<SP, SAT, 1, 32>(sm32, d.g, d.p, a, cf, status, i0, j0, z0, nzc);
+            else tile_q<SP, SAT, 1, 64>(sm, d.g, d.p, a, cf, status, i0, j0, z0, nzc);
+        } else {
+            a.Tin = d.buf[(j - 2) % 3];
+            a.Yjm2 = j == 2 ? d.T : d.buf[(j - 3) % 3];
+            a.MY0in = d.my0;
+            a.MY0out = nullptr;
+            a.out = j == d.s ? d.T : d.buf[(j - 1) % 3];
+            if (narrow) tile_q<SP, SAT, 2, 32>(sm32, d.g, d.p, a, cf, status, i0, j0, z0, nzc);
+            else tile_q<SP, SAT, 2, 64>(sm, d.g, d.p, a, cf, status, i0, j0, z0, nzc);
+        }
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&done[s_p], 1u);
+        }
+    }
+}
+
+template <bool SP, bool SAT>
+cudaError_t ensemble_launch_q(const x2::EnsProb* probs, const x2::EnsSeg* segs, int nseg, int total, int* work,
+                              unsigned* done, unsigned* status, int* abort_flag, long long spin_limit, int grid,
+                              cudaStream_t st)
+{
+    const int smem = (int)std::max(sizeof(SmemQ<64>), sizeof(SmemQ<32>));
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(ensemble_q_kernel<SP, SAT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (grid <= 0) {
+        int per = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ensemble_q_kernel<SP, SAT>, NTHREADS, smem);
+        if (e != cudaSuccess) return e;
+        grid = sm_count() * (per > 0 ? per : 1);
+    }
+    if (grid > total) grid = total > 0 ? total : 1;
+    ensemble_q_kernel<SP, SAT><<<grid, NTHREADS, smem, st>>>(probs, segs, nseg, total, work, done, status, abort_flag,
+                                                             spin_limit);
+    return cudaGetLastError();
 }
 
 // Planes per CTA: among 16 .. 48, the length that minimises (rounds of
 // resident CTAs) x (planes + halo cost), keeping at least 3.5 waves of CTAs
 // where the grid has that many (the paired-cell kernel's rule with this
 // kernel's tile and occupancy).
-int auto_nzchunk_q(const KGrid<float>& g)
+int auto_nzchunk_q(const KGrid<float>& g, int tx, int ty)
 {
-    const int64_t cols = (int64_t)((g.n[0] + TX - 1) / TX) * ((g.n[1] + TY - 1) / TY);
+    const int64_t cols = (int64_t)((g.n[0] + tx - 1) / tx) * ((g.n[1] + ty - 1) / ty);
     const int64_t slots = (int64_t)kCtasPerSm * sm_count();
     const bool many = cols * ((g.n[2] + 15) / 16) * 2 >= 7 * slots;
     int best = 32;
@@ -449,17 +563,35 @@ bool xq_stage_supported(const LaunchCfg& c, const KGrid<float>& g)
 }
 
 cudaError_t launch_stage_xq(const LaunchCfg& c, const KGrid<float>& g, const KPhys<float>& p, const StageIO& io,
-                            const KCoef<float>& coef, unsigned* status, int nzchunk, cudaStream_t st)
+                            const KCoef<float>& coef, unsigned* status, int nzchunk, cudaStream_t st, int txw)
 {
-    if (!xq_stage_supported(c, g)) return cudaErrorNotSupported;
+    if (!xq_stage_supported(c, g) || (txw != 64 && txw != 32)) return cudaErrorNotSupported;
     const x2::FastArgs a = x2_args(io);
-    if (nzchunk <= 0) nzchunk = xq::auto_nzchunk_q(g);
+    if (nzchunk <= 0) nzchunk = xq::auto_nzchunk_q(g, txw, txw == 64 ? xq::SmemQ<64>::TY : xq::SmemQ<32>::TY);
     if (c.saturate) {
-        if (c.spitzer) return xq::launch_q_mode<true, true>(io.mode, g, p, a, coef, status, nzchunk, st);
-        return xq::launch_q_mode<false, true>(io.mode, g, p, a, coef, status, nzchunk, st);
+        if (c.spitzer) return xq::launch_q_txw<true, true>(txw, io.mode, g, p, a, coef, status, nzchunk, st);
+        return xq::launch_q_txw<false, true>(txw, io.mode, g, p, a, coef, status, nzchunk, st);
     }
-    if (c.spitzer) return xq::launch_q_mode<true, false>(io.mode, g, p, a, coef, status, nzchunk, st);
-    return xq::launch_q_mode<false, false>(io.mode, g, p, a, coef, status, nzchunk, st);
+    if (c.spitzer) return xq::launch_q_txw<true, false>(txw, io.mode, g, p, a, coef, status, nzchunk, st);
+    return xq::launch_q_txw<false, false>(txw, io.mode, g, p, a, coef, status, nzchunk, st);
+}
+
+cudaError_t launch_ensemble_xq(bool spitzer, bool saturate, const x2::EnsProb* probs, const x2::EnsSeg* segs,
+                               int nseg, int total, int* work, unsigned* done, unsigned* status, int* abort_flag,
+                               long long spin_limit, int grid, cudaStream_t st)
+{
+    if (spitzer) {
+        if (saturate)
+            return xq::ensemble_launch_q<true, true>(probs, segs, nseg, total, work, done, status, abort_flag,
+                                                     spin_limit, grid, st);
+        return xq::ensemble_launch_q<true, false>(probs, segs, nseg, total, work, done, status, abort_flag,
+                                                  spin_limit, grid, st);
+    }
+    if (saturate)
+        return xq::ensemble_launch_q<false, true>(probs, segs, nseg, total, work, done, status, abort_flag,
+                                                  spin_limit, grid, st);
+    return xq::ensemble_launch_q<false, false>(probs, segs, nseg, total, work, done, status, abort_flag, spin_limit,
+                                               grid, st);
 }
 
 }  // namespace rkl

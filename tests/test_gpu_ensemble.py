@@ -4,6 +4,8 @@ per-launch schedules) against the FP64 oracle, problem by problem.
 * A small ensemble (8 problems, uneven sizes, conductivities, super-steps
   and stage counts, one Dirichlet problem): every cell of every problem
   after two super-steps, both schedules.
+* A periodic one: the four schedules (per-launch or persistent, paired-cell
+  or row-pair tiles) give the same bits, and match the oracle.
 * The full batched workload (64 problems with per-axis sizes drawn from
   {32, 48, 64, 96, 128, 192}, kappa_par0 in [1e-3, 1e-1], dt/dt_expl in
   [20, 400]) in the autotuned schedule: sampled cells of a few problems
@@ -88,6 +90,63 @@ def test_small_ensemble_every_cell(rk, orc, persistent, nzchunk):
         assert np.max(np.abs(got - refs[p])) < F32_STATE_MAX * np.max(np.abs(refs[p])), p
 
 
+def _periodic_specs():
+    """Eight periodic problems whose widths take both tile widths (32-column
+    tiles for 32 and 96, 64-column ones for the rest) and whose heights and
+    depths leave ragged last tiles."""
+    shapes = [(8, 12, 32), (20, 8, 96), (12, 24, 64), (6, 10, 20), (16, 40, 128), (10, 9, 24), (7, 5, 4),
+              (14, 17, 36)]
+    rng = np.random.default_rng(11)
+    out = []
+    for p, sh in enumerate(shapes):
+        prm = dict(dx=(1.0 / sh[2], 1.0 / sh[1], 1.0 / sh[0]), kappa_model="spitzer",
+                   kappa_par0=float(rng.uniform(1e-3, 1e-1)), kappa_perp_ratio=1e-4)
+        out.append(dict(shape=sh, params=prm, seed=700 + p, ratio=float(rng.uniform(10, 80))))
+    return out
+
+
+def test_ensemble_schedules_same_bits(rk, orc):
+    """Every schedule (per-launch or persistent, paired-cell or row-pair
+    tiles, several z-chunks) advances a periodic ensemble to the same bits,
+    and every cell matches the oracle after two super-steps."""
+    import torch
+    specs = _periodic_specs()
+    res = {}
+    for sched, nz in [(0, 32), (1, 32), (1, 5), (2, 32), (2, 7), (3, 32), (3, 3), (3, 16)]:
+        ens, T_all, b_all, views, host, dts = _build(rk, specs)
+        ens.set_schedule(sched, nz)
+        s_steps = [ens.super_step(dts, T_all, b_all) for _ in range(2)]
+        torch.cuda.synchronize()
+        assert ens.check() == 0
+        res[(sched, nz)] = T_all.clone()
+    for k, v in res.items():
+        assert torch.equal(v, res[(0, 32)]), k
+    refs = [T for (_, T, _) in host]
+    for k in range(2):
+        for p, (P, _, b) in enumerate(host):
+            refs[p], sref = orc.super_step(P, refs[p], b, dts[p])
+            assert s_steps[k][p] == sref
+    for p, (Tv, _) in enumerate(views):
+        got = Tv.double().cpu().numpy()
+        assert rel_l2(got, refs[p]) < F32_STATE_REL_L2, p
+
+
+def test_row_pair_schedule_needs_periodic_problems(rk):
+    """The row-pair tile body wraps its halo periodically: an ensemble with
+    a Dirichlet problem refuses schedules 2 and 3 (and the autotuner does not
+    try them), rather than running them wrongly."""
+    specs = _small_specs()                         # problem 5 is Dirichlet
+    ens, T_all, b_all, views, host, dts = _build(rk, specs)
+    for sched in (2, 3):
+        with pytest.raises(Exception):
+            ens.set_schedule(sched, 32)
+    with pytest.raises(Exception):
+        ens.set_schedule(4, 32)
+    ens.set_schedule(1, 32)
+    pers, nz, ms = ens.autotune(dts, T_all, b_all)
+    assert pers in (0, 1)
+
+
 def test_full_batched_workload_sampled(rk, orc):
     import torch
     specs = []
@@ -100,7 +159,7 @@ def test_full_batched_workload_sampled(rk, orc):
     T_before = T_all.clone()
     pers, nz, ms = ens.autotune(dts, T_all, b_all)
     assert torch.equal(T_all, T_before)            # the autotuner works on a scratch copy
-    assert pers in (0, 1) and nz in (8, 16, 32) and ms > 0
+    assert pers in (0, 1, 2, 3) and nz in (8, 16, 32) and ms > 0
     e0 = [float(Tv.double().sum()) for Tv, _ in views]
     s = ens.super_step(dts, T_all, b_all)
     torch.cuda.synchronize()

@@ -75,7 +75,7 @@ def _sampled_first_step(rk, orc, W, dtype, cells, variant=0, tol=F32_STATE_MAX):
     return plan, Td, bd, dt, e0, P
 
 
-@pytest.mark.parametrize("variant", [0, 5, 6, 7, 8, 9, 10])
+@pytest.mark.parametrize("variant", [0, 5, 6, 7, 8, 9, 10, 11])
 def test_tangled_256_sampled_and_conservation(rk, orc, variant):
     """The benchmark's 256^3 workload with the default single-stage kernel,
     the two-stage kernel (tile edges at multiples of 60 and 7) and the

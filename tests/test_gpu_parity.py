@@ -231,7 +231,7 @@ def test_tiled_kernels_match_generic(rk, orc, shape, nzchunk):
     whose runs cross tile columns) and the generic kernel (variant 1) on
     tile-aligned, ragged and degenerate shapes; all against the oracle."""
     params = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4)
-    variants = (1, 2, 3, 4, 5, 6, 8, 9, 10) if shape[2] % 4 == 0 else (1, 2)
+    variants = (1, 2, 3, 4, 5, 6, 8, 9, 10, 11) if shape[2] % 4 == 0 else (1, 2)
     res = {}
     for v in variants:
         P, plan, T, b, Td, bd = _setup(rk, "x", shape, params, "f32", v)
@@ -259,14 +259,18 @@ def test_tiled_kernels_match_generic(rk, orc, shape, nzchunk):
 @pytest.mark.parametrize("shape,nzchunk", [((37, 21, 200), 0), ((16, 16, 128), 0), ((40, 9, 68), 7),
                                            ((3, 8, 64), 1), ((24, 40, 4), 0)])
 def test_row_pair_kernel_same_bits_as_paired_cell(rk, orc, params, shape, nzchunk):
-    """The row-pair kernel (variant 10) evaluates every face, slope,
-    divergence term and update as the paired-cell kernel (variant 3) does,
-    with tile boundaries at other rows (multiples of 8 against 4) and other
-    z-chunks: after two super-steps (every stage, the first one included)
-    the two states agree bit for bit, and with the oracle."""
+    """The row-pair kernel (variant 10: 64 x 8 tiles; variant 11: 32 x 16
+    tiles, two row pairs per warp) evaluates every face, slope, divergence
+    term and update as the paired-cell kernel of the same tile width
+    (variant 3: 64 x 4; variant 9: 32 x 8) does, with tile boundaries at
+    other rows and other z-chunks: after two super-steps (every stage, the
+    first one included) each pair of states agrees bit for bit, and both
+    with the oracle.  (Across tile widths the bits differ: a cell on a
+    tile's left edge adds its left x-face to the divergence after the rest,
+    so columns at multiples of 32 but not 64 round differently.)"""
     import torch
     res = {}
-    for v in (3, 10):
+    for v in (3, 9, 10, 11):
         P, plan, T, b, Td, bd = _setup(rk, "x", shape, params, "f32", v)
         plan.set_variant(v, nzchunk)
         dt = 60 * orc.dt_expl(P, T)
@@ -275,15 +279,17 @@ def test_row_pair_kernel_same_bits_as_paired_cell(rk, orc, params, shape, nzchun
         assert plan.check() == 0
         res[v] = Td.clone()
     assert torch.equal(res[3], res[10])
+    assert torch.equal(res[9], res[11])
     Tref = T
     for _ in range(2):
         Tref, _ = orc.super_step(P, Tref, b, dt)
     assert rel_l2(host(res[10]), Tref) < F32_STATE_REL_L2
+    assert rel_l2(host(res[11]), Tref) < F32_STATE_REL_L2
 
 
 def test_row_pair_kernel_unsupported_plans(rk):
-    """Variant 10 takes periodic FP32 3D grids with nx % 4 == 0 and no
-    limiter; any other plan is refused, not silently routed elsewhere."""
+    """Variants 10 and 11 take periodic FP32 3D grids with nx % 4 == 0 and
+    no limiter; any other plan is refused, not silently routed elsewhere."""
     spitz = dict(kappa_model="spitzer", kappa_par0=0.01)
     for shape, params, dtype in [((8, 8, 30), spitz, "f32"),
                                  ((8, 8, 32), dict(spitz, bc="dirichlet", bc_value=1.0), "f32"),
@@ -291,8 +297,9 @@ def test_row_pair_kernel_unsupported_plans(rk):
                                  ((8, 8, 32), spitz, "f64"),
                                  ((16, 32), spitz, "f32")]:
         plan = rk.Plan(shape, dtype, params=params)
-        with pytest.raises(Exception):
-            plan.set_variant(10)
+        for v in (10, 11):
+            with pytest.raises(Exception):
+                plan.set_variant(v)
 
 
 @pytest.mark.parametrize("shape,nzchunk", [((7, 9, 4), 0), ((40, 3, 68), 0), ((1, 33, 64), 0), ((37, 24, 128), 5),
