@@ -87,13 +87,16 @@ __device__ __forceinline__ FaceK face_consts(const KPhys<float>& p)
     return k;
 }
 
-template <bool SP, bool SAT>
+// KP0: kappa_perp = 0 known at compile time; the perpendicular terms
+// (fma with a zero product) drop out, which for finite operands gives the
+// same bits.
+template <bool SP, bool SAT, bool KP0 = false>
 __device__ __forceinline__ float2 face2s(float2 TL, float2 TR, float2 gn, float2 g1, float2 g2, float2 Bn, float2 B1,
                                          float2 B2, const FaceK& k, const KPhys<float>& p)
 {
     const float2 Ts = add2(TL, TR);
     const float2 bdg = fma2(Bn, gn, fma2(B1, g1, mul2(B2, g2)));
-    const float2 X = fma2(Bn, bdg, mul2(bc2(k.kp4), gn));
+    const float2 X = KP0 ? mul2(Bn, bdg) : fma2(Bn, bdg, mul2(bc2(k.kp4), gn));
     if (!SAT) {
         if (SP) return mul2(mul2(mul2(Ts, Ts), sqrt2(Ts)), X);
         return X;
@@ -101,9 +104,9 @@ __device__ __forceinline__ float2 face2s(float2 TL, float2 TR, float2 gn, float2
     const float2 sTs = sqrt2(Ts);
     // |V|^2, one transverse component at a time
     float2 V2 = mul2(X, X);
-    const float2 Y1 = fma2(B1, bdg, mul2(bc2(k.kp4), g1));
+    const float2 Y1 = KP0 ? mul2(B1, bdg) : fma2(B1, bdg, mul2(bc2(k.kp4), g1));
     V2 = fma2(Y1, Y1, V2);
-    const float2 Y2 = fma2(B2, bdg, mul2(bc2(k.kp4), g2));
+    const float2 Y2 = KP0 ? mul2(B2, bdg) : fma2(B2, bdg, mul2(bc2(k.kp4), g2));
     V2 = fma2(Y2, Y2, V2);
     if (!p.upwind) {
         const float2 Vm = sqrt2(V2);

@@ -13,8 +13,9 @@
 // four cells instead of two.  The copy tasks are positions of a plane (a
 // 16-byte chunk of a tile row with its halo), each issuing the same chunk of
 // T, bx, by and bz (and of Y0, Y_{j-2}, M(Y0)), so a thread holds three
-// 32-bit offset pairs instead of six pointer tasks.  Three CTAs of 68 KB per
-// SM.
+// 32-bit offset pairs instead of six pointer tasks.  Three CTAs of 70 KB per
+// SM.  The saturated builds for kappa_perp = 0 leave out the perpendicular
+// terms at compile time (the same bits for finite values).
 //
 // Every face flux, slope, divergence term and recurrence update is the
 // same operation on the same operands, in the same order, as in the
@@ -134,7 +135,7 @@ __device__ __forceinline__ Pos y_pos(const KGrid<float>& g, int t, int i0, int j
     return Pos{(unsigned)(j0 + row) * (unsigned)g.n[0] + (unsigned)(i0 + cc), (unsigned)((row * TX + cc) * 4)};
 }
 
-template <bool SP, bool SAT, int MODE, int TXW>
+template <bool SP, bool SAT, int MODE, int TXW, bool KP0 = false>
 __device__ __forceinline__ void tile_q(SmemQ<TXW>& sm, const KGrid<float>& g, const KPhys<float>& p,
                                        const x2::FastArgs& a, KCoef<float> cf, unsigned* status, int i0, int j0,
                                        int z0, int nzc)
@@ -221,10 +222,10 @@ __device__ __forceinline__ void tile_q(SmemQ<TXW>& sm, const KGrid<float>& g, co
 
     QZ2 A = read_qz2(sm, tslot(-1), bslot(-1), c, ra);
     QZ2 B = read_qz2(sm, tslot(0), bslot(0), c, ra);
-    float2 Fzl0 = x2::face2s<SP, SAT>(A.T0, B.T0, mul2(sub2(B.T0, A.T0), idz2), mul2(add2(A.gx0, B.gx0), i4x),
+    float2 Fzl0 = x2::face2s<SP, SAT, KP0>(A.T0, B.T0, mul2(sub2(B.T0, A.T0), idz2), mul2(add2(A.gx0, B.gx0), i4x),
                                       mul2(add2(A.gy0, B.gy0), i4y), add2(A.b0[2], B.b0[2]),
                                       add2(A.b0[0], B.b0[0]), add2(A.b0[1], B.b0[1]), fk, p);
-    float2 Fzl1 = x2::face2s<SP, SAT>(A.T1, B.T1, mul2(sub2(B.T1, A.T1), idz2), mul2(add2(A.gx1, B.gx1), i4x),
+    float2 Fzl1 = x2::face2s<SP, SAT, KP0>(A.T1, B.T1, mul2(sub2(B.T1, A.T1), idz2), mul2(add2(A.gx1, B.gx1), i4x),
                                       mul2(add2(A.gy1, B.gy1), i4y), add2(A.b1[2], B.b1[2]),
                                       add2(A.b1[0], B.b1[0]), add2(A.b1[1], B.b1[1]), fk, p);
     // plane q - 1 of the z-march: T of both pairs, at column c + 2, one row up
@@ -313,29 +314,29 @@ __device__ __forceinline__ void tile_q(SmemQ<TXW>& sm, const KGrid<float>& g, co
 
         // +x faces of both pairs
         const float2 TR0 = make_float2(cur.T0.y, cur.r0), TR1 = make_float2(cur.T1.y, cur.r1);
-        const float2 Fx0 = x2::face2s<SP, SAT>(
+        const float2 Fx0 = x2::face2s<SP, SAT, KP0>(
             cur.T0, TR0, mul2(sub2(TR0, cur.T0), idx2), mul2(add2(cur.gy0, gyR0), i4y), mul2(add2(gz0, gzR0), i4z),
             add2(cur.b0[0], make_float2(cur.b0[0].y, bR0[0])), add2(cur.b0[1], make_float2(cur.b0[1].y, bR0[1])),
             add2(cur.b0[2], make_float2(cur.b0[2].y, bR0[2])), fk, p);
-        const float2 Fx1 = x2::face2s<SP, SAT>(
+        const float2 Fx1 = x2::face2s<SP, SAT, KP0>(
             cur.T1, TR1, mul2(sub2(TR1, cur.T1), idx2), mul2(add2(cur.gy1, gyR1), i4y), mul2(add2(gz1, gzR1), i4z),
             add2(cur.b1[0], make_float2(cur.b1[0].y, bR1[0])), add2(cur.b1[1], make_float2(cur.b1[1].y, bR1[1])),
             add2(cur.b1[2], make_float2(cur.b1[2].y, bR1[2])), fk, p);
         // +y faces: between the two rows, and above the upper row
-        const float2 Fy0 = x2::face2s<SP, SAT>(cur.T0, cur.T1, mul2(sub2(cur.T1, cur.T0), idy2),
+        const float2 Fy0 = x2::face2s<SP, SAT, KP0>(cur.T0, cur.T1, mul2(sub2(cur.T1, cur.T0), idy2),
                                                mul2(add2(cur.gx0, cur.gx1), i4x), mul2(add2(gz0, gz1), i4z),
                                                add2(cur.b0[1], cur.b1[1]), add2(cur.b0[0], cur.b1[0]),
                                                add2(cur.b0[2], cur.b1[2]), fk, p);
-        const float2 Fy1 = x2::face2s<SP, SAT>(cur.T1, cur.TU, mul2(sub2(cur.TU, cur.T1), idy2),
+        const float2 Fy1 = x2::face2s<SP, SAT, KP0>(cur.T1, cur.TU, mul2(sub2(cur.TU, cur.T1), idy2),
                                                mul2(add2(cur.gx1, gxU1), i4x), mul2(add2(gz1, gzU1), i4z),
                                                add2(cur.b1[1], bU1[1]), add2(cur.b1[0], bU1[0]),
                                                add2(cur.b1[2], bU1[2]), fk, p);
         // +z faces
-        const float2 Fz0 = x2::face2s<SP, SAT>(cur.T0, nxt.T0, mul2(sub2(nxt.T0, cur.T0), idz2),
+        const float2 Fz0 = x2::face2s<SP, SAT, KP0>(cur.T0, nxt.T0, mul2(sub2(nxt.T0, cur.T0), idz2),
                                                mul2(add2(cur.gx0, nxt.gx0), i4x), mul2(add2(cur.gy0, nxt.gy0), i4y),
                                                add2(cur.b0[2], nxt.b0[2]), add2(cur.b0[0], nxt.b0[0]),
                                                add2(cur.b0[1], nxt.b0[1]), fk, p);
-        const float2 Fz1 = x2::face2s<SP, SAT>(cur.T1, nxt.T1, mul2(sub2(nxt.T1, cur.T1), idz2),
+        const float2 Fz1 = x2::face2s<SP, SAT, KP0>(cur.T1, nxt.T1, mul2(sub2(nxt.T1, cur.T1), idz2),
                                                mul2(add2(cur.gx1, nxt.gx1), i4x), mul2(add2(cur.gy1, nxt.gy1), i4y),
                                                add2(cur.b1[2], nxt.b1[2]), add2(cur.b1[0], nxt.b1[0]),
                                                add2(cur.b1[1], nxt.b1[1]), fk, p);
@@ -397,18 +398,18 @@ __device__ __forceinline__ void tile_q(SmemQ<TXW>& sm, const KGrid<float>& g, co
     __syncthreads();
 }
 
-template <bool SP, bool SAT, int MODE, int TXW>
+template <bool SP, bool SAT, int MODE, int TXW, bool KP0>
 __global__ void __launch_bounds__(NTHREADS, kCtasPerSm)
 stage_q_kernel(KGrid<float> g, KPhys<float> p, x2::FastArgs a, KCoef<float> cf, unsigned* status, int nzchunk)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     SmemQ<TXW>& sm = *reinterpret_cast<SmemQ<TXW>*>(smem_raw);
     const int z0 = blockIdx.z * nzchunk;
-    tile_q<SP, SAT, MODE, TXW>(sm, g, p, a, cf, status, blockIdx.x * SmemQ<TXW>::TX, blockIdx.y * SmemQ<TXW>::TY,
+    tile_q<SP, SAT, MODE, TXW, KP0>(sm, g, p, a, cf, status, blockIdx.x * SmemQ<TXW>::TX, blockIdx.y * SmemQ<TXW>::TY,
                                z0, min(nzchunk, g.n[2] - z0));
 }
 
-template <bool SP, bool SAT, int MODE, int TXW>
+template <bool SP, bool SAT, int MODE, int TXW, bool KP0>
 cudaError_t launch_q(const KGrid<float>& g, const KPhys<float>& p, const x2::FastArgs& a, const KCoef<float>& cf,
                      unsigned* status, int nzchunk, cudaStream_t st)
 {
@@ -416,31 +417,36 @@ cudaError_t launch_q(const KGrid<float>& g, const KPhys<float>& p, const x2::Fas
     const int smem = (int)sizeof(SM);
     static bool attr_set = false;       // the attribute is per function, set once
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(stage_q_kernel<SP, SAT, MODE, TXW>,
+        cudaError_t e = cudaFuncSetAttribute(stage_q_kernel<SP, SAT, MODE, TXW, KP0>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const dim3 grid((g.n[0] + SM::TX - 1) / SM::TX, (g.n[1] + SM::TY - 1) / SM::TY, (g.n[2] + nzchunk - 1) / nzchunk);
-    stage_q_kernel<SP, SAT, MODE, TXW><<<grid, NTHREADS, smem, st>>>(g, p, a, cf, status, nzchunk);
+    stage_q_kernel<SP, SAT, MODE, TXW, KP0><<<grid, NTHREADS, smem, st>>>(g, p, a, cf, status, nzchunk);
     return cudaGetLastError();
 }
 
-template <bool SP, bool SAT, int TXW>
+template <bool SP, bool SAT, int TXW, bool KP0>
 cudaError_t launch_q_mode(int mode, const KGrid<float>& g, const KPhys<float>& p, const x2::FastArgs& a,
                           const KCoef<float>& cf, unsigned* status, int nzchunk, cudaStream_t st)
 {
-    if (mode == 0) return launch_q<SP, SAT, 0, TXW>(g, p, a, cf, status, nzchunk, st);
-    if (mode == 1) return launch_q<SP, SAT, 1, TXW>(g, p, a, cf, status, nzchunk, st);
-    return launch_q<SP, SAT, 2, TXW>(g, p, a, cf, status, nzchunk, st);
+    if (mode == 0) return launch_q<SP, SAT, 0, TXW, KP0>(g, p, a, cf, status, nzchunk, st);
+    if (mode == 1) return launch_q<SP, SAT, 1, TXW, KP0>(g, p, a, cf, status, nzchunk, st);
+    return launch_q<SP, SAT, 2, TXW, KP0>(g, p, a, cf, status, nzchunk, st);
 }
 
 template <bool SP, bool SAT>
 cudaError_t launch_q_txw(int txw, int mode, const KGrid<float>& g, const KPhys<float>& p, const x2::FastArgs& a,
                          const KCoef<float>& cf, unsigned* status, int nzchunk, cudaStream_t st)
 {
-    if (txw == 32) return launch_q_mode<SP, SAT, 32>(mode, g, p, a, cf, status, nzchunk, st);
-    return launch_q_mode<SP, SAT, 64>(mode, g, p, a, cf, status, nzchunk, st);
+    // the saturated builds also come without the kappa_perp terms (kappa_perp = 0)
+    if (SAT && p.kperp == 0.f) {
+        if (txw == 32) return launch_q_mode<SP, SAT, 32, SAT>(mode, g, p, a, cf, status, nzchunk, st);
+        return launch_q_mode<SP, SAT, 64, SAT>(mode, g, p, a, cf, status, nzchunk, st);
+    }
+    if (txw == 32) return launch_q_mode<SP, SAT, 32, false>(mode, g, p, a, cf, status, nzchunk, st);
+    return launch_q_mode<SP, SAT, 64, false>(mode, g, p, a, cf, status, nzchunk, st);
 }
 
 // Persistent ensemble kernel on the row-pair tile body: the work list,
@@ -528,7 +534,7 @@ cudaError_t ensemble_launch_q(const x2::EnsProb* probs, const x2::EnsSeg* segs, 
     return cudaGetLastError();
 }
 
-// Planes per CTA: among 16 .. 48, the length that minimises (rounds of
+// Planes per CTA: among 16 .. 64, the length that minimises (rounds of
 // resident CTAs) x (planes + halo cost), keeping at least 3.5 waves of CTAs
 // where the grid has that many (the paired-cell kernel's rule with this
 // kernel's tile and occupancy).
@@ -539,7 +545,7 @@ int auto_nzchunk_q(const KGrid<float>& g, int tx, int ty)
     const bool many = cols * ((g.n[2] + 15) / 16) * 2 >= 7 * slots;
     int best = 32;
     double cost = 1e300;
-    for (int nzc = 16; nzc <= 48; ++nzc) {
+    for (int nzc = 16; nzc <= 64; ++nzc) {
         const int64_t chunks = (g.n[2] + nzc - 1) / nzc;
         if (many && cols * chunks * 2 < 7 * slots) continue;
         const int64_t rounds = (cols * chunks + slots - 1) / slots;
