@@ -19,7 +19,9 @@
 // once per persistent CTA as [9][Cin/8][3 Cout][8].  The CTA is a
 // pipeline of three roles that meet only at mbarriers: three loader warps
 // stream input planes into the ring with cp.async, keeping two planes in
-// flight per thread; once a plane's copies have landed each loader fences
+// flight per thread (each thread's 16-byte chunks of the halo plane are
+// fixed for a work item, so a plane costs one address add per chunk);
+// once a plane's copies have landed each loader fences
 // them into the tensor cores' (async) proxy and arrives on the slot's
 // "full" barrier.  Thread 0 issues the MMAs of a plane once it is full and
 // commits them to the slot's "empty" barrier (the loaders refill the slot
@@ -52,8 +54,9 @@ constexpr int QX = 8, QY = 16;                 // output block of a plane: M = 1
 constexpr int HX = QX + 2, HY = QY + 2;         // halo plane
 constexpr int HP = HX * HY;                     // 180 voxels
 constexpr int NSLOT = 5;                        // input-plane ring
-constexpr int NTHR_TC = 256;                    // warp 0 MMA, warps 1-3 loads, warps 4-7 TMEM lane quarters
-constexpr int NLOAD = 96;                       // loader threads
+constexpr int NLW = 3;                          // loader warps
+constexpr int NLOAD = 32 * NLW;                 // loader threads
+constexpr int NTHR_TC = 32 * (1 + NLW + 4);     // warp 0 MMA, warps 1 .. NLW loads, the last four drain
 constexpr int NZC_TC = 6;                       // output planes per work item
 constexpr int TMEM_COLS = 256;                  // 32 (NZC_TC + 2) columns
 
@@ -280,24 +283,40 @@ conv_tc_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __rest
                 }
             }
         }
-    } else if (warp < 4) {
-        // ---------------- loads (warps 1-3) ----------------
+    } else if (warp <= NLW) {
+        // ---------------- loads (warps 1 .. NLW) ----------------
         const int lt = tid - 32;
+        // copy tasks of this thread for the current item: 16-byte chunks of
+        // the halo plane (element offset within an input plane, byte offset
+        // within a ring slot), fixed for the item's planes
+        constexpr int NTASK = (HP * NCH + NLOAD - 1) / NLOAD;
+        int toff[NTASK];
+        unsigned tdst[NTASK];
+        const unsigned abase = smem_u32(&sm.A[0][0][0][0]);
+        constexpr unsigned kSlotBytes = (unsigned)(NCH * HP * 16);
+        const int64_t zstride = (int64_t)H * W * CIN;
         unsigned n = 0;
         for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
             const int col = item % ncols, chunk = item / ncols;
             const int x0 = (col % ncolx) * QX, y0 = (col / ncolx) * QY, z0 = chunk * NZC_TC;
             const int nz = min(NZC_TC, D - z0);
+#pragma unroll
+            for (int i = 0; i < NTASK; ++i) {
+                const int t = lt + i * NLOAD;
+                const int hv = t / NCH, ch = t % NCH;
+                const int gy = wrapi_tc(y0 + hv / HX - 1, H), gx = wrapi_tc(x0 + hv % HX - 1, W);
+                toff[i] = t < HP * NCH ? (gy * W + gx) * CIN + ch * 8 : -1;
+                tdst[i] = (unsigned)((ch * HP + hv) * 16);
+            }
             for (int q = -1; q <= nz; ++q, ++n) {
                 const unsigned sl = n % NSLOT;
                 // the slot's previous plane (n - NSLOT) has been multiplied
                 if (n >= NSLOT) wait(sm.empty[sl], (n / NSLOT - 1) & 1u);
-                const int gz = wrapi_tc(z0 + q, D);
-                for (int t = lt; t < HP * NCH; t += NLOAD) {
-                    const int hv = t / NCH, ch = t % NCH;
-                    const int gy = wrapi_tc(y0 + hv / HX - 1, H), gx = wrapi_tc(x0 + hv % HX - 1, W);
-                    cp16(smem_u32(&sm.A[sl][ch][hv][0]), in + (((int64_t)gz * H + gy) * W + gx) * CIN + ch * 8);
-                }
+                const __nv_bfloat16* pz = in + (int64_t)wrapi_tc(z0 + q, D) * zstride;
+                const unsigned sb = abase + sl * kSlotBytes;
+#pragma unroll
+                for (int i = 0; i < NTASK; ++i)
+                    if (toff[i] >= 0) cp16(sb + tdst[i], pz + toff[i]);
                 cp_commit();
                 // the previous plane's copies have landed: make them visible to
                 // the tensor cores' proxy and report the slot full
@@ -314,8 +333,8 @@ conv_tc_kernel(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __rest
             mbar_arrive(smem_u32(&sm.full[(n - 1) % NSLOT]));
         }
     } else {
-        // ---------------- drain (warps 4-7, TMEM lane quarter warp - 4) ----------------
-        const int q4 = warp - 4;
+        // ---------------- drain (the last four warps; a warp reaches TMEM lane quarter warp % 4) ----------------
+        const int q4 = warp & 3;
         const unsigned tlane = tbase + ((unsigned)(q4 * 32) << 16);
         float bs[COUT];
 #pragma unroll
@@ -434,6 +453,7 @@ cudaError_t conv_forward_tc(int cin, int cout, int mode, const void* in, const v
 {
     (void)nzc;                                   // the chunk length is fixed by the TMEM columns
     if (W % QX || H % QY || D < 1) return cudaErrorInvalidValue;
+    if ((int64_t)H * W * cin >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;     // 32-bit in-plane offsets
     if (cin == 16 && cout == 32 && mode == 0)
         return conv_tc_t<16, 32, 0>(in, wt, bias, mask, out, D, H, W, status, st);
     if (cin == 32 && cout == 32 && mode == 0)
