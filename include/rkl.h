@@ -522,7 +522,9 @@ rkl_status rkl_sur_layer_weight_grad(rkl_surrogate *sur, int layer, const void *
 /*
  * One super-step of length dt with the surrogate: predicts dT, computes the
  * trapezoidal-rule residual rho = ||dT - (dt/2)(M(T) + M(T + dT))|| / ||dT||
- * (two applications of M), accepts T + dT if rho <= threshold, otherwise
+ * (two applications of M; with flux features, rkl_sur_set_flux_features,
+ * M(T) is the divergence of the face fluxes the features already evaluated,
+ * so only M(T + dT) is a full evaluation), accepts T + dT if rho <= threshold, otherwise
  * runs rkl_super_step (the fallback).  *accepted, *residual, *s_used (0
  * when accepted) are written.  The plan must describe the same periodic 3D
  * FP32 patch.

@@ -39,6 +39,22 @@ __global__ void axpy_kernel(const float* a, const float* b, float* out, int64_t 
         out[i] = a[i] + b[i];
 }
 
+// M = -sum_d (F_d(c) - F_d(c - e_d)) / dx_d on the periodic patch from the
+// face fluxes of rkl_flux (the flux at face c + e_d / 2 stored at c): the
+// conservative divergence, without evaluating the fluxes again
+__global__ void div3_kernel(const float* __restrict__ F, int D, int H, int W, float ix, float iy, float iz,
+                            float* __restrict__ M)
+{
+    const int64_t V = (int64_t)D * H * W;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < V; c += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(c % W), y = (int)((c / W) % H), z = (int)(c / ((int64_t)W * H));
+        const int64_t cx = c - x + (x == 0 ? W - 1 : x - 1);
+        const int64_t cy = c + (int64_t)((y == 0 ? H - 1 : y - 1) - y) * W;
+        const int64_t cz = c + (int64_t)((z == 0 ? D - 1 : z - 1) - z) * W * H;
+        M[c] = -((F[c] - F[cx]) * ix + (F[V + c] - F[V + cy]) * iy + (F[2 * V + c] - F[2 * V + cz]) * iz);
+    }
+}
+
 // sums of (dT - h (M0 + Mp))^2 and dT^2 in FP64, per block
 __global__ void residual_kernel(const float* dT, const float* M0, const float* Mp, float h, int64_t n, double* part)
 {
@@ -472,8 +488,16 @@ rkl_status rkl_sur_super_step(rkl_surrogate* s, rkl_plan* plan, double dt, void*
     // residual of the trapezoidal rule: dT - (dt / 2) (M(Y0) + M(Y0 + dT)), relative to dT
     axpy_kernel<<<1024, 256, 0, s->stream>>>(static_cast<const float*>(T), s->dT, s->Yp, s->V);
     SUR_CK(s, cudaGetLastError());
-    st = rkl_apply_M(plan, T, b, s->M0);
-    if (st != RKL_OK) return st;
+    if (s->flux_c > 0.0) {
+        // the flux features left T's face fluxes in F3: M(Y0) is their
+        // divergence, so the check evaluates M only once, at Y0 + dT
+        div3_kernel<<<1024, 256, 0, s->stream>>>(s->F3, s->D, s->H, s->W, s->inv_dx[0], s->inv_dx[1], s->inv_dx[2],
+                                                 s->M0);
+        SUR_CK(s, cudaGetLastError());
+    } else {
+        st = rkl_apply_M(plan, T, b, s->M0);
+        if (st != RKL_OK) return st;
+    }
     st = rkl_apply_M(plan, s->Yp, b, s->Mp);
     if (st != RKL_OK) return st;
     residual_kernel<<<kPartials, 256, 0, s->stream>>>(s->dT, s->M0, s->Mp, (float)(0.5 * dt), s->V, s->d_part);

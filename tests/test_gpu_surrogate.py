@@ -310,6 +310,38 @@ def test_surrogate_super_step_accept_and_fallback(rk):
     rk._lib.rkl_sur_destroy(sur)
 
 
+def test_residual_check_with_flux_features_evaluates_m_once(rk):
+    """With flux features the residual check takes M(Y0) as the divergence
+    of the face fluxes the features already hold, and evaluates M only at
+    Y0 + dT: the residual it reports equals the trapezoidal residual built
+    from two full M evaluations (plan.apply_M) up to FP32 rounding."""
+    import torch
+    shape = (16, 16, 32)
+    sur, params, T, b, Td, bd, dx = _setup(rk, shape=shape)
+    prm = dict(dx=(1.0 / shape[2], 1.0 / shape[1], 1.0 / shape[0]), kappa_model="spitzer", kappa_par0=0.01,
+               kappa_perp_ratio=1e-4)
+    plan = rk.Plan(shape, "f32", params=prm)
+    dt = 50 * plan.dt_expl(Td)
+    hs, c = 2e-3, 1.0 / 16
+    rk._lib.rkl_sur_set_flux_features(sur, c)
+    T1 = Td.clone()
+    acc, rho, _ = rk._lib.rkl_sur_super_step(sur, plan.handle, dt, T1, bd, hs, 0.0)
+    assert not acc
+    ratio = dt / plan.dt_expl(Td)
+    rk._lib.rkl_sur_features_flux(sur, plan.handle, Td, bd, ratio, c * dt / hs)
+    dT = torch.empty_like(Td)
+    rk._lib.rkl_sur_forward(sur, hs, dT)
+    M0, Mp = torch.empty_like(Td), torch.empty_like(Td)
+    plan.apply_M(Td, bd, M0)
+    plan.apply_M(Td + dT, bd, Mp)
+    torch.cuda.synchronize()
+    d = dT.double()
+    r = d - 0.5 * dt * (M0.double() + Mp.double())
+    ref = float(r.norm() / d.norm())
+    assert abs(rho - ref) <= 1e-3 * ref, (rho, ref)
+    rk._lib.rkl_sur_destroy(sur)
+
+
 def test_tcgen05_backend_matches_warp_mma_and_oracle(rk):
     """The tcgen05 convolutions (TMEM accumulators) against the warp-level
     mma.sync ones on the same BF16 inputs -- they differ only in the order
