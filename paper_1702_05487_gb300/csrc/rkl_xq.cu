@@ -63,8 +63,10 @@ struct SmemQ {
     static constexpr int NT = 3 + PD, NB = 2 + PD, NY = 1 + PD;
     alignas(16) float T[NT][PLANE];
     float B[NB][3][PLANE];
-    float Y[NY][3][TY * TX];
-    float Fy[2][NRP + 1][TX];       // row k: lower y-face of row 2k (k = 0: the tile's boundary)
+    // rows of TX floats read as 64-bit pairs by a whole row of lanes: on
+    // 128-byte boundaries a row is two shared-memory wavefronts, not three
+    alignas(128) float Y[NY][3][TY * TX];
+    alignas(128) float Fy[2][NRP + 1][TX];   // row k: lower y-face of row 2k (k = 0: the tile's boundary)
     float FxLo[2][TY];              // x-faces on the tile's left boundary
     __device__ static int off(int r, int c) { return (r + 1) * SXS + c + 4; }
 };
