@@ -275,14 +275,16 @@ rkl_status rkl_energy(rkl_plan *plan, const void *T, double *E_out);
  * 10 = the row-pair kernel (the paired-cell arithmetic with two cell pairs
  * per thread, rows 2w and 2w + 1 of 64 x 8 tiles, three CTAs per SM; the
  * same bits as the paired-cell kernel; periodic grids with fewer than 2^31
- * cells, nx % 4 == 0, no limiter, else RKL_ERR_UNSUPPORTED; nzchunk <= 0
- * picks the chunk length), 11 = the row-pair kernel with tiles 32 columns
+ * cells, nx % 4 == 0, no limiter or the MC limiter at every face
+ * (limiter_floor = +inf, a limited build with 64-column tiles), else
+ * RKL_ERR_UNSUPPORTED; nzchunk <= 0 picks the chunk length), 11 = the row-pair kernel with tiles 32 columns
  * wide and 16 rows high (two row pairs per warp, one per half-warp; same
  * conditions and bits as 10; variant 0 takes it where the width is an odd
  * multiple of 32).  With the MC limiter at every face
- * (limiter_floor = +inf) variants 3, 4, 6 and 7 all launch the paired-cell
- * kernel's limited build (20 resident warps per SM, per-thread copies);
- * with a finite floor the paired-cell variants do not apply.
+ * (limiter_floor = +inf) variants 0, 10 and 11 launch the row-pair kernel's
+ * limited build on periodic grids, variants 3, 4, 6 and 7 the paired-cell
+ * kernel's (20 resident warps per SM, per-thread copies; the same bits);
+ * with a finite floor neither applies.
  * RKL_ERR_UNSUPPORTED if the kernel does not apply to the grid.  nzchunk = planes per CTA of the paired-cell
  * kernels (0: chosen from the grid and the SM count, at least 3.5 waves of
  * CTAs where the grid has that many and a last wave that is nearly full); a

@@ -951,7 +951,7 @@ rkl_status rkl_plan_set_variant(rkl_plan* p, int variant, int nzchunk)
         return fail(p, RKL_ERR_UNSUPPORTED, "no paired-cell kernel for this grid");
     if ((variant == 10 || variant == 11) && !p->xqok)
         return fail(p, RKL_ERR_UNSUPPORTED,
-                    "no row-pair kernel for this grid (periodic FP32 3D, nx % 4 == 0, no limiter, < 2^31 cells)");
+                    "no row-pair kernel for this grid (periodic FP32 3D, nx % 4 == 0, no limiter or the limiter at every face, < 2^31 cells)");
     if (variant == 5 && !(p->pairok && p->x2ok))
         return fail(p, RKL_ERR_UNSUPPORTED, "no two-stage kernel for this grid (periodic FP32 3D, nx % 4 == 0)");
     if (variant == 5 && !p->ybuf4) {

@@ -255,7 +255,9 @@ def test_tiled_kernels_match_generic(rk, orc, shape, nzchunk):
     dict(kappa_par0=0.02, kappa_perp_ratio=0.1, saturate=True, phi=0.003),
     dict(kappa_model="spitzer", kappa_par0=0.01, saturate=True, phi=0.05, sat_upwind=True),
     dict(kappa_par0=0.02, kappa_perp_ratio=0.1),
-], ids=["spitzer", "sat", "sat_const", "sat_upwind", "const"])
+    dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4, limiter="mc"),
+    dict(kappa_model="spitzer", kappa_par0=0.01, saturate=True, phi=0.3, limiter="mc"),
+], ids=["spitzer", "sat", "sat_const", "sat_upwind", "const", "mc", "mc_sat"])
 @pytest.mark.parametrize("shape,nzchunk", [((37, 21, 200), 0), ((16, 16, 128), 0), ((40, 9, 68), 7),
                                            ((3, 8, 64), 1), ((24, 40, 4), 0)])
 def test_row_pair_kernel_same_bits_as_paired_cell(rk, orc, params, shape, nzchunk):
@@ -288,12 +290,13 @@ def test_row_pair_kernel_same_bits_as_paired_cell(rk, orc, params, shape, nzchun
 
 
 def test_row_pair_kernel_unsupported_plans(rk):
-    """Variants 10 and 11 take periodic FP32 3D grids with nx % 4 == 0 and
-    no limiter; any other plan is refused, not silently routed elsewhere."""
+    """Variants 10 and 11 take periodic FP32 3D grids with nx % 4 == 0,
+    without a limiter or with it at every face; any other plan is refused,
+    not silently routed elsewhere."""
     spitz = dict(kappa_model="spitzer", kappa_par0=0.01)
     for shape, params, dtype in [((8, 8, 30), spitz, "f32"),
                                  ((8, 8, 32), dict(spitz, bc="dirichlet", bc_value=1.0), "f32"),
-                                 ((8, 8, 32), dict(spitz, limiter="mc"), "f32"),
+                                 ((8, 8, 32), dict(spitz, limiter="mc", limiter_floor=1.0), "f32"),
                                  ((8, 8, 32), spitz, "f64"),
                                  ((16, 32), spitz, "f32")]:
         plan = rk.Plan(shape, dtype, params=params)
@@ -523,24 +526,25 @@ def test_invalid_arguments_and_device_status(rk):
 
 
 def test_limiter_plan_kernel_routing(rk, orc):
-    """A limiter plan with the floor at +inf runs the paired-cell kernel's
-    limited build under variant 0 and every paired-cell variant (so their
-    results are bit-identical), the tiled kernel under variant 2; with a
-    finite floor the paired-cell variants do not apply."""
+    """A limiter plan with the floor at +inf runs the row-pair kernel's
+    limited build under variant 0 and 10, the paired-cell kernel's under
+    every paired-cell variant (the two write the same bits), the tiled
+    kernel under variant 2; with a finite floor neither the paired-cell nor
+    the row-pair variants apply."""
     params = dict(kappa_model="spitzer", kappa_par0=0.01, kappa_perp_ratio=1e-4, limiter="mc")
     shape = (12, 9, 72)
     outs = {}
-    for v in (0, 3, 4, 6, 7, 2):
+    for v in (0, 3, 4, 6, 7, 10, 2):
         P, plan, T, b, Td, bd = _setup(rk, "routing", shape, params, "f32", v)
         dt = 100.0 * orc.dt_expl(P, T)
         plan.super_step(dt, Td, bd)
         assert plan.check() == 0
         outs[v] = host(Td)
-    for v in (3, 4, 6, 7):
+    for v in (3, 4, 6, 7, 10):
         assert np.array_equal(outs[v], outs[0]), v
     # the tiled kernel's rounding differs, its result agrees within FP32
     assert rel_l2(outs[2], outs[0]) < 1e-6
     P, plan, T, b, Td, bd = _setup(rk, "routing", shape, dict(params, limiter_floor=1.0), "f32", 0)
-    for v in (3, 4, 6, 7):
+    for v in (3, 4, 6, 7, 10, 11):
         with pytest.raises(rk.RklError):
             plan.set_variant(v)
