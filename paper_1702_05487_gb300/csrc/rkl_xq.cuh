@@ -62,21 +62,32 @@ struct SmemQ {
     static constexpr int TX = TXW, LPR = TXW / 2, SEGS = 32 / LPR;
     static constexpr int TY = 2 * SEGS * NWARPS;        // 8 rows (64 columns) or 16 (32 columns)
     static constexpr int NRP = TY / 2;                  // row pairs
-    static constexpr int SXS = TX + 8;                  // smem row: halo chunk, interior, halo chunk
-    static constexpr int CPR = SXS / 4;                 // 16-byte chunks per smem row
-    static constexpr int ROWS = TY + 2, PLANE = ROWS * SXS;
+    // A plane: the interior rows (-1 .. TY, TX floats each, 128-byte
+    // aligned so that a row of lanes reads a row in two shared-memory
+    // wavefronts), then the rows' halo chunks (the 4 columns left and the 4
+    // right of each row), padded to a 128-byte multiple.
+    static constexpr int CPR = (TX + 8) / 4;            // 16-byte chunks of a row with its halo
+    static constexpr int ROWS = TY + 2;
+    static constexpr int HALO = ROWS * TX;              // first halo chunk of a plane
+    static constexpr int PLANE = (ROWS * (TX + 8) + 31) / 32 * 32;
     static constexpr int kPos = ROWS * CPR;             // T / b chunk positions of a plane (180)
     static constexpr int kYPos = TY * (TX / 4);         // Y chunk positions (128: one per thread)
     static_assert(kPos <= 2 * NTHREADS && kYPos == NTHREADS, "copy positions");
     static constexpr int NT = 3 + PD, NB = 2 + PD, NY = 1 + PD;
-    alignas(16) float T[NT][PLANE];
-    float B[NB][3][PLANE];
+    alignas(128) float T[NT][PLANE];
+    alignas(128) float B[NB][3][PLANE];
     // rows of TX floats read as 64-bit pairs by a whole row of lanes: on
     // 128-byte boundaries a row is two shared-memory wavefronts, not three
     alignas(128) float Y[NY][3][TY * TX];
     alignas(128) float Fy[2][NRP + 1][TX];   // row k: lower y-face of row 2k (k = 0: the tile's boundary)
     float FxLo[2][TY];              // x-faces on the tile's left boundary
-    __device__ static int off(int r, int c) { return (r + 1) * SXS + c + 4; }
+    // offset of interior cell (row r, column c), 0 <= c < TX, in a plane
+    __device__ static int offI(int r, int c) { return (r + 1) * TX + c; }
+    // offset of any cell of a row with its halo, -4 <= c < TX + 4
+    __device__ static int off(int r, int c)
+    {
+        return (c >= 0 && c < TX) ? offI(r, c) : HALO + (r + 1) * 8 + (c < 0 ? c + 4 : c - TX + 4);
+    }
 };
 using Smem = SmemQ<64>;
 
@@ -97,10 +108,10 @@ __device__ __forceinline__ QZ2 read_qz2(const SM& sm, int ts, int bs, int c, int
     const int rb = ra + 1;
     const float* T = sm.T[ts];
     QZ2 q;
-    const float2 Td = lds2(&T[SM::off(ra - 1, c)]);
-    const float2 Tc0 = lds2(&T[SM::off(ra, c)]);
-    const float2 Tc1 = lds2(&T[SM::off(rb, c)]);
-    const float2 Tu = lds2(&T[SM::off(rb + 1, c)]);
+    const float2 Td = lds2(&T[SM::offI(ra - 1, c)]);
+    const float2 Tc0 = lds2(&T[SM::offI(ra, c)]);
+    const float2 Tc1 = lds2(&T[SM::offI(rb, c)]);
+    const float2 Tu = lds2(&T[SM::offI(rb + 1, c)]);
     const float l0 = T[SM::off(ra, c - 1)], l1 = T[SM::off(rb, c - 1)];
     q.r0 = T[SM::off(ra, c + 2)];
     q.r1 = T[SM::off(rb, c + 2)];
@@ -113,8 +124,8 @@ __device__ __forceinline__ QZ2 read_qz2(const SM& sm, int ts, int bs, int c, int
     q.gy1 = x2::cslope<LIM>(Tu, Tc1, Tc0);
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-        q.b0[e] = lds2(&sm.B[bs][e][SM::off(ra, c)]);
-        q.b1[e] = lds2(&sm.B[bs][e][SM::off(rb, c)]);
+        q.b0[e] = lds2(&sm.B[bs][e][SM::offI(ra, c)]);
+        q.b1[e] = lds2(&sm.B[bs][e][SM::offI(rb, c)]);
     }
     return q;
 }
@@ -311,7 +322,7 @@ __device__ __forceinline__ void tile_q(SmemQ<TXW>& sm, const KGrid<float>& g, co
             const float* Bp = sm.B[bs][e];
             bR0[e] = Bp[Smem::off(ra, c + 2)];
             bR1[e] = Bp[Smem::off(rb, c + 2)];
-            bU1[e] = lds2(&Bp[Smem::off(rb + 1, c)]);
+            bU1[e] = lds2(&Bp[Smem::offI(rb + 1, c)]);
         }
         nxt = read_qz2<LIM>(sm, tslot(q + 1), bslot(q + 1), c, ra);
 
