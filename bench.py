@@ -42,12 +42,12 @@ WORKLOAD = "tangled256_spitzer_rkl2"
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of the stage
 # kernel), valid only while the stage kernel's sources hash to source_hash
 # (sha256 of STAGE_KERNEL_SOURCES, 16 hex).
-MEASURED_TRAFFIC = {"source_hash": "f2a50eaa1507443e", "bytes_per_launch": 546675968}
+MEASURED_TRAFFIC = {"source_hash": "f470e08b66f9d7b3", "bytes_per_launch": 546675968}
 
 
 # the sources of the default stage kernel (stage_q_kernel, the row-pair
 # kernel, built on the paired-cell kernel's face and copy helpers)
-STAGE_KERNEL_SOURCES = ("rkl_xq.cu", "rkl_x2_tile.cuh", "rkl_x2.cuh", "rkl_pair.cuh", "rkl_device.cuh")
+STAGE_KERNEL_SOURCES = ("rkl_xq.cuh", "rkl_xq.cu", "rkl_x2_tile.cuh", "rkl_x2.cuh", "rkl_pair.cuh", "rkl_device.cuh")
 
 
 def kernel_source_hash() -> str:

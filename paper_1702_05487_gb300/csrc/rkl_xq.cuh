@@ -1,11 +1,11 @@
-// Row-pair FP32 3D stage kernel: shared-memory layout, tile body, kernel
-// template and launch helpers, shared by the translation units that
-// instantiate it (rkl_xq.cu: the classical flux and the ensemble kernel;
-// rkl_xq_sat.cu: the saturated flux; rkl_xq_lim.cu: the MC-limited
-// transverse gradients), so that the instantiations compile in parallel.
+// Row-pair FP32 3D stage kernel for the RKL2 conduction super-step:
+// shared-memory layout, tile body, kernel template and launch helpers,
+// shared by the translation units that instantiate it (rkl_xq.cu: the
+// classical flux and the ensemble kernel; rkl_xq_sat.cu: the saturated flux;
+// rkl_xq_lim.cu: the MC-limited transverse gradients), so that the
+// instantiations compile in parallel.
 //
-// Row-pair FP32 3D stage kernel for the RKL2 conduction super-step: the
-// paired-cell kernel's arithmetic with each thread owning two cell pairs,
+// The kernel runs the paired-cell kernel's arithmetic with each thread owning two cell pairs,
 // (2l, 2l + 1) in rows 2w and 2w + 1 of a 64 x 8 tile (lane l, warp w).
 // With 32-column tiles (for grids whose width is an odd multiple of 32) a
 // warp holds two row pairs side by side in its lane halves: lanes 0-15 rows
@@ -20,8 +20,13 @@
 // 16-byte chunk of a tile row with its halo), each issuing the same chunk of
 // T, bx, by and bz (and of Y0, Y_{j-2}, M(Y0)), so a thread holds three
 // 32-bit offset pairs instead of six pointer tasks.  Three CTAs of 70 KB per
-// SM.  The saturated builds for kappa_perp = 0 leave out the perpendicular
-// terms at compile time (the same bits for finite values).
+// SM.  Every shared-memory row that a row of lanes reads starts on a
+// 128-byte boundary (the T and b planes keep their rows' halo chunks apart
+// from the interior rows), so that a 256-byte row is two wavefronts.  The
+// saturated builds for kappa_perp = 0 leave out the perpendicular terms at
+// compile time (the same bits for finite values); the limited builds (the
+// MC limiter at every face) carry half the limited slopes, as the
+// paired-cell kernel's limited build does.
 //
 // Every face flux, slope, divergence term and recurrence update is the
 // same operation on the same operands, in the same order, as in the
