@@ -412,7 +412,7 @@ rkl_status rkl_ensemble_check(rkl_ensemble *ens);
 /*
  * Autotuner: times one super-step of every candidate schedule (persistent
  * with nzchunk 8, 16, 32; per-launch with 16, 32; each with either tile
- * body) on a scratch copy of
+ * body; persistent row-pair with 48, 64) on a scratch copy of
  * T_all (T_all itself is not changed), keeps the fastest and returns it.
  * Allocates and frees one T_all-sized scratch array.
  */

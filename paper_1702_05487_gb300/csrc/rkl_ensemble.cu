@@ -478,7 +478,8 @@ rkl_status rkl_ensemble_autotune(rkl_ensemble* e, const double* dt, const void* 
     cudaEvent_t a = nullptr, b = nullptr;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    const int cand[][2] = {{1, 8}, {1, 16}, {1, 32}, {3, 8}, {3, 16}, {3, 32}, {0, 16}, {0, 32}, {2, 16}, {2, 32}};
+    const int cand[][2] = {{1, 8}, {1, 16}, {1, 32}, {3, 8}, {3, 16}, {3, 32}, {3, 48}, {3, 64},
+                           {0, 16}, {0, 32}, {2, 16}, {2, 32}};
     double best = 1e300;
     int bp = 1, bz = 32;
     const int keep_p = e->persistent, keep_z = e->nzchunk;
